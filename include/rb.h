@@ -1,0 +1,162 @@
+/*
+ * rb.h -- C ABI of the GB300 (sm_103a) greedy reduced-basis library.
+ *
+ * Method: Antil, Chen, Field, "A Note on QR-Based Model Reduction: Algorithm,
+ * Software, and Gravitational Wave Applications", arXiv 1805.06124.
+ *   - RB-greedy, Alg. 3 (Sec. 5.2.1), equivalent to MGS with column pivoting,
+ *     Alg. 2 (Prop. 5.3): a column-pivoted QR of the snapshot matrix S.
+ *   - pivot search with the incremental residual bookkeeping of Eq. (Residual)
+ *     (Sec. 6.1.2): err_j = ||s_j||^2 - sum_l |c_lj|^2, c_lj = q_l^H s_j,
+ *     norms and sums stored separately, no square roots in the argmax.
+ *   - orthogonalisation of each pivot column by Hoffmann's iterated
+ *     Gram-Schmidt (MGSCI, kappa = 2; Sec. 6.1.2 and the remark after
+ *     Prop. 5.3).
+ *   - stopping rule of Cor. 5.4: the max error equals R(k+1,k+1).
+ *
+ * Conventions shared by every entry point:
+ *   - complex128 = two doubles (re, im) interleaved; complex64 = two floats.
+ *   - S (the paper's N x M snapshot matrix) is column-major: snapshot j
+ *     occupies S + j*ldS (in complex elements), N entries, ldS >= N.
+ *   - Q is column-major N x kmax: basis vector q_l at Q + l*ldQ, ldQ >= N.
+ *   - C is row-major kmax x M: C[l*ldC + j] = q_l^H s_j, ldC >= M.
+ *   - c = q^H s (conjugate on the basis vector); |c|^2 = c c^*.
+ *   - tol is a tolerance on the SQUARED error: a vector is appended only while
+ *     max_j err_j >= tol, so every column ends with err_j < tol unless kmax
+ *     or min(N, M) is reached first.
+ *   - ties in the argmax go to the lowest column index; picked columns are
+ *     excluded.
+ *   - Pointers are DEVICE pointers unless an entry point says otherwise.  They
+ *     are borrowed: the caller allocates them (outputs at capacity kmax) and
+ *     keeps them valid until the call returns.  Inputs are never modified.
+ *   - Calls are issued on the context's stream.  The greedy entry points
+ *     synchronise that stream before returning (they return k and a status);
+ *     rb_generate, rb_split and rb_project are asynchronous.
+ *   - Return value: 0 = success, > 0 = warning (outputs valid), < 0 = error
+ *     (outputs unspecified).  rb_last_error() describes the last failure.
+ *     No call aborts the process or traps on the device; device-side waits
+ *     are bounded and report RB_ETIMEOUT.
+ *   - One context per host thread; a context is not thread-safe.
+ */
+#ifndef RB_GB300_H
+#define RB_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rb_ctx rb_ctx;
+
+typedef enum rb_status {
+    RB_OK = 0,
+    RB_KMAX_REACHED = 1,   /* warning: kmax vectors built, max err still >= tol */
+    RB_EINVAL = -1,        /* bad argument (size, leading dimension, alignment, option) */
+    RB_ENOMEM = -2,        /* device workspace could not be allocated */
+    RB_ECUDA = -3,         /* a CUDA runtime call failed */
+    RB_ENONFINITE = -4,    /* NaN or Inf in the input */
+    RB_EORTHO = -5,        /* IMGS did not meet the kappa test within imgs_max_passes */
+    RB_ETIMEOUT = -6,      /* a bounded device-side wait ran out */
+    RB_ESTATE = -7         /* inconsistent device state */
+} rb_status;
+
+/* Sweep arithmetic of the FP64 form. */
+enum {
+    RB_SWEEP_DF32 = 0,  /* FP64-accurate double-float products on the FP32 pipe over a hi/lo copy of S */
+    RB_SWEEP_FP64 = 1   /* plain FP64 (DFMA) products read straight from complex128 S */
+};
+
+/* rb_options.flags */
+#define RB_FLAG_TIMING 1u   /* time every sweep launch with CUDA events (fills rb_result.ms_sweep) */
+
+typedef struct rb_options {
+    int device;            /* CUDA device ordinal */
+    int sweep;             /* RB_SWEEP_DF32 (default) or RB_SWEEP_FP64 */
+    double imgs_kappa;     /* MGSCI kappa, > 1 (default 2.0) */
+    int imgs_max_passes;   /* cap on IMGS passes per vector, >= 1 (default 4) */
+    double switch_err;     /* split form: sweeps read hi+lo once max err < switch_err (default 1e-6) */
+    int iters_per_sync;    /* iterations queued between host checks of the stop flag (default 8) */
+    void *stream;          /* cudaStream_t; NULL = the context creates its own stream */
+    unsigned flags;        /* RB_FLAG_* */
+} rb_options;
+
+/* Fills *opt with the defaults listed above. */
+void rb_default_options(rb_options *opt);
+
+typedef struct rb_result {
+    /* ---- outputs: caller-allocated device buffers ---- */
+    void *Q;               /* complex128 N x kmax, column-major, ldQ >= N (required) */
+    long long ldQ;
+    long long *pivots;     /* kmax entries: 0-based column indices in pick order (required) */
+    double *err_curve;     /* kmax+1 entries: err_curve[l] = max err over unpicked columns after l
+                              vectors; err_curve[0] = max_j ||s_j||^2; err_curve[l] = R(l+1,l+1)^2
+                              (Cor. 5.4) (required) */
+    void *C;               /* optional complex128 kmax x M row-major, ldC >= M: C = Q^H S */
+    long long ldC;
+    double *final_err;     /* optional, M entries: err_j after the last vector */
+    double *rdiag;         /* optional, kmax entries: R(l,l) = ||v|| before normalisation */
+    /* ---- filled by the call (host scalars) ---- */
+    int k;                 /* number of basis vectors built */
+    int imgs_passes;       /* total IMGS passes over all vectors */
+    int switch_iter;       /* split form: first iteration that read hi+lo (-1 = never) */
+    int n_launches;        /* kernels this call launched */
+    int n_sweeps;          /* sweep launches that did work */
+    double ms_total;       /* CUDA-event time of the call on its stream */
+    double ms_sweep;       /* summed CUDA-event time of the sweep launches (RB_FLAG_TIMING) */
+    double sweep_bytes;    /* algorithmic bytes read and written by those sweeps */
+} rb_result;
+
+/* Creates a context on opt->device (NULL opt = defaults).  The context owns
+ * its device workspace and, when opt->stream is NULL, a stream.
+ * Errors: RB_EINVAL (bad option), RB_ECUDA. */
+rb_status rb_create(const rb_options *opt, rb_ctx **out);
+
+/* Releases the context's workspace and stream.  NULL is a no-op. */
+void rb_destroy(rb_ctx *ctx);
+
+/* Text of the last error on this context (never NULL). */
+const char *rb_last_error(const rb_ctx *ctx);
+
+/* Seeded synthetic snapshots (a stand-in for the paper's waveform model,
+ * Sec. 6.1.1): for j < M, i < N, with t_i = i/N, t_c = 1.05,
+ *   s_j(t_i) = (t_c - t_i)^(-1/4) exp(-i omega_j (t_c - t_i)^(5/8)),
+ *   omega_j = 200 eta_j^(-3/8) m_j^(-5/8), eta_j = q_j/(1+q_j)^2,
+ * each column then divided by its 2-norm.  q, m: device doubles, M entries
+ * (the random draws are the caller's).  S: device complex128, ldS >= N.
+ * Errors: RB_EINVAL, RB_ECUDA. */
+rb_status rb_generate(rb_ctx *ctx, const double *q, const double *m, long long N, long long M,
+                      void *S, long long ldS);
+
+/* hi/lo split storage of the split-precision form: per real component
+ * hi = fl32(x) and lo = fl32(x - hi), both rounded to nearest, so that
+ * |x - hi - lo| <= 2^-48 |x| for x in the normal FP32 range.  S: complex128
+ * (ldS >= N); hi, lo: complex64 with leading dimension ldH >= N.
+ * Errors: RB_EINVAL, RB_ECUDA. */
+rb_status rb_split(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS,
+                   void *hi, void *lo, long long ldH);
+
+/* RB-greedy (Alg. 3) on complex128 S in the FP64 form: FP64 bookkeeping of
+ * Eq. (Residual), FP64 IMGS, FP64-accurate sweep products (see
+ * rb_options.sweep).  Builds k <= kmax basis vectors; fills out->Q, pivots,
+ * err_curve (k+1 entries used), C (k rows), final_err, rdiag and the host
+ * scalars.  Returns RB_OK, RB_KMAX_REACHED, or an error (RB_EINVAL,
+ * RB_ENOMEM, RB_ECUDA, RB_ENONFINITE, RB_EORTHO, RB_ETIMEOUT). */
+rb_status rb_greedy(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS,
+                    double tol, int kmax, rb_result *out);
+
+/* Same as rb_greedy, but S, every output array of *out, and the result are in
+ * HOST memory (pinned or pageable).  The call copies S to the device and the
+ * outputs back inside the call; device workspace is owned by the context. */
+rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS,
+                         double tol, int kmax, rb_result *out);
+
+/* Projection onto a basis: C[l*ldC + j] = q_l^H x_j for l < k, j < Mx
+ * (Sec. 2: a column is represented by its orthogonal projection onto the
+ * span of the basis).  Q: complex128 N x k (ldQ >= N); X: complex128 N x Mx
+ * (ldX >= N); C: complex128 row-major k x Mx (ldC >= Mx).  FP64-accurate.
+ * Errors: RB_EINVAL, RB_ECUDA. */
+rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ,
+                     const void *X, long long Mx, long long ldX, void *C, long long ldC);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RB_GB300_H */

@@ -1,0 +1,424 @@
+// rb_api.cu -- host runtime behind the C ABI of include/rb.h: context,
+// device workspace, argument checks and the device-driven greedy loop.
+//
+// The loop never waits on the device per iteration: it queues
+// iters_per_sync iterations (IMGS launches + one sweep each), then reads the
+// 100-byte device state once.  Kernels queued after the stop flag was set
+// return immediately.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rb_internal.cuh"
+
+struct rb_ctx {
+    int device = 0;
+    int sms = 152;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    rb_options opt{};
+    char err[512] = {0};
+    void *ws = nullptr;          // main workspace (split copy + vectors)
+    size_t ws_cap = 0;
+    void *stage = nullptr;       // device staging for rb_greedy_host
+    size_t stage_cap = 0;
+    void *gen = nullptr;         // rb_generate tables
+    size_t gen_cap = 0;
+    rbk::DevState *st_host = nullptr;  // pinned copy of the device state
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> sweep_ev;
+    int grid_cache[2] = {0, 0};
+};
+
+namespace {
+
+rb_status fail(rb_ctx *c, rb_status s, const char *fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+rb_status cuda_fail(rb_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, RB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define RB_CK(call, what)                                  \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    size_t off = 0;
+    size_t add(size_t bytes) {
+        size_t o = align_up(off, 512);
+        off = o + bytes;
+        return o;
+    }
+};
+
+rb_status ensure(rb_ctx *ctx, void **buf, size_t *cap, size_t need) {
+    if (*cap >= need && *buf) return RB_OK;
+    if (*buf) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return fail(ctx, RB_ENOMEM, "cudaMalloc of %zu bytes failed: %s", need, cudaGetErrorString(e));
+    }
+    *cap = need;
+    return RB_OK;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int grid_for_variant(rb_ctx *ctx, int variant) {
+    if (!ctx->grid_cache[variant]) ctx->grid_cache[variant] = rbk::sweep_grid(variant, ctx->device);
+    return ctx->grid_cache[variant];
+}
+
+}  // namespace
+
+extern "C" {
+
+void rb_default_options(rb_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->device = 0;
+    opt->sweep = RB_SWEEP_DF32;
+    opt->imgs_kappa = 2.0;
+    opt->imgs_max_passes = 4;
+    opt->switch_err = 1e-6;
+    opt->iters_per_sync = 8;
+    opt->stream = nullptr;
+    opt->flags = 0;
+}
+
+rb_status rb_create(const rb_options *opt, rb_ctx **out) {
+    if (!out) return RB_EINVAL;
+    *out = nullptr;
+    rb_options o;
+    if (opt)
+        o = *opt;
+    else
+        rb_default_options(&o);
+    if (!(o.imgs_kappa > 1.0) || o.imgs_max_passes < 1 || o.iters_per_sync < 1 ||
+        (o.sweep != RB_SWEEP_DF32 && o.sweep != RB_SWEEP_FP64) || !(o.switch_err > 0.0))
+        return RB_EINVAL;
+    rb_ctx *ctx = new (std::nothrow) rb_ctx();
+    if (!ctx) return RB_ENOMEM;
+    ctx->opt = o;
+    ctx->device = o.device;
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, o.device);
+    if (e == cudaSuccess) {
+        if (o.stream) {
+            ctx->stream = (cudaStream_t)o.stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            ctx->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->st_host, sizeof(rbk::DevState));
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rb_destroy(ctx);
+        return RB_ECUDA;
+    }
+    *out = ctx;
+    return RB_OK;
+}
+
+void rb_destroy(rb_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t ev : ctx->sweep_ev) cudaEventDestroy(ev);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->gen) cudaFree(ctx->gen);
+    if (ctx->st_host) cudaFreeHost(ctx->st_host);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *rb_last_error(const rb_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+rb_status rb_generate(rb_ctx *ctx, const double *q, const double *m, long long N, long long M, void *S,
+                      long long ldS) {
+    if (!ctx) return RB_EINVAL;
+    if (N < 1 || M < 1 || ldS < N || !q || !m || !S || !aligned(S, 16))
+        return fail(ctx, RB_EINVAL, "rb_generate: bad arguments (N=%lld M=%lld ldS=%lld)", N, M, ldS);
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    rb_status s = ensure(ctx, &ctx->gen, &ctx->gen_cap, (size_t)N * 2 * sizeof(double));
+    if (s != RB_OK) return s;
+    double *amp = (double *)ctx->gen, *ph = amp + N;
+    RB_CK(rbk::launch_generate_tables(amp, ph, N, ctx->stream), "generate tables");
+    RB_CK(rbk::launch_generate(q, m, amp, ph, N, M, (double2 *)S, ldS, ctx->stream), "generate");
+    return RB_OK;
+}
+
+rb_status rb_split(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, void *hi, void *lo,
+                   long long ldH) {
+    if (!ctx) return RB_EINVAL;
+    if (N < 1 || M < 1 || ldS < N || ldH < N || !S || !hi || !lo || !aligned(S, 16) || !aligned(hi, 8) ||
+        !aligned(lo, 8))
+        return fail(ctx, RB_EINVAL, "rb_split: bad arguments (N=%lld M=%lld ldS=%lld ldH=%lld)", N, M, ldS, ldH);
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    RB_CK(rbk::launch_split((const double2 *)S, N, M, ldS, (float2 *)hi, (float2 *)lo, ldH, nullptr, ctx->stream),
+          "split");
+    return RB_OK;
+}
+
+rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ, const void *X, long long Mx,
+                     long long ldX, void *C, long long ldC) {
+    if (!ctx) return RB_EINVAL;
+    if (N < 1 || k < 0 || Mx < 0 || ldQ < N || ldX < N || ldC < Mx || (k > 0 && (!Q || !X || !C)) ||
+        !aligned(Q, 16) || !aligned(X, 16) || !aligned(C, 16))
+        return fail(ctx, RB_EINVAL, "rb_project: bad arguments (N=%lld k=%d Mx=%lld)", N, k, Mx);
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    RB_CK(rbk::launch_project((const double2 *)Q, N, k, ldQ, (const double2 *)X, Mx, ldX, (double2 *)C, ldC,
+                              ctx->stream),
+          "project");
+    return RB_OK;
+}
+
+static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol,
+                               int kmax, rb_result *out) {
+    const rb_options &o = ctx->opt;
+    const int variant = o.sweep;
+    const bool df = (variant == RB_SWEEP_DF32);
+    const int G = grid_for_variant(ctx, variant);
+    const long long ldH = (long long)align_up((size_t)N, 64);
+    const int chunk = 2048;
+    const int nchunk = (int)((N + chunk - 1) / chunk);
+    const int gN = (int)((N + rbk::kThreads - 1) / rbk::kThreads);
+    const int kcap = kmax > 0 ? kmax : 1;
+
+    Layout L;
+    size_t o_hi = 0, o_lo = 0;
+    if (df) {
+        o_hi = L.add((size_t)M * ldH * sizeof(float2));
+        o_lo = L.add((size_t)M * ldH * sizeof(float2));
+    }
+    size_t o_norm = L.add((size_t)M * 8), o_acc = L.add((size_t)M * 8), o_pick = L.add((size_t)M);
+    size_t o_qh = L.add((size_t)(N + 2) * sizeof(float2)), o_ql = L.add((size_t)(N + 2) * sizeof(float2));
+    size_t o_v = L.add((size_t)N * sizeof(double2));
+    size_t o_hp = L.add((size_t)kcap * nchunk * sizeof(double2));
+    size_t np = (size_t)(G > gN ? G : gN);
+    size_t o_np = L.add(np * 8), o_be = L.add((size_t)G * 8), o_bi = L.add((size_t)G * 8);
+    size_t o_st = L.add(sizeof(rbk::DevState));
+    rb_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.off);
+    if (s != RB_OK) return s;
+    char *w = (char *)ctx->ws;
+
+    rbk::Prob p{};
+    p.N = N;
+    p.M = M;
+    p.ldS = ldS;
+    p.ldH = ldH;
+    p.ldQ = out->ldQ;
+    p.ldC = out->ldC;
+    p.minNM = N < M ? N : M;
+    p.kmax = kmax;
+    p.max_passes = o.imgs_max_passes;
+    p.nchunk = nchunk;
+    p.chunk = chunk;
+    p.tol = tol;
+    p.kappa2 = o.imgs_kappa * o.imgs_kappa;
+    p.S = (const double2 *)S;
+    p.hi = df ? (const float2 *)(w + o_hi) : nullptr;
+    p.lo = df ? (const float2 *)(w + o_lo) : nullptr;
+    p.Q = (double2 *)out->Q;
+    p.pivots = out->pivots;
+    p.err_curve = out->err_curve;
+    p.C = (double2 *)out->C;
+    p.rdiag = out->rdiag;
+    p.norm2 = (double *)(w + o_norm);
+    p.acc = (double *)(w + o_acc);
+    p.picked = (unsigned char *)(w + o_pick);
+    p.qh = df ? (float2 *)(w + o_qh) : nullptr;
+    p.ql = df ? (float2 *)(w + o_ql) : nullptr;
+    p.v = (double2 *)(w + o_v);
+    p.hpart = (double2 *)(w + o_hp);
+    p.npart = (double *)(w + o_np);
+    p.bpart_err = (double *)(w + o_be);
+    p.bpart_idx = (long long *)(w + o_bi);
+    p.st = (rbk::DevState *)(w + o_st);
+
+    cudaStream_t sm = ctx->stream;
+    const bool timing = (o.flags & RB_FLAG_TIMING) != 0;
+    if (timing && (int)ctx->sweep_ev.size() < 2 * kcap) {
+        while ((int)ctx->sweep_ev.size() < 2 * kcap) {
+            cudaEvent_t ev;
+            RB_CK(cudaEventCreate(&ev), "cudaEventCreate");
+            ctx->sweep_ev.push_back(ev);
+        }
+    }
+    int nlaunch = 0;
+    RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
+    RB_CK(cudaMemsetAsync(p.st, 0, sizeof(rbk::DevState), sm), "memset state");
+    if (df)
+        RB_CK(rbk::launch_split(p.S, N, M, ldS, (float2 *)p.hi, (float2 *)p.lo, ldH, p.norm2, sm), "split");
+    else
+        RB_CK(rbk::launch_norms(p.S, N, M, ldS, p.norm2, sm), "norms");
+    RB_CK(rbk::launch_init(p, G, sm), "init");
+    nlaunch += 2;
+
+    int it = 0;
+    bool stopped = false;
+    while (!stopped) {
+        for (int t = 0; t < o.iters_per_sync && it < kcap; t++, it++) {
+            RB_CK(rbk::launch_imgs(p, G, false, sm, &nlaunch), "imgs");
+            if (timing) RB_CK(cudaEventRecord(ctx->sweep_ev[2 * it], sm), "cudaEventRecord");
+            RB_CK(rbk::launch_sweep(p, variant, G, sm), "sweep");
+            if (timing) RB_CK(cudaEventRecord(ctx->sweep_ev[2 * it + 1], sm), "cudaEventRecord");
+            nlaunch += 1;
+        }
+        RB_CK(cudaMemcpyAsync(ctx->st_host, p.st, sizeof(rbk::DevState), cudaMemcpyDeviceToHost, sm), "state copy");
+        RB_CK(cudaStreamSynchronize(sm), "stream sync");
+        stopped = ctx->st_host->stop != 0;
+        if (!stopped && it >= kcap) return fail(ctx, RB_ESTATE, "greedy loop did not stop after kmax iterations");
+    }
+    if (out->final_err) {
+        RB_CK(rbk::launch_final_err(p, out->final_err, sm), "final_err");
+        nlaunch += 1;
+    }
+    RB_CK(cudaEventRecord(ctx->ev1, sm), "cudaEventRecord");
+    RB_CK(cudaEventSynchronize(ctx->ev1), "cudaEventSynchronize");
+    const rbk::DevState &hs = *ctx->st_host;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    out->k = hs.k;
+    out->imgs_passes = hs.total_passes;
+    out->switch_iter = -1;
+    out->n_launches = nlaunch;
+    out->n_sweeps = hs.n_sweeps;
+    out->ms_total = ms;
+    out->ms_sweep = 0.0;
+    if (timing) {
+        for (int i = 0; i < hs.n_sweeps && i < it; i++) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ctx->sweep_ev[2 * i], ctx->sweep_ev[2 * i + 1]);
+            out->ms_sweep += t;
+        }
+    }
+    // algorithmic bytes of one sweep: S (16 N M: complex128, or hi+lo complex64),
+    // q (16 N), norm2 + acc reads (16 M), picked (M), C row + acc writes (24 M)
+    out->sweep_bytes = (double)hs.n_sweeps * (16.0 * N * M + 16.0 * N + 41.0 * M);
+    if (hs.status < 0) {
+        const char *why = hs.status == RB_ENONFINITE ? "NaN or Inf in S"
+                          : hs.status == RB_EORTHO   ? "IMGS did not pass the kappa test within imgs_max_passes"
+                                                     : "device error";
+        return fail(ctx, (rb_status)hs.status, "rb_greedy: %s", why);
+    }
+    return (rb_status)hs.status;
+}
+
+static rb_status check_greedy_args(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol,
+                                   int kmax, const rb_result *out) {
+    if (!ctx) return RB_EINVAL;
+    if (!out || !S) return fail(ctx, RB_EINVAL, "null S or result");
+    if (N < 1 || M < 1 || ldS < N) return fail(ctx, RB_EINVAL, "bad sizes N=%lld M=%lld ldS=%lld", N, M, ldS);
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(ctx, RB_EINVAL, "tol must be finite and >= 0");
+    if (kmax < 0) return fail(ctx, RB_EINVAL, "kmax must be >= 0");
+    if (!out->Q || !out->pivots || !out->err_curve) return fail(ctx, RB_EINVAL, "Q, pivots, err_curve are required");
+    if (out->ldQ < N) return fail(ctx, RB_EINVAL, "ldQ < N");
+    if (out->C && out->ldC < M) return fail(ctx, RB_EINVAL, "ldC < M");
+    return RB_OK;
+}
+
+rb_status rb_greedy(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol, int kmax,
+                    rb_result *out) {
+    rb_status s = check_greedy_args(ctx, S, N, M, ldS, tol, kmax, out);
+    if (s != RB_OK) return s;
+    if (!aligned(S, 16) || !aligned(out->Q, 16) || (out->C && !aligned(out->C, 16)))
+        return fail(ctx, RB_EINVAL, "complex128 arrays must be 16-byte aligned");
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    return greedy_device(ctx, S, N, M, ldS, tol, kmax, out);
+}
+
+rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol, int kmax,
+                         rb_result *out) {
+    rb_status s = check_greedy_args(ctx, S, N, M, ldS, tol, kmax, out);
+    if (s != RB_OK) return s;
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int kcap = kmax > 0 ? kmax : 1;
+    Layout L;
+    size_t o_S = L.add((size_t)M * N * 16), o_Q = L.add((size_t)kcap * N * 16), o_p = L.add((size_t)kcap * 8);
+    size_t o_e = L.add((size_t)(kcap + 1) * 8);
+    size_t o_C = out->C ? L.add((size_t)kcap * M * 16) : 0;
+    size_t o_f = out->final_err ? L.add((size_t)M * 8) : 0;
+    size_t o_r = out->rdiag ? L.add((size_t)kcap * 8) : 0;
+    s = ensure(ctx, &ctx->stage, &ctx->stage_cap, L.off);
+    if (s != RB_OK) return s;
+    char *w = (char *)ctx->stage;
+    cudaStream_t sm = ctx->stream;
+    RB_CK(cudaMemcpy2DAsync(w + o_S, (size_t)N * 16, S, (size_t)ldS * 16, (size_t)N * 16, (size_t)M,
+                            cudaMemcpyHostToDevice, sm),
+          "copy S to device");
+    rb_result d = *out;
+    d.Q = w + o_Q;
+    d.ldQ = N;
+    d.pivots = (long long *)(w + o_p);
+    d.err_curve = (double *)(w + o_e);
+    d.C = out->C ? (void *)(w + o_C) : nullptr;
+    d.ldC = M;
+    d.final_err = out->final_err ? (double *)(w + o_f) : nullptr;
+    d.rdiag = out->rdiag ? (double *)(w + o_r) : nullptr;
+    rb_status st = greedy_device(ctx, w + o_S, N, M, N, tol, kmax, &d);
+    if (st < 0) return st;
+    const int k = d.k;
+    if (k > 0) {
+        RB_CK(cudaMemcpy2DAsync(out->Q, (size_t)out->ldQ * 16, d.Q, (size_t)N * 16, (size_t)N * 16, (size_t)k,
+                                cudaMemcpyDeviceToHost, sm),
+              "copy Q");
+        RB_CK(cudaMemcpyAsync(out->pivots, d.pivots, (size_t)k * 8, cudaMemcpyDeviceToHost, sm), "copy pivots");
+        if (out->C)
+            RB_CK(cudaMemcpy2DAsync(out->C, (size_t)out->ldC * 16, d.C, (size_t)M * 16, (size_t)M * 16, (size_t)k,
+                                    cudaMemcpyDeviceToHost, sm),
+                  "copy C");
+        if (out->rdiag)
+            RB_CK(cudaMemcpyAsync(out->rdiag, d.rdiag, (size_t)k * 8, cudaMemcpyDeviceToHost, sm), "copy rdiag");
+    }
+    RB_CK(cudaMemcpyAsync(out->err_curve, d.err_curve, (size_t)(k + 1) * 8, cudaMemcpyDeviceToHost, sm),
+          "copy err_curve");
+    if (out->final_err)
+        RB_CK(cudaMemcpyAsync(out->final_err, d.final_err, (size_t)M * 8, cudaMemcpyDeviceToHost, sm),
+              "copy final_err");
+    RB_CK(cudaStreamSynchronize(sm), "stream sync");
+    void *keepQ = out->Q, *keepC = out->C;
+    long long *keepP = out->pivots;
+    double *keepE = out->err_curve, *keepF = out->final_err, *keepR = out->rdiag;
+    long long kldQ = out->ldQ, kldC = out->ldC;
+    *out = d;
+    out->Q = keepQ;
+    out->C = keepC;
+    out->pivots = keepP;
+    out->err_curve = keepE;
+    out->final_err = keepF;
+    out->rdiag = keepR;
+    out->ldQ = kldQ;
+    out->ldC = kldC;
+    return st;
+}
+
+}  // extern "C"

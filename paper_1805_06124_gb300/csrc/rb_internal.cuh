@@ -1,0 +1,226 @@
+// rb_internal.cuh -- shared device-side definitions of the CUDA path.
+//
+// Every kernel of the greedy loop reads and writes one small DevState in
+// device memory, so an iteration can be queued (or replayed) without the host
+// knowing k, the pivot or whether the loop has already stopped: each kernel
+// returns at once when `stop` is set.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rb.h"
+
+namespace rbk {
+
+constexpr int kThreads = 256;
+constexpr long long kNoIdx = 0x7fffffffffffffffLL;
+
+struct DevState {
+    int k;             // basis vectors appended so far
+    int stop;          // 1 once the greedy loop has ended
+    int status;        // rb_status at stop
+    int accepted;      // IMGS: the current v passed the kappa test
+    int passes;        // IMGS passes in the current iteration
+    int total_passes;  // IMGS passes over the whole call
+    int nonfinite;     // a column norm was NaN/Inf
+    int phase;         // split form: 0 = hi-only sweeps, 1 = hi+lo sweeps
+    int switch_iter;   // split form: first iteration at phase 1 (-1 = never)
+    int n_sweeps;      // sweep launches that did work
+    int ncand;         // split form: candidates in the last recheck
+    int pad0;
+    long long J;       // next pivot column (kNoIdx = none left)
+    double errJ;       // its error
+    double before2;    // IMGS: ||v||^2 before the current pass
+    double after2;     // IMGS: ||v||^2 after the current pass
+    unsigned int ticket_sweep;  // last-block-done counters (reset by the last block)
+    unsigned int ticket_imgs;
+    unsigned int ticket_init;
+    unsigned int ticket_aux;
+};
+
+// Problem description passed by value to every kernel of a greedy call.
+struct Prob {
+    long long N, M;
+    long long ldS, ldH, ldQ, ldC;
+    long long minNM;
+    int kmax;
+    int max_passes;
+    int nchunk;        // IMGS dot-product row chunks
+    int chunk;         // rows per chunk
+    double tol;
+    double kappa2;     // kappa^2 (the kappa test compares squared norms)
+    const double2 *S;  // complex128 snapshots (FP64 form)
+    const float2 *hi;  // split storage
+    const float2 *lo;
+    double2 *Q;
+    long long *pivots;
+    double *err_curve;
+    double2 *C;        // may be null
+    double *rdiag;     // may be null
+    double *norm2;
+    double *acc;
+    unsigned char *picked;
+    float2 *qh;        // current basis vector, rounded to FP32
+    float2 *ql;        // its FP32 remainder
+    double2 *v;        // IMGS work vector
+    double2 *hpart;    // IMGS partial dot products [kmax][nchunk]
+    double *npart;     // per-block partial norms
+    double *bpart_err; // per-block argmax partials
+    long long *bpart_idx;
+    DevState *st;
+};
+
+// ---------------------------------------------------------------- argmax key
+// (err, idx) is better than (err2, idx2) when err is larger, ties to the
+// lower index.
+__device__ __forceinline__ bool better(double e1, long long i1, double e2, long long i2) {
+    return e1 > e2 || (e1 == e2 && i1 < i2);
+}
+
+__device__ __forceinline__ void warp_best(double &e, long long &i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double e2 = __shfl_xor_sync(0xffffffffu, e, o);
+        long long i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (better(e2, i2, e, i)) { e = e2; i = i2; }
+    }
+}
+
+// Block-wide best; the result is valid in thread 0.
+__device__ __forceinline__ void block_best(double &e, long long &i) {
+    __shared__ double se[32];
+    __shared__ long long si[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    warp_best(e, i);
+    __syncthreads();
+    if (lane == 0) { se[w] = e; si[w] = i; }
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        e = lane < nw ? se[lane] : -INFINITY;
+        i = lane < nw ? si[lane] : kNoIdx;
+        warp_best(e, i);
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Block-wide sum in a fixed order; valid in thread 0.
+__device__ __forceinline__ double block_sum(double x) {
+    __shared__ double sx[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    x = warp_sum(x);
+    __syncthreads();
+    if (lane == 0) sx[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        x = lane < nw ? sx[lane] : 0.0;
+        x = warp_sum(x);
+    }
+    return x;
+}
+
+__device__ __forceinline__ double2 block_sum2(double2 x) {
+    double a = block_sum(x.x);
+    double b = block_sum(x.y);
+    return make_double2(a, b);
+}
+
+// Last-block-done ticket: returns true in every thread of the block that
+// arrives last.  Each block must have published its partial (and fenced)
+// before calling.
+__device__ __forceinline__ bool last_block(unsigned int *ticket) {
+    __shared__ int amlast;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        amlast = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (amlast) __threadfence();
+    return amlast != 0;
+}
+
+// --------------------------------------------------------- double-float ops
+// Error-free transformations (Knuth's TwoSum; the FMA form of Dekker's
+// TwoProduct).  The __f*_rn intrinsics keep the compiler from contracting or
+// reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// (sh, sl) += (ah + al) * (bh + bl), dropping al*bl (below 2^-48 relative).
+__device__ __forceinline__ void df_mac(float &sh, float &sl, float ah, float al, float bh, float bl) {
+    float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    float s, t;
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
+// (ah, al) += (bh, bl)
+__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
+    float s, t;
+    two_sum(ah, bh, s, t);
+    t = __fadd_rn(t, __fadd_rn(al, bl));
+    ah = __fadd_rn(s, t);
+    al = __fsub_rn(t, __fsub_rn(ah, s));
+}
+
+__device__ __forceinline__ void warp_df_sum(float &h, float &l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+        float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+        df_add(h, l, h2, l2);
+    }
+}
+
+// Streaming 128-bit load that does not allocate in L1 (S is read once per sweep).
+__device__ __forceinline__ float4 ld_stream(const float4 *p) {
+    float4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ double2 ld_stream_d2(const double2 *p) {
+    double2 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+}  // namespace rbk
+
+// ------------------------------------------------------------- host launchers
+namespace rbk {
+cudaError_t launch_generate_tables(double *amp, double *ph, long long N, cudaStream_t s);
+cudaError_t launch_generate(const double *q, const double *m, const double *amp, const double *ph,
+                            long long N, long long M, double2 *S, long long ldS, cudaStream_t s);
+cudaError_t launch_split(const double2 *S, long long N, long long M, long long ldS, float2 *hi, float2 *lo,
+                         long long ldH, double *norm2, cudaStream_t s);
+cudaError_t launch_norms(const double2 *S, long long N, long long M, long long ldS, double *norm2,
+                         cudaStream_t s);
+cudaError_t launch_init(const Prob &p, int grid, cudaStream_t s);
+cudaError_t launch_sweep(const Prob &p, int variant, int grid, cudaStream_t s);
+cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s, int *nlaunch);
+cudaError_t launch_final_err(const Prob &p, double *final_err, cudaStream_t s);
+cudaError_t launch_project(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mx,
+                           long long ldX, double2 *C, long long ldC, cudaStream_t s);
+int sweep_grid(int variant, int device);
+}  // namespace rbk

@@ -1,0 +1,180 @@
+// rb_sweep.cu -- the fused pivot-search sweep of RB-greedy (Alg. 3 with the
+// bookkeeping of Eq. (Residual), Sec. 6.1.2).
+//
+// One launch streams all of S once: for every column j it forms
+// c_kj = q_k^H s_j, stores C[k, j], updates acc_j += |c_kj|^2 in FP64,
+// err_j = ||s_j||^2 - acc_j, and folds (err_j, j) into a warp -> block ->
+// grid argmax over unpicked columns (ties to the lowest index).  The last
+// block to finish reduces the per-block partials, appends err_curve[k+1],
+// publishes the next pivot and applies the stopping rule.
+//
+// Work split: one warp owns a whole column at a time (lanes stride over
+// rows with 128-bit loads, warp-shuffle reduction at the end), so no
+// shared-memory traffic or __syncthreads sits inside the streaming loop.
+#include "rb_internal.cuh"
+
+namespace rbk {
+
+enum { SWEEP_DF32 = 0, SWEEP_FP64 = 1 };
+
+// Double-float product of a conjugated basis element (hi + lo parts) with a
+// snapshot element (hi + lo parts), accumulated into (re_h, re_l), (im_h, im_l):
+//   Re += qr*sr + qi*si,  Im += qr*si - qi*sr.
+__device__ __forceinline__ void df_cmac(float &rh, float &rl, float &ih, float &il, float qrh, float qih, float qrl,
+                                        float qil, float srh, float sih, float srl, float sil) {
+    df_mac(rh, rl, qrh, qrl, srh, srl);
+    df_mac(rh, rl, qih, qil, sih, sil);
+    df_mac(ih, il, qrh, qrl, sih, sil);
+    df_mac(ih, il, -qih, -qil, srh, srl);
+}
+
+// Column dot product c = q^H s_j over the hi/lo split storage (double-float).
+__device__ __forceinline__ double2 col_dot_df32(const float2 *__restrict__ hcol, const float2 *__restrict__ lcol,
+                                                const float2 *__restrict__ qh, const float2 *__restrict__ ql,
+                                                long long N, int lane) {
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const float4 *h4 = reinterpret_cast<const float4 *>(hcol);
+    const float4 *l4 = reinterpret_cast<const float4 *>(lcol);
+    const float4 *qh4 = reinterpret_cast<const float4 *>(qh);
+    const float4 *ql4 = reinterpret_cast<const float4 *>(ql);
+    long long n2 = N >> 1;  // complex pairs
+    long long t = lane;
+    constexpr int U = 4;
+    for (; t + 32 * (U - 1) < n2; t += 32 * U) {
+        float4 a[U], b[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            a[u] = ld_stream(h4 + t + 32 * u);
+            b[u] = ld_stream(l4 + t + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            float4 qa = __ldg(qh4 + t + 32 * u);
+            float4 qb = __ldg(ql4 + t + 32 * u);
+            df_cmac(rh, rl, ih, il, qa.x, qa.y, qb.x, qb.y, a[u].x, a[u].y, b[u].x, b[u].y);
+            df_cmac(rh, rl, ih, il, qa.z, qa.w, qb.z, qb.w, a[u].z, a[u].w, b[u].z, b[u].w);
+        }
+    }
+    for (; t < n2; t += 32) {
+        float4 a = ld_stream(h4 + t), b = ld_stream(l4 + t);
+        float4 qa = __ldg(qh4 + t), qb = __ldg(ql4 + t);
+        df_cmac(rh, rl, ih, il, qa.x, qa.y, qb.x, qb.y, a.x, a.y, b.x, b.y);
+        df_cmac(rh, rl, ih, il, qa.z, qa.w, qb.z, qb.w, a.z, a.w, b.z, b.w);
+    }
+    if ((N & 1) && lane == 0) {
+        long long i = N - 1;
+        float2 a = hcol[i], b = lcol[i], qa = qh[i], qb = ql[i];
+        df_cmac(rh, rl, ih, il, qa.x, qa.y, qb.x, qb.y, a.x, a.y, b.x, b.y);
+    }
+    warp_df_sum(rh, rl);
+    warp_df_sum(ih, il);
+    return make_double2((double)rh + (double)rl, (double)ih + (double)il);
+}
+
+// Column dot product c = q^H s_j in plain FP64 straight from complex128.
+__device__ __forceinline__ double2 col_dot_fp64(const double2 *__restrict__ s, const double2 *__restrict__ q,
+                                                long long N, int lane) {
+    double re = 0.0, im = 0.0;
+    long long i = lane;
+    constexpr int U = 4;
+    for (; i + 32 * (U - 1) < N; i += 32 * U) {
+        double2 a[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) a[u] = ld_stream_d2(s + i + 32 * u);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            double2 b = __ldg(q + i + 32 * u);
+            re = fma(b.x, a[u].x, fma(b.y, a[u].y, re));
+            im = fma(b.x, a[u].y, fma(-b.y, a[u].x, im));
+        }
+    }
+    for (; i < N; i += 32) {
+        double2 a = ld_stream_d2(s + i), b = __ldg(q + i);
+        re = fma(b.x, a.x, fma(b.y, a.y, re));
+        im = fma(b.x, a.y, fma(-b.y, a.x, im));
+    }
+    return make_double2(warp_sum(re), warp_sum(im));
+}
+
+template <int VARIANT>
+__global__ void __launch_bounds__(kThreads) k_sweep(Prob p) {
+    DevState *st = p.st;
+    if (ld_volatile(&st->stop)) return;
+    const int k = st->k;  // row of C written by this sweep; q_k is the newest vector
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    double be = -INFINITY;
+    long long bi = kNoIdx;
+    const double2 *qk = p.Q + (long long)k * p.ldQ;
+    for (long long j = gw; j < p.M; j += nw) {
+        double2 c;
+        if (VARIANT == SWEEP_DF32)
+            c = col_dot_df32(p.hi + j * p.ldH, p.lo + j * p.ldH, p.qh, p.ql, p.N, lane);
+        else
+            c = col_dot_fp64(p.S + j * p.ldS, qk, p.N, lane);
+        if (lane == 0) {
+            if (p.C) p.C[(long long)k * p.ldC + j] = c;
+            double a = p.acc[j] + (c.x * c.x + c.y * c.y);
+            p.acc[j] = a;
+            double e = p.norm2[j] - a;
+            if (!p.picked[j] && better(e, j, be, bi)) { be = e; bi = j; }
+        }
+    }
+    block_best(be, bi);
+    if (threadIdx.x == 0) {
+        p.bpart_err[blockIdx.x] = be;
+        p.bpart_idx[blockIdx.x] = bi;
+    }
+    if (!last_block(&st->ticket_sweep)) return;
+    be = -INFINITY;
+    bi = kNoIdx;
+    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        double e = __ldcg(p.bpart_err + b);
+        long long i = __ldcg(p.bpart_idx + b);
+        if (better(e, i, be, bi)) { be = e; bi = i; }
+    }
+    block_best(be, bi);
+    if (threadIdx.x == 0) {
+        st->ticket_sweep = 0;
+        int k1 = k + 1;
+        st->k = k1;
+        st->n_sweeps += 1;
+        double emax = bi == kNoIdx ? 0.0 : be;
+        p.err_curve[k1] = emax;
+        st->J = bi;
+        st->errJ = emax;
+        // Stopping rule (Alg. 3 while-test on the squared error, Cor. 5.4).
+        if (bi == kNoIdx || emax < p.tol) {
+            st->status = RB_OK;
+            st->stop = 1;
+        } else if (k1 >= p.kmax) {
+            st->status = RB_KMAX_REACHED;
+            st->stop = 1;
+        } else if (k1 >= p.minNM) {
+            st->status = RB_OK;
+            st->stop = 1;
+        }
+    }
+}
+
+int sweep_grid(int variant, int device) {
+    int sms = 152, per = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (variant == SWEEP_DF32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<SWEEP_DF32>, kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<SWEEP_FP64>, kThreads, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_sweep(const Prob &p, int variant, int grid, cudaStream_t s) {
+    if (variant == SWEEP_DF32)
+        k_sweep<SWEEP_DF32><<<grid, kThreads, 0, s>>>(p);
+    else
+        k_sweep<SWEEP_FP64><<<grid, kThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace rbk

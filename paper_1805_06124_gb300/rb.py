@@ -1,0 +1,258 @@
+"""Thin ctypes binding of the C ABI in ``include/rb.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``_build/librb_gb300.so``.  PyTorch supplies device memory and the
+stream.  There is no CPU fallback: if the library is missing or no GPU is
+present, the calls raise.
+
+Python-side layouts (all C-contiguous torch tensors on the GPU):
+  S      complex128 (M, N)    row j = snapshot s_j (the paper's column j)
+  Q      complex128 (kmax, N) row l = basis vector q_l
+  C      complex128 (kmax, M) C[l, j] = q_l^H s_j
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int, c_double, c_ll, c_void_p, c_uint = ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_uint
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_ll_p = ctypes.POINTER(ctypes.c_longlong)
+
+OK, KMAX_REACHED = 0, 1
+EINVAL, ENOMEM, ECUDA, ENONFINITE, EORTHO, ETIMEOUT, ESTATE = -1, -2, -3, -4, -5, -6, -7
+SWEEP = {"df32": 0, "fp64": 1}
+FLAG_TIMING = 1
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("device", c_int), ("sweep", c_int), ("imgs_kappa", c_double), ("imgs_max_passes", c_int),
+                ("switch_err", c_double), ("iters_per_sync", c_int), ("stream", c_void_p), ("flags", c_uint)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("Q", c_void_p), ("ldQ", c_ll), ("pivots", c_ll_p), ("err_curve", c_double_p),
+                ("C", c_void_p), ("ldC", c_ll), ("final_err", c_double_p), ("rdiag", c_double_p),
+                ("k", c_int), ("imgs_passes", c_int), ("switch_iter", c_int), ("n_launches", c_int),
+                ("n_sweeps", c_int), ("ms_total", c_double), ("ms_sweep", c_double), ("sweep_bytes", c_double)]
+
+
+class RBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rb status {status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load the CUDA library (building it first when asked)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    lib.rb_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.rb_default_options.restype = None
+    lib.rb_create.argtypes = [ctypes.POINTER(Options), ctypes.POINTER(c_void_p)]
+    lib.rb_create.restype = c_int
+    lib.rb_destroy.argtypes = [c_void_p]
+    lib.rb_destroy.restype = None
+    lib.rb_last_error.argtypes = [c_void_p]
+    lib.rb_last_error.restype = ctypes.c_char_p
+    lib.rb_generate.argtypes = [c_void_p, c_void_p, c_void_p, c_ll, c_ll, c_void_p, c_ll]
+    lib.rb_split.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_void_p, c_void_p, c_ll]
+    lib.rb_greedy.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int, ctypes.POINTER(Result)]
+    lib.rb_greedy_host.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int, ctypes.POINTER(Result)]
+    lib.rb_project.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_void_p, c_ll]
+    for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_project"):
+        getattr(lib, f).restype = c_int
+    _LIB = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ld(t) -> int:
+    """Leading dimension (in elements) of a 2-D row-major tensor."""
+    return int(t.stride(0)) if t.shape[0] > 1 else int(t.shape[1])
+
+
+def _check2d(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.dim() != 2 or t.dtype != dtype or t.stride(1) != 1:
+        raise TypeError(f"{name} must be a 2-D {dtype} tensor with unit column stride")
+    if not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+
+
+class RB:
+    """One rb_ctx.  ``stream`` defaults to torch's current stream on ``device``."""
+
+    def __init__(self, device: int = 0, sweep: str = "df32", kappa: float = 2.0, max_passes: int = 4,
+                 switch_err: float = 1e-6, iters_per_sync: int = 8, stream=None, timing: bool = False):
+        torch = _torch()
+        self.lib = load()
+        self.device = device
+        opt = Options()
+        self.lib.rb_default_options(ctypes.byref(opt))
+        opt.device = device
+        opt.sweep = SWEEP[sweep]
+        opt.imgs_kappa = kappa
+        opt.imgs_max_passes = max_passes
+        opt.switch_err = switch_err
+        opt.iters_per_sync = iters_per_sync
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        opt.stream = c_void_p(stream.cuda_stream)
+        opt.flags = FLAG_TIMING if timing else 0
+        h = c_void_p()
+        st = self.lib.rb_create(ctypes.byref(opt), ctypes.byref(h))
+        if st != OK:
+            raise RBError(st, "rb_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.rb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st < 0:
+            raise RBError(st, self.lib.rb_last_error(self._h).decode())
+        return st
+
+    # ---------------------------------------------------------------- calls
+    def generate(self, q, m, N: int, ld: int | None = None):
+        """Chirp snapshots on the GPU from per-column parameters (q, m)."""
+        torch = _torch()
+        q = torch.as_tensor(q, dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
+        m = torch.as_tensor(m, dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
+        M = q.numel()
+        ld = N if ld is None else ld
+        S = torch.empty((M, ld), dtype=torch.complex128, device=q.device)[:, :N]
+        self._check(self.lib.rb_generate(self._h, q.data_ptr(), m.data_ptr(), N, M, S.data_ptr(), ld))
+        return S
+
+    def split(self, S, ldh: int | None = None):
+        torch = _torch()
+        _check2d(S, torch.complex128, "S")
+        M, N = S.shape
+        ldh = N if ldh is None else ldh
+        hi = torch.empty((M, ldh), dtype=torch.complex64, device=S.device)
+        lo = torch.empty((M, ldh), dtype=torch.complex64, device=S.device)
+        self._check(self.lib.rb_split(self._h, S.data_ptr(), N, M, _ld(S), hi.data_ptr(), lo.data_ptr(), ldh))
+        return hi[:, :N], lo[:, :N]
+
+    def _alloc_result(self, N, M, kmax, dev, want_C, want_final):
+        torch = _torch()
+        kc = max(kmax, 1)
+        bufs = dict(Q=torch.zeros((kc, N), dtype=torch.complex128, device=dev),
+                    pivots=torch.full((kc,), -1, dtype=torch.int64, device=dev),
+                    err_curve=torch.zeros((kc + 1,), dtype=torch.float64, device=dev),
+                    rdiag=torch.zeros((kc,), dtype=torch.float64, device=dev))
+        if want_C:
+            bufs["C"] = torch.zeros((kc, M), dtype=torch.complex128, device=dev)
+        if want_final:
+            bufs["final_err"] = torch.zeros((M,), dtype=torch.float64, device=dev)
+        r = Result()
+        r.Q = bufs["Q"].data_ptr()
+        r.ldQ = N
+        r.pivots = ctypes.cast(bufs["pivots"].data_ptr(), c_ll_p)
+        r.err_curve = ctypes.cast(bufs["err_curve"].data_ptr(), c_double_p)
+        r.rdiag = ctypes.cast(bufs["rdiag"].data_ptr(), c_double_p)
+        r.C = bufs["C"].data_ptr() if want_C else None
+        r.ldC = M
+        r.final_err = ctypes.cast(bufs["final_err"].data_ptr(), c_double_p) if want_final else None
+        return r, bufs
+
+    @staticmethod
+    def _pack(st, r, bufs):
+        k = r.k
+        out = dict(status=st, k=k, imgs_passes=r.imgs_passes, switch_iter=r.switch_iter, n_launches=r.n_launches,
+                   n_sweeps=r.n_sweeps, ms_total=r.ms_total, ms_sweep=r.ms_sweep, sweep_bytes=r.sweep_bytes)
+        out["Q"] = bufs["Q"][:k]
+        out["pivots"] = bufs["pivots"][:k]
+        out["err_curve"] = bufs["err_curve"][:k + 1]
+        out["rdiag"] = bufs["rdiag"][:k]
+        if "C" in bufs:
+            out["C"] = bufs["C"][:k]
+        if "final_err" in bufs:
+            out["final_err"] = bufs["final_err"]
+        return out
+
+    def greedy(self, S, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True):
+        """RB-greedy (Alg. 3) on device snapshots S (M, N) complex128."""
+        torch = _torch()
+        _check2d(S, torch.complex128, "S")
+        M, N = S.shape
+        r, bufs = self._alloc_result(N, M, kmax, S.device, want_C, want_final_err)
+        st = self._check(self.lib.rb_greedy(self._h, S.data_ptr(), N, M, _ld(S), float(tol), int(kmax),
+                                            ctypes.byref(r)))
+        return self._pack(st, r, bufs)
+
+    def greedy_host(self, S, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True):
+        """Same as greedy, with S and all outputs in host memory (CPU tensors;
+        pinned memory gives the fastest copies)."""
+        torch = _torch()
+        if S.dim() != 2 or S.dtype != torch.complex128 or S.is_cuda or S.stride(1) != 1:
+            raise TypeError("S must be a 2-D complex128 CPU tensor with unit column stride")
+        M, N = S.shape
+        kc = max(kmax, 1)
+        pin = S.is_pinned()
+        bufs = dict(Q=torch.zeros((kc, N), dtype=torch.complex128, pin_memory=pin),
+                    pivots=torch.full((kc,), -1, dtype=torch.int64, pin_memory=pin),
+                    err_curve=torch.zeros((kc + 1,), dtype=torch.float64, pin_memory=pin),
+                    rdiag=torch.zeros((kc,), dtype=torch.float64, pin_memory=pin))
+        if want_C:
+            bufs["C"] = torch.zeros((kc, M), dtype=torch.complex128, pin_memory=pin)
+        if want_final_err:
+            bufs["final_err"] = torch.zeros((M,), dtype=torch.float64, pin_memory=pin)
+        r = Result()
+        r.Q = bufs["Q"].data_ptr()
+        r.ldQ = N
+        r.pivots = ctypes.cast(bufs["pivots"].data_ptr(), c_ll_p)
+        r.err_curve = ctypes.cast(bufs["err_curve"].data_ptr(), c_double_p)
+        r.rdiag = ctypes.cast(bufs["rdiag"].data_ptr(), c_double_p)
+        r.C = bufs["C"].data_ptr() if want_C else None
+        r.ldC = M
+        r.final_err = ctypes.cast(bufs["final_err"].data_ptr(), c_double_p) if want_final_err else None
+        st = self._check(self.lib.rb_greedy_host(self._h, S.data_ptr(), N, M, _ld(S), float(tol), int(kmax),
+                                                 ctypes.byref(r)))
+        return self._pack(st, r, bufs)
+
+    def project(self, Q, X, k: int | None = None):
+        """C[l, j] = q_l^H x_j for l < k (Q: (k, N), X: (Mx, N), both complex128)."""
+        torch = _torch()
+        _check2d(Q, torch.complex128, "Q")
+        _check2d(X, torch.complex128, "X")
+        k = Q.shape[0] if k is None else k
+        N = Q.shape[1]
+        if X.shape[1] != N:
+            raise ValueError("Q and X disagree on N")
+        Mx = X.shape[0]
+        C = torch.empty((max(k, 1), Mx), dtype=torch.complex128, device=X.device)
+        self._check(self.lib.rb_project(self._h, Q.data_ptr(), N, k, _ld(Q), X.data_ptr(), Mx, _ld(X),
+                                        C.data_ptr(), Mx))
+        return C[:k]

@@ -1,0 +1,66 @@
+"""Parity protocol between the CUDA path and the FP64 oracle.
+
+The CUDA path runs first; its pivots are then replayed in the oracle.  At
+every step the oracle's own argmax must equal the GPU pivot whenever the
+top-two gap exceeds max(1e-12 * err_max, delta_l); otherwise the GPU pivot's
+exact error must lie within that margin of the max.  delta_l is the FP64
+bookkeeping noise of Eq. (Residual): c0 * (l + log2 N) * u * max ||s||^2.
+"""
+import math
+
+import numpy as np
+
+U = 2.0 ** -53
+
+
+def delta(l, N, scale, c0=4.0):
+    return c0 * (l + math.log2(max(N, 2))) * U * scale
+
+
+def replay_and_check(orc, S, gpu, tol, kmax, rel_gap=1e-12):
+    """Returns the replayed oracle result; asserts the pivot protocol."""
+    M, N = S.shape
+    piv = np.asarray(gpu["pivots"])
+    k = len(piv)
+    rep = orc.rb_greedy(S, tol, kmax, forced=piv)
+    assert rep["k"] == k, (rep["k"], k)
+    assert list(rep["pivots"]) == list(piv)
+    scale = rep["err_curve"][0]
+    for l in range(k):
+        emax = rep["own_max"][l]
+        margin = max(rel_gap * emax, delta(l, N, scale))
+        assert emax - rep["forced_err"][l] <= margin, (l, emax, rep["forced_err"][l], margin)
+        if emax - rep["second_max"][l] > margin:
+            assert rep["own_argmax"][l] == piv[l], l
+    return rep
+
+
+def basis_tol(err_curve, k):
+    """Per-vector tolerance: cancellation amplifies rounding by 1/||v||."""
+    d = np.sqrt(np.maximum(np.asarray(err_curve[:k]), 1e-300))
+    return np.maximum(1e-12, 64 * U * math.sqrt(max(k, 1)) / d)
+
+
+def compare(gpu, rep, S, err_atol=1e-12):
+    k = rep["k"]
+    ec_g, ec_r = np.asarray(gpu["err_curve"]), rep["err_curve"]
+    assert np.max(np.abs(ec_g - ec_r)) <= err_atol, np.max(np.abs(ec_g - ec_r))
+    bt = basis_tol(ec_r, k)
+    dq = np.max(np.abs(np.asarray(gpu["Q"]) - rep["Q"]), axis=1) if k else np.zeros(0)
+    assert np.all(dq <= bt), (np.max(dq / bt), int(np.argmax(dq / bt)))
+    if "C" in gpu:
+        dc = np.max(np.abs(np.asarray(gpu["C"]) - rep["C"]), axis=1) if k else np.zeros(0)
+        assert np.all(dc <= bt + 1e-13), np.max(dc / (bt + 1e-13))
+    if "final_err" in gpu:
+        df = np.max(np.abs(np.asarray(gpu["final_err"]) - rep["final_err"]))
+        assert df <= err_atol, df
+    return dict(max_dq_over_tol=float(np.max(dq / bt)) if k else 0.0,
+                max_err_curve_diff=float(np.max(np.abs(ec_g - ec_r))))
+
+
+def first_divergence(a, b):
+    n = min(len(a), len(b))
+    for i in range(n):
+        if a[i] != b[i]:
+            return i
+    return n
