@@ -1,0 +1,284 @@
+"""Benchmark of the greedy reduced-basis sweep on one GB300.
+
+One step = one full RB-greedy call (split + norms, then per iteration IMGS
+and the fused sweep/argmax, until max err < tol) on the FP64 form, over the
+synthetic chirp snapshots N = 8192 x M = 262,144 (complex128, 34.4 GB in
+HBM, larger than L2), tol 1e-12, kmax 800.
+
+value  = algorithmic sweep bytes of all iterations / device time of the
+         whole call (GB/s), i.e. the greedy's effective sweep bandwidth.
+roofline = the sweep kernel alone: its algorithmic bytes per launch over its
+         average CUDA-event duration, against the measured HBM copy peak.
+e2e    = the same metric through rb_greedy_host: S and all outputs in pinned
+         host memory, the host<->device copies inside the timed region.
+cpu_baseline / --impl reference = the FP64 C oracle on a bounded column
+         sample of the same family, timed on this host.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: replicas only (each rank runs its own problem; no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "greedy sweep HBM GB/s (% of peak); time-to-basis at tol 1e-10, split vs FP64"
+N_DEF, M_DEF, SEED, TOL, KMAX = 8192, 262144, 1, 1e-12, 800
+CPU_SAMPLE_M = 24576
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _sweep_traffic_per_byte():
+    """ncu DRAM bytes per algorithmic byte of the sweep kernel, from the
+    committed profile summary, if it was taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1805_06124_gb300", "csrc", "rb_sweep.cu"), "rb").read()
+        if d.get("rb_sweep_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return float(d["dram_bytes_per_algorithmic_byte"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        import statistics
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except Exception:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_run(m_sample: int, steps: int = 1):
+    """Times the FP64 C oracle on an N x m_sample column sample (seed 1)."""
+    from oracle import oracle
+    from paper_1805_06124_gb300 import synth
+    oracle.build()
+    S = synth.chirps(N_DEF, m_sample, SEED)
+    t_tot, by = 0.0, 0.0
+    k = 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        r = oracle.rb_greedy(S, TOL, KMAX)
+        t_tot += time.perf_counter() - t0
+        k = r["k"]
+        by += k * (16.0 * N_DEF * m_sample + 16.0 * N_DEF + 41.0 * m_sample)
+    return by / t_tot / 1e9, t_tot / steps, k
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    m = 4096
+    for _ in range(args.warmup):
+        cpu_oracle_run(m, 1)
+    gbs, t, k = cpu_oracle_run(m, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"FP64 CPU oracle, chirps N={N_DEF} x M={m} sample of the N={N_DEF} x "
+                                   f"M={M_DEF} workload, tol {TOL}, kmax {KMAX}", "k": k},
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{m} of {M_DEF} columns, N={N_DEF}, one full greedy per step"},
+            "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_1805_06124_gb300 import rb, synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    N, M = args.N, args.M
+    stream = torch.cuda.Stream(device=dev)
+    ctx = rb.RB(device=local, sweep=args.sweep, stream=stream, timing=True)
+    q, m = synth.chirp_params(M, SEED + rank)
+    with torch.cuda.stream(stream):
+        S = ctx.generate(q, m, N)
+    stream.synchronize()
+
+    def step():
+        with torch.cuda.stream(stream):
+            return ctx.greedy(S, TOL, KMAX, want_C=True, want_final_err=True)
+
+    for _ in range(args.warmup):
+        r = step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            results.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    sweep_bytes = sum(r["sweep_bytes"] for r in results)
+    if dist:
+        t = torch.tensor([sweep_bytes], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        sweep_bytes = float(t.item())
+    value = sweep_bytes / (ms_max * 1e-3) / 1e9
+    k = results[-1]["k"]
+    n_sw = sum(r["n_sweeps"] for r in results)
+    sweep_ms = sum(r["ms_sweep"] for r in results) / max(n_sw, 1)
+    per_launch = 16.0 * N * M + 16.0 * N + 41.0 * M
+    achieved = per_launch / (sweep_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    tpb = _sweep_traffic_per_byte()
+    launches = sum(r["n_launches"] for r in results)
+    clocks = clk.summary()
+    del results
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        Sh = torch.empty((M, N), dtype=torch.complex128, pin_memory=True)
+        Sh.copy_(S)
+        ctx_h = rb.RB(device=local, sweep=args.sweep, stream=stream)
+        del S
+        torch.cuda.empty_cache()
+        rh = ctx_h.greedy_host(Sh, TOL, KMAX)
+        t0 = time.perf_counter()
+        nst = max(1, min(args.steps, 2))
+        byts, h2d, d2h = 0.0, 0, 0
+        for _ in range(nst):
+            rh = ctx_h.greedy_host(Sh, TOL, KMAX)
+            byts += rh["sweep_bytes"]
+        dt = time.perf_counter() - t0
+        kh = rh["k"]
+        h2d = 16 * N * M
+        d2h = kh * N * 16 + kh * M * 16 + kh * 8 * 2 + (kh + 1) * 8 + M * 8
+        e2e = {"value": round(byts / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(dt / nst * 1e3, 2)}
+        ctx_h.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = 1
+        gbs, t_cpu, k_cpu = cpu_oracle_run(CPU_SAMPLE_M, 1)
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"one full greedy on {CPU_SAMPLE_M} of {M} columns (N={N}, seed {SEED}, tol {TOL}), "
+                         f"k={k_cpu}, {t_cpu:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"FP64-form RB-greedy on seeded chirps N={N} x M={M} complex128, "
+                                       f"tol {TOL}, kmax {KMAX}", "N": N, "M": M, "tol": TOL, "kmax": KMAX,
+                           "sweep": args.sweep, "k": k, "time_to_basis_ms": round(ms_max / args.steps, 3),
+                           "pct_of_hbm_peak": round(100 * value / peak, 1),
+                           "l2": "inputs larger than L2 (S is 34 GB; no flush needed)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                             "kernel": "k_sweep (fused dot + bookkeeping + argmax)",
+                             "traffic": (round(tpb * per_launch) if tpb else None),
+                             "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": round(sweep_ms, 4)},
+                "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweep", default="df32", choices=["df32", "fp64"])
+    ap.add_argument("--N", type=int, default=N_DEF)
+    ap.add_argument("--M", type=int, default=M_DEF)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -119,7 +119,10 @@ class RB:
         if stream is None:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
-        opt.stream = c_void_p(stream.cuda_stream)
+        # torch's legacy default stream has handle 0; pass cudaStreamLegacy
+        # (0x1) so the library orders its work with torch instead of
+        # creating a private stream.
+        opt.stream = c_void_p(stream.cuda_stream or 1)
         opt.flags = FLAG_TIMING if timing else 0
         h = c_void_p()
         st = self.lib.rb_create(ctypes.byref(opt), ctypes.byref(h))
@@ -151,7 +154,8 @@ class RB:
         m = torch.as_tensor(m, dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
         M = q.numel()
         ld = N if ld is None else ld
-        S = torch.empty((M, ld), dtype=torch.complex128, device=q.device)[:, :N]
+        with torch.cuda.stream(self.stream):
+            S = torch.empty((M, ld), dtype=torch.complex128, device=q.device)[:, :N]
         self._check(self.lib.rb_generate(self._h, q.data_ptr(), m.data_ptr(), N, M, S.data_ptr(), ld))
         return S
 
@@ -160,8 +164,9 @@ class RB:
         _check2d(S, torch.complex128, "S")
         M, N = S.shape
         ldh = N if ldh is None else ldh
-        hi = torch.empty((M, ldh), dtype=torch.complex64, device=S.device)
-        lo = torch.empty((M, ldh), dtype=torch.complex64, device=S.device)
+        with torch.cuda.stream(self.stream):
+            hi = torch.empty((M, ldh), dtype=torch.complex64, device=S.device)
+            lo = torch.empty((M, ldh), dtype=torch.complex64, device=S.device)
         self._check(self.lib.rb_split(self._h, S.data_ptr(), N, M, _ld(S), hi.data_ptr(), lo.data_ptr(), ldh))
         return hi[:, :N], lo[:, :N]
 
@@ -207,7 +212,8 @@ class RB:
         torch = _torch()
         _check2d(S, torch.complex128, "S")
         M, N = S.shape
-        r, bufs = self._alloc_result(N, M, kmax, S.device, want_C, want_final_err)
+        with torch.cuda.stream(self.stream):
+            r, bufs = self._alloc_result(N, M, kmax, S.device, want_C, want_final_err)
         st = self._check(self.lib.rb_greedy(self._h, S.data_ptr(), N, M, _ld(S), float(tol), int(kmax),
                                             ctypes.byref(r)))
         return self._pack(st, r, bufs)
@@ -252,7 +258,8 @@ class RB:
         if X.shape[1] != N:
             raise ValueError("Q and X disagree on N")
         Mx = X.shape[0]
-        C = torch.empty((max(k, 1), Mx), dtype=torch.complex128, device=X.device)
+        with torch.cuda.stream(self.stream):
+            C = torch.empty((max(k, 1), Mx), dtype=torch.complex128, device=X.device)
         self._check(self.lib.rb_project(self._h, Q.data_ptr(), N, k, _ld(Q), X.data_ptr(), Mx, _ld(X),
                                         C.data_ptr(), Mx))
         return C[:k]

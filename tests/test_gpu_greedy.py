@@ -179,7 +179,9 @@ def test_config2_full_size_sampled(orc, rbm, sweep):
     assert ec[k] < tol <= ec[k - 1]
     assert np.all(np.diff(ec) <= parity.delta(k, N, ec[0]))
     rd = g["rdiag"].cpu().numpy()
-    np.testing.assert_allclose(rd ** 2, ec[:k], rtol=1e-6, atol=1e-14)
+    # R(l,l)^2 (a direct norm) equals the bookkeeping max error up to the
+    # FP64 noise of Eq. (Residual) at N = 8192 (a few 1e-14 here)
+    np.testing.assert_allclose(rd ** 2, ec[:k], rtol=1e-9, atol=1e-13)
     piv = g["pivots"].cpu().numpy()
     Q = g["Q"].cpu().numpy()
     Gm = orc.project(Q, Q)
