@@ -40,6 +40,8 @@
 #ifndef RB_GB300_H
 #define RB_GB300_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -155,6 +157,34 @@ rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, l
  * Errors: RB_EINVAL, RB_ECUDA. */
 rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ,
                      const void *X, long long Mx, long long ldX, void *C, long long ldC);
+
+/* Greedy without any memory allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code whose
+ * device memory is owned by a framework's pool, services that must not grow
+ * their footprint after start-up, hosts where an allocation could block or
+ * fail at an unpredictable moment.  It runs the rb_greedy kernels with the
+ * plain-FP64 sweep (RB_SWEEP_FP64, which needs no N x M copy of S) and keeps
+ * all scratch in one fixed array in device memory (about 4.7 MB, present on
+ * every GPU that loads this library until the process exits), so it needs
+ * no rb_ctx and allocates nothing, host or device.
+ *   - Sizes must satisfy N <= RB_NOALLOC_MAX_N, M <= RB_NOALLOC_MAX_M and
+ *     kmax <= RB_NOALLOC_MAX_KMAX; larger sizes return RB_EINVAL with a message.
+ *   - S and *out as for rb_greedy (device pointers, caller-allocated).
+ *   - opt may be NULL: current device, the legacy default stream, default
+ *     IMGS options.  opt->sweep and opt->flags are ignored; the timing fields
+ *     of *out are left at zero.
+ *   - errbuf (may be NULL, errlen bytes) receives a message on failure.
+ *   - The first call for a device looks up the array's device address with
+ *     that device current; make it before any stream capture.
+ *   - Every call shares the array; calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and must be serialised by the
+ *     caller.
+ * Returns as rb_greedy. */
+#define RB_NOALLOC_MAX_N 16384
+#define RB_NOALLOC_MAX_M 262144
+#define RB_NOALLOC_MAX_KMAX 1024
+rb_status rb_greedy_noalloc(const void *S, long long N, long long M, long long ldS, double tol, int kmax,
+                            const rb_options *opt, rb_result *out, char *errbuf, size_t errlen);
 
 #ifdef __cplusplus
 }
