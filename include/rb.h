@@ -144,6 +144,20 @@ rb_status rb_split(rb_ctx *ctx, const void *S, long long N, long long M, long lo
 rb_status rb_greedy(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS,
                     double tol, int kmax, rb_result *out);
 
+/* Split-precision RB-greedy on S stored as complex64 hi + lo (see rb_split;
+ * column j at hi + j*ld and lo + j*ld, ld even, both 16-byte aligned).
+ * Phase 0 reads hi only: c = q^H hi with exact FP32 products summed in
+ * double-float, FP64 bookkeeping of the error of hi_j, and a certified bound
+ * |sqrt(err_j) - sqrt(err_hi_j)| <= ||lo_j||; the columns whose bound reaches
+ * the best lower bound are re-checked exactly and the exact argmax is the
+ * pivot.  Once the max error falls below opt.switch_err (or the loop ends),
+ * the basis is projected onto lo to make C and every error exact, and the
+ * remaining sweeps read hi + lo (the FP64 form's sweep).  IMGS, norms, the
+ * bookkeeping and the re-check stay FP64(-accurate).  Outputs and returns as
+ * rb_greedy; out->switch_iter is the first iteration that read hi + lo. */
+rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long N, long long M, long long ld,
+                          double tol, int kmax, rb_result *out);
+
 /* Same as rb_greedy, but S, every output array of *out, and the result are in
  * HOST memory (pinned or pageable).  The call copies S to the device and the
  * outputs back inside the call; device workspace is owned by the context. */

@@ -333,6 +333,124 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     return (rb_status)hs.status;
 }
 
+static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo, long long N, long long M,
+                                     long long ld, double tol, int kmax, rb_result *out) {
+    const rb_options &o = ctx->opt;
+    const int G = grid_for_variant(ctx, RB_SWEEP_DF32);
+    const int chunk = 2048;
+    const int nchunk = (int)((N + chunk - 1) / chunk);
+    const int gN = (int)((N + rbk::kThreads - 1) / rbk::kThreads);
+    const int kcap = kmax > 0 ? kmax : 1;
+    const long long qs = (long long)align_up((size_t)N, 64);
+    const int cand_cap = 1024;
+
+    Layout L;
+    size_t o_norm = L.add((size_t)M * 8), o_acc = L.add((size_t)M * 8), o_pick = L.add((size_t)M);
+    size_t o_nh = L.add((size_t)M * 8), o_ln = L.add((size_t)M * 4);
+    size_t o_qh = L.add((size_t)kcap * qs * sizeof(float2)), o_ql = L.add((size_t)kcap * qs * sizeof(float2));
+    size_t o_v = L.add((size_t)N * sizeof(double2));
+    size_t o_hp = L.add((size_t)kcap * nchunk * sizeof(double2));
+    size_t np = (size_t)(G > gN ? G : gN);
+    size_t o_np = L.add(np * 8), o_be = L.add((size_t)G * 8), o_bi = L.add((size_t)G * 8);
+    size_t o_bc = L.add((size_t)G * 4), o_cd = L.add((size_t)cand_cap * 8), o_ce = L.add((size_t)cand_cap * 8);
+    size_t o_C = out->C ? 0 : L.add((size_t)kcap * M * sizeof(double2));
+    size_t o_st = L.add(sizeof(rbk::DevState));
+    rb_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.off);
+    if (s != RB_OK) return s;
+    char *w = (char *)ctx->ws;
+
+    rbk::Prob p{};
+    p.N = N;
+    p.M = M;
+    p.ldS = 0;
+    p.ldH = ld;
+    p.ldQ = out->ldQ;
+    p.ldC = out->C ? out->ldC : M;
+    p.minNM = N < M ? N : M;
+    p.kmax = kmax;
+    p.max_passes = o.imgs_max_passes;
+    p.nchunk = nchunk;
+    p.chunk = chunk;
+    p.tol = tol;
+    p.kappa2 = o.imgs_kappa * o.imgs_kappa;
+    p.S = nullptr;
+    p.hi = (const float2 *)hi;
+    p.lo = (const float2 *)lo;
+    p.Q = (double2 *)out->Q;
+    p.pivots = out->pivots;
+    p.err_curve = out->err_curve;
+    p.C = out->C ? (double2 *)out->C : (double2 *)(w + o_C);
+    p.rdiag = out->rdiag;
+    p.norm2 = (double *)(w + o_norm);
+    p.acc = (double *)(w + o_acc);
+    p.picked = (unsigned char *)(w + o_pick);
+    p.qh = (float2 *)(w + o_qh);
+    p.ql = (float2 *)(w + o_ql);
+    p.qs_stride = qs;
+    p.v = (double2 *)(w + o_v);
+    p.hpart = (double2 *)(w + o_hp);
+    p.npart = (double *)(w + o_np);
+    p.bpart_err = (double *)(w + o_be);
+    p.bpart_idx = (long long *)(w + o_bi);
+    p.st = (rbk::DevState *)(w + o_st);
+    p.norm2_hi = (double *)(w + o_nh);
+    p.lonrm = (float *)(w + o_ln);
+    p.bcount = (int *)(w + o_bc);
+    p.nblk_cand = G;
+    p.cand = (long long *)(w + o_cd);
+    p.cand_err = (double *)(w + o_ce);
+    p.cand_cap = cand_cap;
+    p.switch_err = o.switch_err;
+
+    cudaStream_t sm = ctx->stream;
+    int nlaunch = 0;
+    RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
+    RB_CK(cudaMemsetAsync(p.st, 0, sizeof(rbk::DevState), sm), "memset state");
+    RB_CK(rbk::launch_split_init(p, sm), "split init");
+    RB_CK(rbk::launch_init(p, G, sm), "init");
+    nlaunch += 2;
+    int it = 0;
+    bool stopped = false;
+    // one more round than kmax: a loop that ends in the hi-only phase still
+    // queues its projection onto lo after the last sweep
+    while (!stopped) {
+        for (int t = 0; t < o.iters_per_sync && it <= kcap; t++, it++) {
+            RB_CK(rbk::launch_imgs(p, G, true, sm, &nlaunch), "imgs");
+            RB_CK(rbk::launch_split_iteration(p, G, sm, &nlaunch), "split iteration");
+        }
+        RB_CK(cudaMemcpyAsync(ctx->st_host, p.st, sizeof(rbk::DevState), cudaMemcpyDeviceToHost, sm), "state copy");
+        RB_CK(cudaStreamSynchronize(sm), "stream sync");
+        stopped = ctx->st_host->stop != 0;
+        if (!stopped && it > kcap) return fail(ctx, RB_ESTATE, "split greedy did not stop after kmax iterations");
+    }
+    if (out->final_err) {
+        RB_CK(rbk::launch_final_err(p, out->final_err, sm), "final_err");
+        nlaunch += 1;
+    }
+    RB_CK(cudaEventRecord(ctx->ev1, sm), "cudaEventRecord");
+    RB_CK(cudaEventSynchronize(ctx->ev1), "cudaEventSynchronize");
+    const rbk::DevState &hs = *ctx->st_host;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    out->k = hs.k;
+    out->imgs_passes = hs.total_passes;
+    out->switch_iter = hs.phase ? hs.switch_iter : -1;
+    out->n_launches = nlaunch;
+    out->n_sweeps = hs.n_sweeps;
+    out->ms_total = ms;
+    out->ms_sweep = 0.0;
+    const int n0 = hs.phase ? hs.switch_iter : hs.k;
+    const int n1 = hs.n_sweeps - n0;
+    out->sweep_bytes = (double)n0 * (8.0 * N * M + 16.0 * N + 41.0 * M) + (double)n1 * (16.0 * N * M + 16.0 * N + 41.0 * M);
+    if (hs.status < 0) {
+        const char *why = hs.status == RB_ENONFINITE ? "NaN or Inf in hi/lo"
+                          : hs.status == RB_EORTHO   ? "IMGS did not pass the kappa test within imgs_max_passes"
+                                                     : "device error";
+        return fail(ctx, (rb_status)hs.status, "rb_greedy_split: %s", why);
+    }
+    return (rb_status)hs.status;
+}
+
 static rb_status check_greedy_args(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol,
                                    int kmax, const rb_result *out) {
     if (!ctx) return RB_EINVAL;
@@ -354,6 +472,17 @@ rb_status rb_greedy(rb_ctx *ctx, const void *S, long long N, long long M, long l
         return fail(ctx, RB_EINVAL, "complex128 arrays must be 16-byte aligned");
     RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     return greedy_device(ctx, S, N, M, ldS, tol, kmax, out);
+}
+
+rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long N, long long M, long long ld,
+                          double tol, int kmax, rb_result *out) {
+    rb_status s = check_greedy_args(ctx, hi, N, M, ld, tol, kmax, out);
+    if (s != RB_OK) return s;
+    if (!lo || (ld & 1) || !aligned(hi, 16) || !aligned(lo, 16) || !aligned(out->Q, 16) ||
+        (out->C && !aligned(out->C, 16)))
+        return fail(ctx, RB_EINVAL, "rb_greedy_split: lo required, ld must be even and hi/lo 16-byte aligned");
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    return greedy_split_device(ctx, hi, lo, N, M, ld, tol, kmax, out);
 }
 
 rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol, int kmax,

@@ -133,8 +133,14 @@ __global__ void __launch_bounds__(kThreads) k_imgs_finalize(Prob p) {
     if (!(nv2 > 0.0)) {
         // the pivot column lies in the span already: exact rank reached
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            st->status = RB_OK;
-            st->stop = 1;
+            if (p.qs_stride && st->phase == 0) {
+                // split form, hi-only phase: make C and the errors exact, then stop
+                st->switch_pending = 1;
+                st->force_stop = 1;
+            } else {
+                st->status = RB_OK;
+                st->stop = 1;
+            }
         }
         return;
     }
@@ -147,8 +153,9 @@ __global__ void __launch_bounds__(kThreads) k_imgs_finalize(Prob p) {
         qk[i] = q;
         if (p.qh) {
             float hr = __double2float_rn(q.x), hm = __double2float_rn(q.y);
-            p.qh[i] = make_float2(hr, hm);
-            p.ql[i] = make_float2(__double2float_rn(q.x - (double)hr), __double2float_rn(q.y - (double)hm));
+            long long o = (long long)k * p.qs_stride + i;
+            p.qh[o] = make_float2(hr, hm);
+            p.ql[o] = make_float2(__double2float_rn(q.x - (double)hr), __double2float_rn(q.y - (double)hm));
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {

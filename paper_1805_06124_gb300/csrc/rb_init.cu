@@ -47,8 +47,48 @@ __global__ void __launch_bounds__(kThreads) k_generate(const double *q, const do
     }
 }
 
-// Warp per column: hi = fl32(x), lo = fl32(x - hi) (round to nearest), and
-// (when norm2 != null) ||s_j||^2 summed in FP64.
+// Round-to-nearest split of one double into hi = fl32(x), lo = fl32(x - hi)
+// with integer operations (the FP64 conversion units of this GPU run at the
+// FP64 rate).  Valid when the biased exponent e of x is in [949, 1149]: hi is
+// then a normal float and lo = (x - hi) is an integer of at most 29 bits
+// times 2^(e-1075), a normal float after one rounding.  Returns false
+// outside that range (zero, tiny, huge, Inf, NaN).
+__device__ __forceinline__ bool split_rn_fast(double x, float &h, float &l) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned int e = (unsigned int)(mag >> 52);
+    if (e < 949u || e > 1149u) return false;
+    const unsigned int w0 = (unsigned int)b;
+    const unsigned int lsb = (w0 >> 29) & 1u;
+    // round the 52-bit mantissa to 23 bits, ties to even; a carry moves
+    // into the exponent field by itself
+    const unsigned long long r = mag + 0x0FFFFFFFull + lsb;
+    const unsigned int fb = (unsigned int)(r >> 29) - (896u << 23);
+    h = __uint_as_float(fb | sign);
+    // x - hi: the dropped 29 bits, minus 2^29 when the mantissa rounded up
+    const unsigned int rem = w0 & 0x1FFFFFFFu;
+    int ri = (int)rem - ((rem + lsb > 0x10000000u) ? 0x20000000 : 0);
+    if (sign) ri = -ri;
+    l = __int2float_rn(ri) * __uint_as_float((e - 948u) << 23);
+    return true;
+}
+
+// (sh, sl) += (h + l)^2 in double-float.
+__device__ __forceinline__ void df_sq(float &sh, float &sl, float h, float l) {
+    float p = __fmul_rn(h, h);
+    float e = __fmaf_rn(h, h, -p);
+    e = __fmaf_rn(2.0f * h, l, e);
+    e = __fmaf_rn(l, l, e);
+    float s, t;
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
+// Warp per column: hi = fl32(x), lo = fl32(x - hi) (round to nearest) and,
+// when norm2 != null, ||hi + lo||^2 in double-float: the sweep works on
+// hi + lo, so its norms are taken of the same numbers.
 __global__ void __launch_bounds__(kThreads) k_split(const double2 *__restrict__ S, long long N, long long M,
                                                     long long ldS, float2 *__restrict__ hi,
                                                     float2 *__restrict__ lo, long long ldH,
@@ -58,21 +98,56 @@ __global__ void __launch_bounds__(kThreads) k_split(const double2 *__restrict__ 
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long j = gw; j < M; j += nw) {
         const double2 *s = S + j * ldS;
-        float2 *h = hi ? hi + j * ldH : nullptr;
-        float2 *l = lo ? lo + j * ldH : nullptr;
+        float2 *h = hi + j * ldH;
+        float2 *l = lo + j * ldH;
+        float nh = 0.f, nl = 0.f;
+        constexpr int U = 4;
+        long long i = lane;
+        for (; i < N; i += 32 * U) {
+            double2 x[U];
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (i + 32 * u < N) x[u] = ld_stream_d2(s + i + 32 * u);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (i + 32 * u >= N) break;
+                float hr, lr, hm, lm;
+                bool ok = split_rn_fast(x[u].x, hr, lr);
+                ok = split_rn_fast(x[u].y, hm, lm) && ok;
+                if (!ok) {
+                    hr = __double2float_rn(x[u].x);
+                    hm = __double2float_rn(x[u].y);
+                    lr = __double2float_rn(x[u].x - (double)hr);
+                    lm = __double2float_rn(x[u].y - (double)hm);
+                }
+                h[i + 32 * u] = make_float2(hr, hm);
+                l[i + 32 * u] = make_float2(lr, lm);
+                df_sq(nh, nl, hr, lr);
+                df_sq(nh, nl, hm, lm);
+            }
+        }
+        if (norm2) {
+            double nrm = warp_sum((double)nh + (double)nl);
+            if (lane == 0) norm2[j] = nrm;
+        }
+    }
+}
+
+// Warp per column: ||s_j||^2 in FP64 straight from complex128 (plain-FP64 form).
+__global__ void __launch_bounds__(kThreads) k_norms(const double2 *__restrict__ S, long long N, long long M,
+                                                    long long ldS, double *__restrict__ norm2) {
+    int lane = threadIdx.x & 31;
+    long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long j = gw; j < M; j += nw) {
+        const double2 *s = S + j * ldS;
         double nrm = 0.0;
         for (long long i = lane; i < N; i += 32) {
             double2 x = ld_stream_d2(s + i);
-            if (h) {
-                float hr = __double2float_rn(x.x), hm = __double2float_rn(x.y);
-                float lr = __double2float_rn(x.x - (double)hr), lm = __double2float_rn(x.y - (double)hm);
-                h[i] = make_float2(hr, hm);
-                l[i] = make_float2(lr, lm);
-            }
             nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
         }
         nrm = warp_sum(nrm);
-        if (lane == 0 && norm2) norm2[j] = nrm;
+        if (lane == 0) norm2[j] = nrm;
     }
 }
 
@@ -161,7 +236,7 @@ cudaError_t launch_split(const double2 *S, long long N, long long M, long long l
 cudaError_t launch_norms(const double2 *S, long long N, long long M, long long ldS, double *norm2,
                          cudaStream_t s) {
     int g = grid_for(M * 32, kThreads, 152 * 8);
-    k_split<<<g, kThreads, 0, s>>>(S, N, M, ldS, nullptr, nullptr, 0, norm2);
+    k_norms<<<g, kThreads, 0, s>>>(S, N, M, ldS, norm2);
     return cudaGetLastError();
 }
 

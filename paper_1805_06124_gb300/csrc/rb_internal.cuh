@@ -28,7 +28,12 @@ struct DevState {
     int switch_iter;   // split form: first iteration at phase 1 (-1 = never)
     int n_sweeps;      // sweep launches that did work
     int ncand;         // split form: candidates in the last recheck
-    int pad0;
+    int switch_pending;  // split form: rebase queued (hi+lo projection of the basis)
+    int cand_overflow;   // split form: a candidate list was truncated at its capacity
+    int max_cand;        // split form: largest candidate list seen
+    int force_stop;      // split form: stop right after the pending projection onto lo
+    int pad1;
+    double Lmax;       // split form: largest certified lower bound of the error
     long long J;       // next pivot column (kNoIdx = none left)
     double errJ;       // its error
     double before2;    // IMGS: ||v||^2 before the current pass
@@ -61,14 +66,25 @@ struct Prob {
     double *norm2;
     double *acc;
     unsigned char *picked;
-    float2 *qh;        // current basis vector, rounded to FP32
-    float2 *ql;        // its FP32 remainder
+    float2 *qh;        // basis vectors rounded to FP32 (slot k at qh + k * qs_stride)
+    float2 *ql;        // their FP32 remainders
+    long long qs_stride;  // 0: one slot reused every iteration; else N rounded up
     double2 *v;        // IMGS work vector
     double2 *hpart;    // IMGS partial dot products [kmax][nchunk]
     double *npart;     // per-block partial norms
     double *bpart_err; // per-block argmax partials
     long long *bpart_idx;
     DevState *st;
+    // split form
+    double *norm2_hi;  // ||hi_j||^2
+    float *lonrm;      // ||lo_j||
+    double *ehi;       // err of hi_j during the hi-only phase
+    long long *cand;   // candidate columns
+    double *cand_err;  // their exact errors
+    int *bcount;       // per-block candidate counts
+    int nblk_cand;     // blocks of the candidate kernels
+    int cand_cap;
+    double switch_err;
 };
 
 // ---------------------------------------------------------------- argmax key
@@ -220,6 +236,8 @@ cudaError_t launch_init(const Prob &p, int grid, cudaStream_t s);
 cudaError_t launch_sweep(const Prob &p, int variant, int grid, cudaStream_t s);
 cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s, int *nlaunch);
 cudaError_t launch_final_err(const Prob &p, double *final_err, cudaStream_t s);
+cudaError_t launch_split_init(const Prob &p, cudaStream_t s);
+cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
 cudaError_t launch_project(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mx,
                            long long ldX, double2 *C, long long ldC, cudaStream_t s);
 int sweep_grid(int variant, int device);

@@ -100,6 +100,7 @@ template <int VARIANT>
 __global__ void __launch_bounds__(kThreads) k_sweep(Prob p) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop)) return;
+    if (p.qs_stride && (ld_volatile(&st->phase) == 0 || ld_volatile(&st->switch_pending))) return;  // split form, hi-only phase
     const int k = st->k;  // row of C written by this sweep; q_k is the newest vector
     const int lane = threadIdx.x & 31;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -110,7 +111,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep(Prob p) {
     for (long long j = gw; j < p.M; j += nw) {
         double2 c;
         if (VARIANT == SWEEP_DF32)
-            c = col_dot_df32(p.hi + j * p.ldH, p.lo + j * p.ldH, p.qh, p.ql, p.N, lane);
+            c = col_dot_df32(p.hi + j * p.ldH, p.lo + j * p.ldH, p.qh + (long long)k * p.qs_stride,
+                             p.ql + (long long)k * p.qs_stride, p.N, lane);
         else
             c = col_dot_fp64(p.S + j * p.ldS, qk, p.N, lane);
         if (lane == 0) {

@@ -75,8 +75,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.rb_split.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_void_p, c_void_p, c_ll]
     lib.rb_greedy.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int, ctypes.POINTER(Result)]
     lib.rb_greedy_host.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int, ctypes.POINTER(Result)]
+    lib.rb_greedy_split.argtypes = [c_void_p, c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int,
+                                    ctypes.POINTER(Result)]
     lib.rb_project.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_void_p, c_ll]
-    for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_project"):
+    for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_greedy_split", "rb_project"):
         getattr(lib, f).restype = c_int
     _LIB = lib
     return lib
@@ -216,6 +218,21 @@ class RB:
             r, bufs = self._alloc_result(N, M, kmax, S.device, want_C, want_final_err)
         st = self._check(self.lib.rb_greedy(self._h, S.data_ptr(), N, M, _ld(S), float(tol), int(kmax),
                                             ctypes.byref(r)))
+        return self._pack(st, r, bufs)
+
+    def greedy_split(self, hi, lo, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True):
+        """Split-precision RB-greedy on hi/lo complex64 tensors of shape (M, N)
+        sharing one even leading dimension."""
+        torch = _torch()
+        _check2d(hi, torch.complex64, "hi")
+        _check2d(lo, torch.complex64, "lo")
+        if hi.shape != lo.shape or _ld(hi) != _ld(lo):
+            raise ValueError("hi and lo must have the same shape and leading dimension")
+        M, N = hi.shape
+        with torch.cuda.stream(self.stream):
+            r, bufs = self._alloc_result(N, M, kmax, hi.device, want_C, want_final_err)
+        st = self._check(self.lib.rb_greedy_split(self._h, hi.data_ptr(), lo.data_ptr(), N, M, _ld(hi), float(tol),
+                                                  int(kmax), ctypes.byref(r)))
         return self._pack(st, r, bufs)
 
     def greedy_host(self, S, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True):
