@@ -172,6 +172,39 @@ rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, l
 rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ,
                      const void *X, long long Mx, long long ldX, void *C, long long ldC);
 
+/* ---------------------------------------------------------------------------
+ * Learned surrogate (no counterpart in the paper): an MLP mapping a snapshot's
+ * parameters (q, m), scaled by the caller, to its n_out = 2k basis
+ * coefficients (Re/Im of c = Q^H s, interleaved), widths 2-256-256-256-n_out,
+ * exact-erf GELU, BF16 weights with FP32 master copies and FP32 accumulation
+ * on the tensor cores, Adam (beta 0.9/0.999, eps 1e-8) with cosine
+ * learning-rate decay.  Parameters are one FP32 vector: W1 (256x2), b1, W2
+ * (256x256), b2, W3 (256x256), b3, W4 (n_out x 256), b4, row-major.  Work is
+ * issued on the context's stream; rb_mlp_train synchronises it.
+ * ------------------------------------------------------------------------- */
+typedef struct rb_mlp rb_mlp;
+
+/* Glorot-uniform weights from splitmix64(seed), zero biases; batch_cap bounds
+ * the rows of one rb_mlp_grad call and the chunk of rb_mlp_infer. */
+rb_status rb_mlp_create(rb_ctx *ctx, int n_out, int batch_cap, unsigned long long seed, rb_mlp **out);
+void rb_mlp_destroy(rb_mlp *mlp);
+long long rb_mlp_num_params(const rb_mlp *mlp);
+/* dst / src: device FP32, rb_mlp_num_params entries.  set_params also resets
+ * the Adam moments and the step counter. */
+rb_status rb_mlp_get_params(rb_mlp *mlp, float *dst);
+rb_status rb_mlp_set_params(rb_mlp *mlp, const float *src);
+/* Y (rows x n_out, FP32) = MLP(X (rows x 2, FP32)); device pointers. */
+rb_status rb_mlp_infer(rb_mlp *mlp, const float *X, long long rows, float *Y);
+/* One forward + backward on rows <= batch_cap: grad (num_params) = d loss /
+ * d params for loss = (1/rows) sum_r ||MLP(x_r) - t_r||^2, *loss = that loss. */
+rb_status rb_mlp_grad(rb_mlp *mlp, const float *X, const float *T, long long rows, float *grad, float *loss);
+/* epochs x floor(rows/batch) Adam steps over (X, T); batch b of epoch e takes
+ * rows (a_e (b*batch + r) + c_e) mod rows (a seeded bijection per
+ * epoch); loss_curve (optional, device, epochs entries) receives each epoch's
+ * mean batch loss.  Returns RB_ETIMEOUT if a tensor-core wait ran out. */
+rb_status rb_mlp_train(rb_mlp *mlp, const float *X, const float *T, long long rows, int epochs, int batch, double lr,
+                       unsigned long long seed, float *loss_curve);
+
 /* Greedy without any memory allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- code whose
  * device memory is owned by a framework's pool, services that must not grow

@@ -93,6 +93,11 @@ int grid_for_variant(rb_ctx *ctx, int variant) {
 
 }  // namespace
 
+namespace rbk {
+cudaStream_t ctx_stream(rb_ctx *ctx) { return ctx->stream; }
+int ctx_device(rb_ctx *ctx) { return ctx->device; }
+}  // namespace rbk
+
 extern "C" {
 
 void rb_default_options(rb_options *opt) {

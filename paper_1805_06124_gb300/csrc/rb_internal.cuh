@@ -241,4 +241,6 @@ cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int 
 cudaError_t launch_project(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mx,
                            long long ldX, double2 *C, long long ldC, cudaStream_t s);
 int sweep_grid(int variant, int device);
+cudaStream_t ctx_stream(rb_ctx *ctx);
+int ctx_device(rb_ctx *ctx);
 }  // namespace rbk

@@ -226,17 +226,12 @@ __global__ void __launch_bounds__(kThreads) k_cand_write(Prob p) {
     if (!recheck_active(st)) return;
     const int k1 = st->k;
     const double Lmax = st->Lmax;
-    __shared__ int base, total;
+    __shared__ int base;
     __shared__ int wcount[kThreads / 32];
     if (threadIdx.x == 0) {
-        int b0 = 0, t = 0;
-        for (int b = 0; b < (int)gridDim.x; b++) {
-            int c = p.bcount[b];
-            if (b < (int)blockIdx.x) b0 += c;
-            t += c;
-        }
+        int b0 = 0;
+        for (int b = 0; b < (int)blockIdx.x; b++) b0 += p.bcount[b];
         base = b0;
-        total = t;
     }
     __syncthreads();
     const long long per = (p.M + gridDim.x - 1) / gridDim.x;
@@ -262,7 +257,6 @@ __global__ void __launch_bounds__(kThreads) k_cand_write(Prob p) {
         off += round;
         __syncthreads();
     }
-    (void)total;
 }
 
 // Exact error of each candidate: err_j = ||hi_j + lo_j||^2 - sum_l |c_hi,lj + q_l^H lo_j|^2.

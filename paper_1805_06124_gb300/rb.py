@@ -280,3 +280,108 @@ class RB:
         self._check(self.lib.rb_project(self._h, Q.data_ptr(), N, k, _ld(Q), X.data_ptr(), Mx, _ld(X),
                                         C.data_ptr(), Mx))
         return C[:k]
+
+
+class MLP:
+    """Learned surrogate (q, m) -> 2k coefficients on one RB context's stream.
+
+    Inputs X are (rows, 2) float32, targets T (rows, n_out) float32, all CUDA
+    tensors; the caller scales the inputs (e.g. to [-1, 1])."""
+
+    def __init__(self, ctx: "RB", n_out: int, batch_cap: int = 4096, seed: int = 0):
+        lib = ctx.lib
+        if not hasattr(lib.rb_mlp_create, "_rb_typed"):
+            lib.rb_mlp_create.argtypes = [c_void_p, c_int, c_int, ctypes.c_ulonglong, ctypes.POINTER(c_void_p)]
+            lib.rb_mlp_create.restype = c_int
+            lib.rb_mlp_destroy.argtypes = [c_void_p]
+            lib.rb_mlp_destroy.restype = None
+            lib.rb_mlp_num_params.argtypes = [c_void_p]
+            lib.rb_mlp_num_params.restype = c_ll
+            for f in ("rb_mlp_get_params", "rb_mlp_set_params"):
+                getattr(lib, f).argtypes = [c_void_p, c_void_p]
+                getattr(lib, f).restype = c_int
+            lib.rb_mlp_infer.argtypes = [c_void_p, c_void_p, c_ll, c_void_p]
+            lib.rb_mlp_infer.restype = c_int
+            lib.rb_mlp_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_ll, c_void_p, c_void_p]
+            lib.rb_mlp_grad.restype = c_int
+            lib.rb_mlp_train.argtypes = [c_void_p, c_void_p, c_void_p, c_ll, c_int, c_int, c_double,
+                                         ctypes.c_ulonglong, c_void_p]
+            lib.rb_mlp_train.restype = c_int
+            lib.rb_mlp_create._rb_typed = True
+        self.ctx, self.lib, self.n_out = ctx, lib, n_out
+        h = c_void_p()
+        st = lib.rb_mlp_create(ctx._h, n_out, batch_cap, seed, ctypes.byref(h))
+        if st != OK:
+            raise RBError(st, "rb_mlp_create failed")
+        self._h = h
+        self.n_params = int(lib.rb_mlp_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.rb_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st, what):
+        if st < 0:
+            raise RBError(st, what)
+        return st
+
+    def _dev(self):
+        return f"cuda:{self.ctx.device}"
+
+    def get_params(self):
+        torch = _torch()
+        with torch.cuda.stream(self.ctx.stream):
+            p = torch.empty(self.n_params, dtype=torch.float32, device=self._dev())
+        self._chk(self.lib.rb_mlp_get_params(self._h, p.data_ptr()), "rb_mlp_get_params")
+        self.ctx.stream.synchronize()
+        return p
+
+    def set_params(self, p):
+        torch = _torch()
+        p = p.to(device=self._dev(), dtype=torch.float32).contiguous()
+        self.ctx.stream.wait_stream(torch.cuda.current_stream())
+        self._chk(self.lib.rb_mlp_set_params(self._h, p.data_ptr()), "rb_mlp_set_params")
+        self.ctx.stream.synchronize()
+
+    def _inputs(self, X, T=None):
+        torch = _torch()
+        X = X.to(device=self._dev(), dtype=torch.float32).contiguous()
+        T = None if T is None else T.to(device=self._dev(), dtype=torch.float32).contiguous()
+        self.ctx.stream.wait_stream(torch.cuda.current_stream())
+        return X, T
+
+    def infer(self, X):
+        torch = _torch()
+        X, _ = self._inputs(X)
+        with torch.cuda.stream(self.ctx.stream):
+            Y = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=self._dev())
+        self._chk(self.lib.rb_mlp_infer(self._h, X.data_ptr(), X.shape[0], Y.data_ptr()), "rb_mlp_infer")
+        self.ctx.stream.synchronize()
+        return Y
+
+    def grad(self, X, T):
+        torch = _torch()
+        X, T = self._inputs(X, T)
+        with torch.cuda.stream(self.ctx.stream):
+            g = torch.empty(self.n_params, dtype=torch.float32, device=self._dev())
+            loss = torch.empty(1, dtype=torch.float32, device=self._dev())
+        self._chk(self.lib.rb_mlp_grad(self._h, X.data_ptr(), T.data_ptr(), X.shape[0], g.data_ptr(),
+                                       loss.data_ptr()), "rb_mlp_grad")
+        self.ctx.stream.synchronize()
+        return g, float(loss.item())
+
+    def train(self, X, T, epochs: int, batch: int = 1024, lr: float = 1e-3, seed: int = 0):
+        torch = _torch()
+        X, T = self._inputs(X, T)
+        with torch.cuda.stream(self.ctx.stream):
+            curve = torch.zeros(max(epochs, 1), dtype=torch.float32, device=self._dev())
+        self._chk(self.lib.rb_mlp_train(self._h, X.data_ptr(), T.data_ptr(), X.shape[0], epochs, batch, float(lr),
+                                        seed, curve.data_ptr()), "rb_mlp_train")
+        return curve[:epochs]
