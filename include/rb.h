@@ -104,6 +104,7 @@ typedef struct rb_result {
     double ms_total;       /* CUDA-event time of the call on its stream */
     double ms_sweep;       /* summed CUDA-event time of the sweep launches (RB_FLAG_TIMING) */
     double sweep_bytes;    /* algorithmic bytes read and written by those sweeps */
+    int status;            /* this problem's rb_status (the batched call returns the most severe) */
 } rb_result;
 
 /* Creates a context on opt->device (NULL opt = defaults).  The context owns
@@ -157,6 +158,26 @@ rb_status rb_greedy(rb_ctx *ctx, const void *S, long long N, long long M, long l
  * rb_greedy; out->switch_iter is the first iteration that read hi + lo. */
 rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long N, long long M, long long ld,
                           double tol, int kmax, rb_result *out);
+
+/* One problem of a batch: complex128 snapshots, column-major, ldS >= N (device). */
+typedef struct rb_problem {
+    const void *S;
+    long long N, M, ldS;
+} rb_problem;
+
+/* nprob independent RB-greedy problems of uneven N and M (Alg. 3 on each), in
+ * the FP64 form's arithmetic.  Every iteration runs each active problem's IMGS
+ * and ONE persistent sweep launch over the columns of all active problems
+ * (chunks of columns numbered across problems); each problem keeps its own
+ * state and stops on its own.  The iteration is captured once as a CUDA graph
+ * and replayed.  The sweep reads complex128 directly (hi/lo split in
+ * registers), so the batch needs no copy of its data.  The sweep's unroll
+ * depth, block width and columns per chunk are chosen by timing every variant
+ * on a dry sweep of the batch (cached per batch shape in the context).
+ * outs[b] as for rb_greedy.  Returns the most severe status over the
+ * problems (an error if any failed, RB_KMAX_REACHED if any stopped at kmax). */
+rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, double tol, int kmax,
+                            rb_result *outs);
 
 /* Same as rb_greedy, but S, every output array of *out, and the result are in
  * HOST memory (pinned or pageable).  The call copies S to the device and the

@@ -9,7 +9,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "rb_internal.cuh"
@@ -31,6 +34,7 @@ struct rb_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> sweep_ev;
     int grid_cache[2] = {0, 0};
+    std::map<std::tuple<int, long long, long long>, std::pair<int, int>> tune;  // batch shape -> (variant, CW)
 };
 
 namespace {
@@ -313,6 +317,7 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     out->k = hs.k;
+    out->status = hs.status;
     out->imgs_passes = hs.total_passes;
     out->switch_iter = -1;
     out->n_launches = nlaunch;
@@ -438,6 +443,7 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     out->k = hs.k;
+    out->status = hs.status;
     out->imgs_passes = hs.total_passes;
     out->switch_iter = hs.phase ? hs.switch_iter : -1;
     out->n_launches = nlaunch;
@@ -454,6 +460,259 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
         return fail(ctx, (rb_status)hs.status, "rb_greedy_split: %s", why);
     }
     return (rb_status)hs.status;
+}
+
+static int rb_log_level() {
+    const char *e = getenv("RB_LOG");
+    return e ? atoi(e) : 0;
+}
+
+rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, double tol, int kmax,
+                            rb_result *outs) {
+    if (!ctx) return RB_EINVAL;
+    if (nprob < 1 || !probs || !outs) return fail(ctx, RB_EINVAL, "rb_greedy_batched: bad problem list");
+    if (!(tol >= 0.0) || !std::isfinite(tol) || kmax < 0) return fail(ctx, RB_EINVAL, "rb_greedy_batched: bad tol/kmax");
+    long long maxN = 0, sumNM = 0;
+    for (int b = 0; b < nprob; b++) {
+        const rb_problem &pr = probs[b];
+        const rb_result &o = outs[b];
+        if (!pr.S || pr.N < 1 || pr.M < 1 || pr.ldS < pr.N || !aligned(pr.S, 16) || !o.Q || !o.pivots ||
+            !o.err_curve || o.ldQ < pr.N || !aligned(o.Q, 16) || (o.C && (o.ldC < pr.M || !aligned(o.C, 16))))
+            return fail(ctx, RB_EINVAL, "rb_greedy_batched: bad arguments for problem %d", b);
+        maxN = pr.N > maxN ? pr.N : maxN;
+        sumNM += pr.N * pr.M;
+    }
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const rb_options &o = ctx->opt;
+    const int G = grid_for_variant(ctx, RB_SWEEP_DF32);
+    const int chunk = 2048;
+    const int kcap = kmax > 0 ? kmax : 1;
+    const int CWs[2] = {32, 128};
+    // workspace layout
+    Layout L;
+    std::vector<size_t> o_norm(nprob), o_acc(nprob), o_pick(nprob), o_qh(nprob), o_ql(nprob), o_v(nprob),
+        o_hp(nprob), o_np(nprob), o_be(nprob), o_bi(nprob), o_st(nprob);
+    long long chunks_min_cw = 0, total_cols = 0;
+    for (int b = 0; b < nprob; b++) {
+        const long long N = probs[b].N, M = probs[b].M;
+        const int nchunk = (int)((N + chunk - 1) / chunk), gN = (int)((N + rbk::kThreads - 1) / rbk::kThreads);
+        o_norm[b] = L.add((size_t)M * 8);
+        o_acc[b] = L.add((size_t)M * 8);
+        o_pick[b] = L.add((size_t)M);
+        o_qh[b] = L.add((size_t)(N + 2) * 8);
+        o_ql[b] = L.add((size_t)(N + 2) * 8);
+        o_v[b] = L.add((size_t)N * 16);
+        o_hp[b] = L.add((size_t)kcap * nchunk * 16);
+        o_np[b] = L.add((size_t)(G > gN ? G : gN) * 8);
+        o_be[b] = L.add((size_t)G * 8);
+        o_bi[b] = L.add((size_t)G * 8);
+        o_st[b] = L.add(sizeof(rbk::DevState));
+        chunks_min_cw += (M + CWs[0] - 1) / CWs[0];
+        total_cols += M;
+    }
+    size_t o_P = L.add((size_t)nprob * sizeof(rbk::BProb));
+    size_t o_ch = L.add((size_t)(nprob + 1) * 8), o_col = L.add((size_t)(nprob + 1) * 8);
+    size_t o_pe = L.add((size_t)chunks_min_cw * 8), o_pi = L.add((size_t)chunks_min_cw * 8);
+    rb_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.off);
+    if (s != RB_OK) return s;
+    char *w = (char *)ctx->ws;
+    cudaStream_t sm = ctx->stream;
+    RB_CK(cudaMemsetAsync(w, 0, L.off, sm), "memset workspace");
+
+    std::vector<rbk::Prob> pp(nprob);
+    std::vector<rbk::BProb> bp(nprob);
+    std::vector<long long> col0(nprob + 1, 0);
+    for (int b = 0; b < nprob; b++) {
+        const long long N = probs[b].N, M = probs[b].M;
+        rbk::Prob &p = pp[b];
+        p = rbk::Prob{};
+        p.N = N;
+        p.M = M;
+        p.ldS = probs[b].ldS;
+        p.ldQ = outs[b].ldQ;
+        p.ldC = outs[b].ldC;
+        p.minNM = N < M ? N : M;
+        p.kmax = kmax;
+        p.max_passes = o.imgs_max_passes;
+        p.chunk = chunk;
+        p.nchunk = (int)((N + chunk - 1) / chunk);
+        p.tol = tol;
+        p.kappa2 = o.imgs_kappa * o.imgs_kappa;
+        p.S = (const double2 *)probs[b].S;
+        p.Q = (double2 *)outs[b].Q;
+        p.pivots = outs[b].pivots;
+        p.err_curve = outs[b].err_curve;
+        p.C = (double2 *)outs[b].C;
+        p.rdiag = outs[b].rdiag;
+        p.norm2 = (double *)(w + o_norm[b]);
+        p.acc = (double *)(w + o_acc[b]);
+        p.picked = (unsigned char *)(w + o_pick[b]);
+        p.qh = (float2 *)(w + o_qh[b]);
+        p.ql = (float2 *)(w + o_ql[b]);
+        p.v = (double2 *)(w + o_v[b]);
+        p.hpart = (double2 *)(w + o_hp[b]);
+        p.npart = (double *)(w + o_np[b]);
+        p.bpart_err = (double *)(w + o_be[b]);
+        p.bpart_idx = (long long *)(w + o_bi[b]);
+        p.st = (rbk::DevState *)(w + o_st[b]);
+        rbk::BProb &q = bp[b];
+        q = rbk::BProb{};
+        q.N = N;
+        q.M = M;
+        q.ldS = p.ldS;
+        q.ldC = p.ldC;
+        q.S = p.S;
+        q.C = p.C;
+        q.err_curve = p.err_curve;
+        q.norm2 = p.norm2;
+        q.acc = p.acc;
+        q.picked = p.picked;
+        q.qh = p.qh;
+        q.ql = p.ql;
+        q.st = p.st;
+        q.kmax = kmax;
+        q.minNM = p.minNM;
+        q.tol = tol;
+        col0[b + 1] = col0[b] + M;
+    }
+    rbk::BProb *dP = (rbk::BProb *)(w + o_P);
+    long long *dch = (long long *)(w + o_ch), *dcol = (long long *)(w + o_col);
+    double *dpe = (double *)(w + o_pe);
+    long long *dpi = (long long *)(w + o_pi);
+    RB_CK(cudaMemcpyAsync(dP, bp.data(), nprob * sizeof(rbk::BProb), cudaMemcpyHostToDevice, sm), "copy problems");
+    RB_CK(cudaMemcpyAsync(dcol, col0.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm), "copy prefix");
+    auto chunk_prefix = [&](int CW) {
+        std::vector<long long> c(nprob + 1, 0);
+        for (int b = 0; b < nprob; b++) c[b + 1] = c[b] + (probs[b].M + CW - 1) / CW;
+        return c;
+    };
+    // ---- autotune (dry sweeps of this batch), cached per batch shape
+    auto key = std::make_tuple(nprob, sumNM, maxN);
+    int best_v = 4, best_cw = 32;
+    auto it_t = ctx->tune.find(key);
+    if (it_t != ctx->tune.end()) {
+        best_v = it_t->second.first;
+        best_cw = it_t->second.second;
+    } else {
+        float best_ms = 1e30f;
+        for (int ci = 0; ci < 2; ci++) {
+            std::vector<long long> c = chunk_prefix(CWs[ci]);
+            RB_CK(cudaMemcpyAsync(dch, c.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm), "copy chunks");
+            for (int v = 0; v < 6; v++) {
+                int g = rbk::bsweep_grid(v, ctx->device);
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; rep++) {
+                    RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
+                    RB_CK(rbk::launch_bsweep(v, g, dP, nprob, dch, CWs[ci], dpe, dpi, 1, sm), "dry sweep");
+                    RB_CK(cudaEventRecord(ctx->ev1, sm), "cudaEventRecord");
+                    RB_CK(cudaEventSynchronize(ctx->ev1), "cudaEventSynchronize");
+                    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+                }
+                if (rb_log_level() > 0)
+                    fprintf(stderr, "rb autotune: U=%d threads=%d CW=%d  %.3f ms\n", (int[]){2, 4, 8}[v % 3],
+                            rbk::bsweep_threads(v), CWs[ci], ms);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_v = v;
+                    best_cw = CWs[ci];
+                }
+            }
+        }
+        ctx->tune[key] = std::make_pair(best_v, best_cw);
+    }
+    {
+        std::vector<long long> c = chunk_prefix(best_cw);
+        RB_CK(cudaMemcpyAsync(dch, c.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm), "copy chunks");
+    }
+    const int gv = rbk::bsweep_grid(best_v, ctx->device);
+    for (int b = 0; b < nprob; b++) RB_CK(cudaMemsetAsync(pp[b].st, 0, sizeof(rbk::DevState), sm), "memset state");
+    RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
+    RB_CK(rbk::launch_bnorms(dP, nprob, dcol, total_cols, sm), "norms");
+    int nlaunch = 1;
+    for (int b = 0; b < nprob; b++) {
+        RB_CK(rbk::launch_init(pp[b], G, sm), "init");
+        nlaunch++;
+    }
+    // ---- capture one iteration: per-problem IMGS on 8 forked streams, then the sweep and reduction
+    const int NS = 8;
+    cudaStream_t cap = nullptr, br[NS] = {};
+    cudaEvent_t fork = nullptr, join[NS] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    for (int i = 0; i < NS && e == cudaSuccess; i++) e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < NS && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    int per_iter = 0;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecord(fork, cap);
+        for (int i = 0; i < NS; i++) cudaStreamWaitEvent(br[i], fork, 0);
+        for (int b = 0; b < nprob; b++) rbk::launch_imgs(pp[b], G, false, br[b % NS], &per_iter);
+        for (int i = 0; i < NS; i++) {
+            cudaEventRecord(join[i], br[i]);
+            cudaStreamWaitEvent(cap, join[i], 0);
+        }
+        rbk::launch_bsweep(best_v, gv, dP, nprob, dch, best_cw, dpe, dpi, 0, cap);
+        rbk::launch_breduce(dP, nprob, dch, dpe, dpi, cap);
+        per_iter += 2;
+        e = cudaStreamEndCapture(cap, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    // ---- replay until every problem has stopped
+    std::vector<rbk::DevState> hs(nprob);
+    int it = 0;
+    bool all = false;
+    while (e == cudaSuccess && !all) {
+        for (int t = 0; t < o.iters_per_sync && it <= kcap && e == cudaSuccess; t++, it++) {
+            e = cudaGraphLaunch(exec, sm);
+            nlaunch += per_iter;
+        }
+        for (int b = 0; b < nprob && e == cudaSuccess; b++)
+            e = cudaMemcpyAsync(&hs[b], pp[b].st, sizeof(rbk::DevState), cudaMemcpyDeviceToHost, sm);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+        all = true;
+        for (int b = 0; b < nprob; b++) all = all && hs[b].stop;
+        if (!all && it > kcap) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (int i = 0; i < NS; i++) {
+        if (join[i]) cudaEventDestroy(join[i]);
+        if (br[i]) cudaStreamDestroy(br[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rb_greedy_batched loop");
+    if (!all) return fail(ctx, RB_ESTATE, "rb_greedy_batched: a problem did not stop after kmax iterations");
+    for (int b = 0; b < nprob; b++)
+        if (outs[b].final_err) {
+            RB_CK(rbk::launch_final_err(pp[b], outs[b].final_err, sm), "final_err");
+            nlaunch++;
+        }
+    RB_CK(cudaEventRecord(ctx->ev1, sm), "cudaEventRecord");
+    RB_CK(cudaEventSynchronize(ctx->ev1), "cudaEventSynchronize");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    rb_status worst = RB_OK;
+    for (int b = 0; b < nprob; b++) {
+        rb_result &out = outs[b];
+        const long long N = probs[b].N, M = probs[b].M;
+        out.k = hs[b].k;
+        out.status = hs[b].status;
+        out.imgs_passes = hs[b].total_passes;
+        out.switch_iter = -1;
+        out.n_launches = nlaunch;
+        out.n_sweeps = hs[b].n_sweeps;
+        out.ms_total = ms;
+        out.ms_sweep = 0.0;
+        out.sweep_bytes = (double)hs[b].n_sweeps * (16.0 * N * M + 16.0 * N + 41.0 * M);
+        rb_status sb = (rb_status)hs[b].status;
+        if (sb < 0 && (worst >= 0 || sb < worst)) worst = sb;
+        else if (worst == RB_OK && sb == RB_KMAX_REACHED) worst = sb;
+    }
+    if (worst < 0) return fail(ctx, worst, "rb_greedy_batched: a problem failed (status %d)", (int)worst);
+    return worst;
 }
 
 static rb_status check_greedy_args(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol,

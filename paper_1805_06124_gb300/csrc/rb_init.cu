@@ -47,45 +47,6 @@ __global__ void __launch_bounds__(kThreads) k_generate(const double *q, const do
     }
 }
 
-// Round-to-nearest split of one double into hi = fl32(x), lo = fl32(x - hi)
-// with integer operations (the FP64 conversion units of this GPU run at the
-// FP64 rate).  Valid when the biased exponent e of x is in [949, 1149]: hi is
-// then a normal float and lo = (x - hi) is an integer of at most 29 bits
-// times 2^(e-1075), a normal float after one rounding.  Returns false
-// outside that range (zero, tiny, huge, Inf, NaN).
-__device__ __forceinline__ bool split_rn_fast(double x, float &h, float &l) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
-    const unsigned int e = (unsigned int)(mag >> 52);
-    if (e < 949u || e > 1149u) return false;
-    const unsigned int w0 = (unsigned int)b;
-    const unsigned int lsb = (w0 >> 29) & 1u;
-    // round the 52-bit mantissa to 23 bits, ties to even; a carry moves
-    // into the exponent field by itself
-    const unsigned long long r = mag + 0x0FFFFFFFull + lsb;
-    const unsigned int fb = (unsigned int)(r >> 29) - (896u << 23);
-    h = __uint_as_float(fb | sign);
-    // x - hi: the dropped 29 bits, minus 2^29 when the mantissa rounded up
-    const unsigned int rem = w0 & 0x1FFFFFFFu;
-    int ri = (int)rem - ((rem + lsb > 0x10000000u) ? 0x20000000 : 0);
-    if (sign) ri = -ri;
-    l = __int2float_rn(ri) * __uint_as_float((e - 948u) << 23);
-    return true;
-}
-
-// (sh, sl) += (h + l)^2 in double-float.
-__device__ __forceinline__ void df_sq(float &sh, float &sl, float h, float l) {
-    float p = __fmul_rn(h, h);
-    float e = __fmaf_rn(h, h, -p);
-    e = __fmaf_rn(2.0f * h, l, e);
-    e = __fmaf_rn(l, l, e);
-    float s, t;
-    two_sum(sh, p, s, t);
-    sh = s;
-    sl = __fadd_rn(sl, __fadd_rn(t, e));
-}
-
 // Warp per column: hi = fl32(x), lo = fl32(x - hi) (round to nearest) and,
 // when norm2 != null, ||hi + lo||^2 in double-float: the sweep works on
 // hi + lo, so its norms are taken of the same numbers.

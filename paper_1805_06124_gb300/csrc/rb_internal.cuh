@@ -87,6 +87,25 @@ struct Prob {
     double switch_err;
 };
 
+// One problem of a batch (rb_greedy_batched): what the persistent sweep and
+// the per-problem reduction need.
+struct BProb {
+    long long N, M, ldS, ldC;
+    const double2 *S;
+    double2 *C;
+    double *err_curve;
+    double *norm2;
+    double *acc;
+    unsigned char *picked;
+    const float2 *qh;
+    const float2 *ql;
+    DevState *st;
+    int kmax;
+    int pad;
+    long long minNM;
+    double tol;
+};
+
 // ---------------------------------------------------------------- argmax key
 // (err, idx) is better than (err2, idx2) when err is larger, ties to the
 // lower index.
@@ -221,6 +240,53 @@ __device__ __forceinline__ double2 ld_stream_d2(const double2 *p) {
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
 
+// Round-to-nearest split of one double into hi = fl32(x), lo = fl32(x - hi)
+// with integer operations (the FP64 conversion units of this GPU run at the
+// FP64 rate).  Valid when the biased exponent e of x is in [949, 1149]: hi is
+// then a normal float and lo = (x - hi) is an integer of at most 29 bits
+// times 2^(e-1075), a normal float after one rounding.  Returns false
+// outside that range (zero, tiny, huge, Inf, NaN).
+__device__ __forceinline__ bool split_rn_fast(double x, float &h, float &l) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned int e = (unsigned int)(mag >> 52);
+    if (e < 949u || e > 1149u) return false;
+    const unsigned int w0 = (unsigned int)b;
+    const unsigned int lsb = (w0 >> 29) & 1u;
+    // round the 52-bit mantissa to 23 bits, ties to even; a carry moves
+    // into the exponent field by itself
+    const unsigned long long r = mag + 0x0FFFFFFFull + lsb;
+    const unsigned int fb = (unsigned int)(r >> 29) - (896u << 23);
+    h = __uint_as_float(fb | sign);
+    // x - hi: the dropped 29 bits, minus 2^29 when the mantissa rounded up
+    const unsigned int rem = w0 & 0x1FFFFFFFu;
+    int ri = (int)rem - ((rem + lsb > 0x10000000u) ? 0x20000000 : 0);
+    if (sign) ri = -ri;
+    l = __int2float_rn(ri) * __uint_as_float((e - 948u) << 23);
+    return true;
+}
+
+// (sh, sl) += (h + l)^2 in double-float.
+__device__ __forceinline__ void df_sq(float &sh, float &sl, float h, float l) {
+    float p = __fmul_rn(h, h);
+    float e = __fmaf_rn(h, h, -p);
+    e = __fmaf_rn(2.0f * h, l, e);
+    e = __fmaf_rn(l, l, e);
+    float s, t;
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
+// Split with the intrinsic conversions when the fast path does not apply.
+__device__ __forceinline__ void split_rn(double x, float &h, float &l) {
+    if (!split_rn_fast(x, h, l)) {
+        h = __double2float_rn(x);
+        l = __double2float_rn(x - (double)h);
+    }
+}
+
 }  // namespace rbk
 
 // ------------------------------------------------------------- host launchers
@@ -241,6 +307,13 @@ cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int 
 cudaError_t launch_project(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mx,
                            long long ldX, double2 *C, long long ldC, cudaStream_t s);
 int sweep_grid(int variant, int device);
+cudaError_t launch_bnorms(const BProb *P, int nprob, const long long *col0, long long total_cols, cudaStream_t s);
+int bsweep_threads(int v);
+int bsweep_grid(int v, int device);
+cudaError_t launch_bsweep(int v, int grid, const BProb *P, int nprob, const long long *chunk0, int CW,
+                          double *part_err, long long *part_idx, int dry, cudaStream_t s);
+cudaError_t launch_breduce(const BProb *P, int nprob, const long long *chunk0, const double *part_err,
+                           const long long *part_idx, cudaStream_t s);
 cudaStream_t ctx_stream(rb_ctx *ctx);
 int ctx_device(rb_ctx *ctx);
 }  // namespace rbk

@@ -36,7 +36,12 @@ class Result(ctypes.Structure):
     _fields_ = [("Q", c_void_p), ("ldQ", c_ll), ("pivots", c_ll_p), ("err_curve", c_double_p),
                 ("C", c_void_p), ("ldC", c_ll), ("final_err", c_double_p), ("rdiag", c_double_p),
                 ("k", c_int), ("imgs_passes", c_int), ("switch_iter", c_int), ("n_launches", c_int),
-                ("n_sweeps", c_int), ("ms_total", c_double), ("ms_sweep", c_double), ("sweep_bytes", c_double)]
+                ("n_sweeps", c_int), ("ms_total", c_double), ("ms_sweep", c_double), ("sweep_bytes", c_double),
+                ("status", c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("S", c_void_p), ("N", c_ll), ("M", c_ll), ("ldS", c_ll)]
 
 
 class RBError(RuntimeError):
@@ -78,6 +83,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.rb_greedy_split.argtypes = [c_void_p, c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int,
                                     ctypes.POINTER(Result)]
     lib.rb_project.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_void_p, c_ll]
+    lib.rb_greedy_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(Problem), c_double, c_int,
+                                      ctypes.POINTER(Result)]
+    lib.rb_greedy_batched.restype = c_int
     for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_greedy_split", "rb_project"):
         getattr(lib, f).restype = c_int
     _LIB = lib
@@ -234,6 +242,25 @@ class RB:
         st = self._check(self.lib.rb_greedy_split(self._h, hi.data_ptr(), lo.data_ptr(), N, M, _ld(hi), float(tol),
                                                   int(kmax), ctypes.byref(r)))
         return self._pack(st, r, bufs)
+
+    def greedy_batched(self, Ss, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True):
+        """Independent RB-greedy problems (a list of (M_b, N_b) complex128 CUDA
+        tensors) in one batched call; returns one result dict per problem."""
+        torch = _torch()
+        n = len(Ss)
+        probs = (Problem * n)()
+        results = (Result * n)()
+        keep = []
+        for b, S in enumerate(Ss):
+            _check2d(S, torch.complex128, f"S[{b}]")
+            M, N = S.shape
+            probs[b].S, probs[b].N, probs[b].M, probs[b].ldS = S.data_ptr(), N, M, _ld(S)
+            with torch.cuda.stream(self.stream):
+                r, bufs = self._alloc_result(N, M, kmax, S.device, want_C, want_final_err)
+            results[b] = r
+            keep.append(bufs)
+        st = self._check(self.lib.rb_greedy_batched(self._h, n, probs, float(tol), int(kmax), results))
+        return [self._pack(results[b].status, results[b], keep[b]) for b in range(n)]
 
     def greedy_host(self, S, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True):
         """Same as greedy, with S and all outputs in host memory (CPU tensors;
