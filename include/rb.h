@@ -205,7 +205,8 @@ rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long l
  * ------------------------------------------------------------------------- */
 typedef struct rb_mlp rb_mlp;
 
-/* Glorot-uniform weights from splitmix64(seed), zero biases; batch_cap bounds
+/* Weights and biases of each layer uniform on +-1/sqrt(fan_in) from
+ * splitmix64(seed); batch_cap bounds
  * the rows of one rb_mlp_grad call and the chunk of rb_mlp_infer. */
 rb_status rb_mlp_create(rb_ctx *ctx, int n_out, int batch_cap, unsigned long long seed, rb_mlp **out);
 void rb_mlp_destroy(rb_mlp *mlp);

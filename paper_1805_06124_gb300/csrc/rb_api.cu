@@ -510,6 +510,24 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
         chunks_min_cw += (M + CWs[0] - 1) / CWs[0];
         total_cols += M;
     }
+    // pre-split hi/lo copy when it fits in free device memory (sweeps then stream
+    // 16 bytes per element without the in-register split)
+    std::vector<size_t> o_hi(nprob), o_lo(nprob);
+    std::vector<long long> ldHs(nprob);
+    size_t split_bytes = 0;
+    for (int b = 0; b < nprob; b++) {
+        ldHs[b] = (long long)align_up((size_t)probs[b].N, 64);
+        split_bytes += 2 * (size_t)probs[b].M * ldHs[b] * sizeof(float2) + 1024;
+    }
+    size_t freeb = 0, totalb = 0;
+    RB_CK(cudaMemGetInfo(&freeb, &totalb), "cudaMemGetInfo");
+    const size_t have = ctx->ws_cap;
+    const bool presplit = (split_bytes + L.off + (4ull << 30)) < (size_t)(0.95 * (double)(freeb + have));
+    if (presplit)
+        for (int b = 0; b < nprob; b++) {
+            o_hi[b] = L.add((size_t)probs[b].M * ldHs[b] * sizeof(float2));
+            o_lo[b] = L.add((size_t)probs[b].M * ldHs[b] * sizeof(float2));
+        }
     size_t o_P = L.add((size_t)nprob * sizeof(rbk::BProb));
     size_t o_ch = L.add((size_t)(nprob + 1) * 8), o_col = L.add((size_t)(nprob + 1) * 8);
     size_t o_pe = L.add((size_t)chunks_min_cw * 8), o_pi = L.add((size_t)chunks_min_cw * 8);
@@ -573,6 +591,11 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
         q.kmax = kmax;
         q.minNM = p.minNM;
         q.tol = tol;
+        if (presplit) {
+            q.hi = (const float2 *)(w + o_hi[b]);
+            q.lo = (const float2 *)(w + o_lo[b]);
+            q.ldH = ldHs[b];
+        }
         col0[b + 1] = col0[b] + M;
     }
     rbk::BProb *dP = (rbk::BProb *)(w + o_P);
@@ -587,8 +610,14 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
         return c;
     };
     // ---- autotune (dry sweeps of this batch), cached per batch shape
-    auto key = std::make_tuple(nprob, sumNM, maxN);
-    int best_v = 4, best_cw = 32;
+    const int v0 = presplit ? 6 : 0;
+    auto key = std::make_tuple(nprob * (presplit ? -1 : 1), sumNM, maxN);
+    if (presplit && ctx->tune.find(key) == ctx->tune.end())  // the tuning sweeps read the copy
+        for (int b = 0; b < nprob; b++)
+            RB_CK(rbk::launch_split(pp[b].S, probs[b].N, probs[b].M, probs[b].ldS, (float2 *)bp[b].hi,
+                                    (float2 *)bp[b].lo, ldHs[b], pp[b].norm2, sm),
+                  "split");
+    int best_v = v0 + 3, best_cw = 32;
     auto it_t = ctx->tune.find(key);
     if (it_t != ctx->tune.end()) {
         best_v = it_t->second.first;
@@ -598,7 +627,7 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
         for (int ci = 0; ci < 2; ci++) {
             std::vector<long long> c = chunk_prefix(CWs[ci]);
             RB_CK(cudaMemcpyAsync(dch, c.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm), "copy chunks");
-            for (int v = 0; v < 6; v++) {
+            for (int v = v0; v < v0 + 6; v++) {
                 int g = rbk::bsweep_grid(v, ctx->device);
                 float ms = 0.f;
                 for (int rep = 0; rep < 2; rep++) {
@@ -609,8 +638,8 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
                     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
                 }
                 if (rb_log_level() > 0)
-                    fprintf(stderr, "rb autotune: U=%d threads=%d CW=%d  %.3f ms\n", (int[]){2, 4, 8}[v % 3],
-                            rbk::bsweep_threads(v), CWs[ci], ms);
+                    fprintf(stderr, "rb autotune: %s U=%d threads=%d CW=%d  %.3f ms\n",
+                            presplit ? "hi/lo" : "complex128", 2 << (v % 3), rbk::bsweep_threads(v), CWs[ci], ms);
                 if (ms < best_ms) {
                     best_ms = ms;
                     best_v = v;
@@ -627,8 +656,19 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
     const int gv = rbk::bsweep_grid(best_v, ctx->device);
     for (int b = 0; b < nprob; b++) RB_CK(cudaMemsetAsync(pp[b].st, 0, sizeof(rbk::DevState), sm), "memset state");
     RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
-    RB_CK(rbk::launch_bnorms(dP, nprob, dcol, total_cols, sm), "norms");
-    int nlaunch = 1;
+    int nlaunch = 0;
+    if (presplit) {
+        // timed region starts after the copy made for tuning: redo it here
+        for (int b = 0; b < nprob; b++) {
+            RB_CK(rbk::launch_split(pp[b].S, probs[b].N, probs[b].M, probs[b].ldS, (float2 *)bp[b].hi,
+                                    (float2 *)bp[b].lo, ldHs[b], pp[b].norm2, sm),
+                  "split");
+            nlaunch++;
+        }
+    } else {
+        RB_CK(rbk::launch_bnorms(dP, nprob, dcol, total_cols, sm), "norms");
+        nlaunch++;
+    }
     for (int b = 0; b < nprob; b++) {
         RB_CK(rbk::launch_init(pp[b], G, sm), "init");
         nlaunch++;

@@ -4,10 +4,11 @@
 // column ranges of all problems are cut into chunks of CW columns, the chunks
 // are numbered across problems (prefix sums), and each block takes chunks in
 // a grid-stride loop, finds their problem by binary search, and streams the
-// columns warp by warp.  Snapshots are read as complex128 and split into
-// hi/lo FP32 pairs in registers (integer round-to-nearest split), so the
-// batch needs no second copy of its data; the dot products are the FP64
-// form's double-float arithmetic.  Per-chunk argmax partials are reduced per
+// columns warp by warp.  When a hi/lo copy of the batch fits in free device
+// memory the sweep streams it (16 bytes per element, as the FP64 form);
+// otherwise it reads complex128 and splits each element into hi/lo FP32 pairs
+// in registers (integer round-to-nearest split), needing no copy.  Either way
+// the dot products are the FP64 form's double-float arithmetic.  Per-chunk argmax partials are reduced per
 // problem by a second small kernel, which also applies each problem's own
 // stopping rule; stopped problems' chunks return at once.
 //
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_bnorms(const BProb *__restrict__ P
     }
 }
 
-template <int U, int THREADS>
+template <int U, int THREADS, bool SPLIT>
 __global__ void __launch_bounds__(THREADS) k_bsweep(const BProb *__restrict__ P, int nprob,
                                                     const long long *__restrict__ chunk0, int CW,
                                                     double *__restrict__ part_err, long long *__restrict__ part_idx,
@@ -149,7 +150,8 @@ __global__ void __launch_bounds__(THREADS) k_bsweep(const BProb *__restrict__ P,
             double be = -INFINITY;
             long long bi = kNoIdx;
             for (long long j = j0 + warp; j < j1; j += NW) {
-                double2 c = col_dot_c128<U>(pr.S + j * pr.ldS, pr.qh, pr.ql, pr.N, lane);
+                double2 c = SPLIT ? col_dot_df32<U>(pr.hi + j * pr.ldH, pr.lo + j * pr.ldH, pr.qh, pr.ql, pr.N, lane)
+                                  : col_dot_c128<U>(pr.S + j * pr.ldS, pr.qh, pr.ql, pr.N, lane);
                 if (lane == 0) {
                     if (dry) {
                         if (better(c.x, j, be, bi)) { be = c.x; bi = j; }
@@ -218,16 +220,19 @@ cudaError_t launch_bnorms(const BProb *P, int nprob, const long long *col0, long
     return cudaGetLastError();
 }
 
-// variant index v: U = {2, 4, 8}[v % 3], THREADS = {128, 256}[(v / 3) % 2]
+// variant index v: U = {2, 4, 8}[v % 3], THREADS = {128, 256}[(v / 3) % 2],
+// v >= 6: the sweep reads a pre-split hi/lo copy instead of complex128.
+#define RB_BSWEEP_CASES(X)                                                                             \
+    X(0, 2, 128, false) X(1, 4, 128, false) X(2, 8, 128, false) X(3, 2, 256, false) X(4, 4, 256, false) \
+    X(5, 8, 256, false) X(6, 2, 128, true) X(7, 4, 128, true) X(8, 8, 128, true) X(9, 2, 256, true)     \
+    X(10, 4, 256, true) X(11, 8, 256, true)
+
 static void *bsweep_fn(int v) {
-    switch (v) {
-    case 0: return (void *)k_bsweep<2, 128>;
-    case 1: return (void *)k_bsweep<4, 128>;
-    case 2: return (void *)k_bsweep<8, 128>;
-    case 3: return (void *)k_bsweep<2, 256>;
-    case 4: return (void *)k_bsweep<4, 256>;
-    default: return (void *)k_bsweep<8, 256>;
-    }
+#define RB_FN(i, u, t, sp) \
+    if (v == i) return (void *)k_bsweep<u, t, sp>;
+    RB_BSWEEP_CASES(RB_FN)
+#undef RB_FN
+    return (void *)k_bsweep<4, 256, false>;
 }
 
 int bsweep_threads(int v) { return (v / 3) % 2 ? 256 : 128; }
@@ -242,15 +247,10 @@ int bsweep_grid(int v, int device) {
 
 cudaError_t launch_bsweep(int v, int grid, const BProb *P, int nprob, const long long *chunk0, int CW,
                           double *part_err, long long *part_idx, int dry, cudaStream_t s) {
-    int t = bsweep_threads(v);
-    switch (v) {
-    case 0: k_bsweep<2, 128><<<grid, t, 0, s>>>(P, nprob, chunk0, CW, part_err, part_idx, dry); break;
-    case 1: k_bsweep<4, 128><<<grid, t, 0, s>>>(P, nprob, chunk0, CW, part_err, part_idx, dry); break;
-    case 2: k_bsweep<8, 128><<<grid, t, 0, s>>>(P, nprob, chunk0, CW, part_err, part_idx, dry); break;
-    case 3: k_bsweep<2, 256><<<grid, t, 0, s>>>(P, nprob, chunk0, CW, part_err, part_idx, dry); break;
-    case 4: k_bsweep<4, 256><<<grid, t, 0, s>>>(P, nprob, chunk0, CW, part_err, part_idx, dry); break;
-    default: k_bsweep<8, 256><<<grid, t, 0, s>>>(P, nprob, chunk0, CW, part_err, part_idx, dry); break;
-    }
+#define RB_LAUNCH(i, u, t, sp) \
+    if (v == i) k_bsweep<u, t, sp><<<grid, t, 0, s>>>(P, nprob, chunk0, CW, part_err, part_idx, dry);
+    RB_BSWEEP_CASES(RB_LAUNCH)
+#undef RB_LAUNCH
     return cudaGetLastError();
 }
 

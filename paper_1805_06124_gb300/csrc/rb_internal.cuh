@@ -104,6 +104,9 @@ struct BProb {
     int pad;
     long long minNM;
     double tol;
+    const float2 *hi;  // pre-split copy (null: split in registers)
+    const float2 *lo;
+    long long ldH;
 };
 
 // ---------------------------------------------------------------- argmax key
@@ -277,6 +280,61 @@ __device__ __forceinline__ void df_sq(float &sh, float &sl, float h, float l) {
     two_sum(sh, p, s, t);
     sh = s;
     sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
+// Double-float product of a conjugated basis element (hi + lo parts) with a
+// snapshot element (hi + lo parts), accumulated into (re_h, re_l), (im_h, im_l):
+//   Re += qr*sr + qi*si,  Im += qr*si - qi*sr.
+__device__ __forceinline__ void df_cmac(float &rh, float &rl, float &ih, float &il, float qrh, float qih, float qrl,
+                                        float qil, float srh, float sih, float srl, float sil) {
+    df_mac(rh, rl, qrh, qrl, srh, srl);
+    df_mac(rh, rl, qih, qil, sih, sil);
+    df_mac(ih, il, qrh, qrl, sih, sil);
+    df_mac(ih, il, -qih, -qil, srh, srl);
+}
+
+// Column dot product c = q^H s_j over the hi/lo split storage (double-float);
+// U 128-bit loads of hi and of lo in flight per lane.
+template <int U = 4>
+__device__ __forceinline__ double2 col_dot_df32(const float2 *__restrict__ hcol, const float2 *__restrict__ lcol,
+                                                const float2 *__restrict__ qh, const float2 *__restrict__ ql,
+                                                long long N, int lane) {
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const float4 *h4 = reinterpret_cast<const float4 *>(hcol);
+    const float4 *l4 = reinterpret_cast<const float4 *>(lcol);
+    const float4 *qh4 = reinterpret_cast<const float4 *>(qh);
+    const float4 *ql4 = reinterpret_cast<const float4 *>(ql);
+    long long n2 = N >> 1;  // complex pairs
+    long long t = lane;
+    for (; t + 32 * (U - 1) < n2; t += 32 * U) {
+        float4 a[U], b[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            a[u] = ld_stream(h4 + t + 32 * u);
+            b[u] = ld_stream(l4 + t + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            float4 qa = __ldg(qh4 + t + 32 * u);
+            float4 qb = __ldg(ql4 + t + 32 * u);
+            df_cmac(rh, rl, ih, il, qa.x, qa.y, qb.x, qb.y, a[u].x, a[u].y, b[u].x, b[u].y);
+            df_cmac(rh, rl, ih, il, qa.z, qa.w, qb.z, qb.w, a[u].z, a[u].w, b[u].z, b[u].w);
+        }
+    }
+    for (; t < n2; t += 32) {
+        float4 a = ld_stream(h4 + t), b = ld_stream(l4 + t);
+        float4 qa = __ldg(qh4 + t), qb = __ldg(ql4 + t);
+        df_cmac(rh, rl, ih, il, qa.x, qa.y, qb.x, qb.y, a.x, a.y, b.x, b.y);
+        df_cmac(rh, rl, ih, il, qa.z, qa.w, qb.z, qb.w, a.z, a.w, b.z, b.w);
+    }
+    if ((N & 1) && lane == 0) {
+        long long i = N - 1;
+        float2 a = hcol[i], b = lcol[i], qa = qh[i], qb = ql[i];
+        df_cmac(rh, rl, ih, il, qa.x, qa.y, qb.x, qb.y, a.x, a.y, b.x, b.y);
+    }
+    warp_df_sum(rh, rl);
+    warp_df_sum(ih, il);
+    return make_double2((double)rh + (double)rl, (double)ih + (double)il);
 }
 
 // Split with the intrinsic conversions when the fast path does not apply.

@@ -173,15 +173,14 @@ __host__ __device__ inline MlpLayout mlp_layout(int O) {
     return L;
 }
 
-// Glorot-uniform weights, zero biases.
+// Weights and biases of a layer with fan-in f uniform on [-1/sqrt(f), 1/sqrt(f)]:
+// the first layer's random biases spread its GELU kinks (at -b/w) across the
+// input range, which the oscillating coefficient map needs.
 __global__ void k_mlp_init(float *p, int O, unsigned long long seed) {
     MlpLayout L = mlp_layout(O);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.n; i += (long long)gridDim.x * blockDim.x) {
-        float a = 0.f;
-        if (i < L.b1) a = sqrtf(6.f / (2 + MW));
-        else if (i >= L.w2 && i < L.b2) a = sqrtf(6.f / (MW + MW));
-        else if (i >= L.w3 && i < L.b3) a = sqrtf(6.f / (MW + MW));
-        else if (i >= L.w4 && i < L.b4) a = sqrtf(6.f / (MW + O));
+        float fan_in = i < L.w2 ? 2.f : (float)MW;
+        float a = rsqrtf(fan_in);
         unsigned long long r = splitmix64(seed ^ (unsigned long long)(i * 0x2545F4914F6CDD1Dull));
         float u = (float)((r >> 40) * (1.0 / 16777216.0));  // [0, 1)
         p[i] = a * (2.f * u - 1.f);
