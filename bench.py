@@ -146,6 +146,129 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def split_vs_fp64(torch, rb, synth, dev, stream, N=16384, M=196608, tol=1e-10, reps=3):
+    """Time to basis of the FP64 form (complex128 input) and of the split form
+    (hi/lo input) on the same chirps, seed 2; returns the ratio and both curves'
+    agreement."""
+    import numpy as np
+    c = rb.RB(device=dev, stream=stream)
+    q, m = synth.chirp_params(M, 2)
+    with torch.cuda.stream(stream):
+        S = c.generate(q, m, N)
+        hi, lo = c.split(S)
+    stream.synchronize()
+    res = {}
+    for name in ("fp64", "split"):
+        f = (lambda: c.greedy(S, tol, 800)) if name == "fp64" else (lambda: c.greedy_split(hi, lo, tol, 800))
+        with torch.cuda.stream(stream):
+            r = f()
+            ts = []
+            for _ in range(reps):
+                r = f()
+                ts.append(r["ms_total"])
+        res[name] = dict(ms=float(np.median(ts)), k=r["k"], err_curve=r["err_curve"].cpu().numpy(),
+                         switch_iter=r["switch_iter"], final_max=float(r["final_err"].max()))
+    c.close()
+    del S, hi, lo
+    n = min(len(res["fp64"]["err_curve"]), len(res["split"]["err_curve"]))
+    return {"workload": f"chirps N={N} x M={M} seed 2, tol {tol}; FP64 form reads complex128, split form reads "
+                        "complex64 hi+lo (prepared by rb_split, not timed)",
+            "fp64_ms": round(res["fp64"]["ms"], 2), "split_ms": round(res["split"]["ms"], 2),
+            "ratio": round(res["fp64"]["ms"] / res["split"]["ms"], 3),
+            "k_fp64": res["fp64"]["k"], "k_split": res["split"]["k"], "switch_iter": res["split"]["switch_iter"],
+            "max_abs_err_curve_diff": float(np.max(np.abs(res["fp64"]["err_curve"][:n] - res["split"]["err_curve"][:n]))),
+            "split_final_max_err": res["split"]["final_max"]}
+
+
+def batched_run(torch, rb, synth, dev, stream, nprob=96, seed=3, tol=1e-10, reps=2):
+    """The 96-problem batched workload: aggregate sweep GB/s and problems/s."""
+    import numpy as np
+    probs, used = synth.batched_problems(nprob, seed)
+    c = rb.RB(device=dev, stream=stream)
+    Ss = []
+    with torch.cuda.stream(stream):
+        for p in probs:
+            q, m = synth.chirp_params(p["M"], p["seed"], q_range=p["q_range"], m_range=p["m_range"])
+            Ss.append(c.generate(q, m, p["N"]))
+        outs = c.greedy_batched(Ss, tol, 300, want_C=False, want_final_err=False)  # includes autotuning
+        ts, by = [], 0.0
+        for _ in range(reps):
+            outs = c.greedy_batched(Ss, tol, 300, want_C=False, want_final_err=False)
+            ts.append(outs[0]["ms_total"])
+            by = sum(o["sweep_bytes"] for o in outs)
+    ms = float(np.median(ts))
+    ks = [o["k"] for o in outs]
+    total = sum(16.0 * p["N"] * p["M"] for p in probs)
+    c.close()
+    del Ss
+    return {"workload": f"{nprob} chirp problems, N~logU[512,8192], M~logU[4096,131072], seed {used}, "
+                        f"{total / 1e9:.1f} GB complex128, tol {tol}",
+            "ms": round(ms, 2), "sweep_GBps": round(by / ms / 1e6, 1), "problems_per_s": round(nprob / ms * 1e3, 2),
+            "k_min": min(ks), "k_max": max(ks), "gpu_launches": outs[0]["n_launches"]}
+
+
+def run_surrogate(args):
+    """Learned surrogate: greedy on N=8192 x M=131072 chirps (seed 4, tol 1e-10),
+    MLP on its C, 16384 held-out (seed 5) judged by exact projection."""
+    import numpy as np
+    import torch
+    from paper_1805_06124_gb300 import rb, surrogate, synth
+    N, M, Mt = 8192, 131072, 16384
+    stream = torch.cuda.Stream()
+    c = rb.RB(device=0, stream=stream)
+    q, m = synth.chirp_params(M, 4)
+    qt, mt = synth.chirp_params(Mt, 5)
+    with torch.cuda.stream(stream):
+        S = c.generate(q, m, N)
+        g = c.greedy(S, 1e-10, 800)
+        St = c.generate(qt, mt, N)
+    stream.synchronize()
+    k = g["k"]
+    del S
+    net, curve, t_train = surrogate.train(c, q, m, g["C"], epochs=args.epochs, batch=1024, lr=1e-3, seed=4)
+    Xt = surrogate.scale_inputs(qt, mt).cuda()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        Y = net.infer(Xt)
+        ev0.record(stream)
+        Y = net.infer(Xt)
+        ev1.record(stream)
+    stream.synchronize()
+    t_mlp = ev0.elapsed_time(ev1)
+    q_t, m_t = torch.as_tensor(qt, device="cuda"), torch.as_tensor(mt, device="cuda")
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        St2 = c.generate(q_t, m_t, N)
+        Ct = c.project(g["Q"], St2)
+        ev1.record(stream)
+    stream.synchronize()
+    t_exact = ev0.elapsed_time(ev1)
+    Tt = surrogate.targets_from_C(Ct)
+    rel_e, abs_e = surrogate.relative_errors(Y, Tt)
+    # non-learned baseline: coefficients of the training snapshot nearest in omega
+    om = torch.as_tensor(synth.chirp_omega(q, m), device="cuda")
+    omt = torch.as_tensor(synth.chirp_omega(qt, mt), device="cuda")
+    order = torch.argsort(om)
+    pos = torch.searchsorted(om[order], omt).clamp(1, M - 1)
+    left, right = order[pos - 1], order[pos]
+    nn = torch.where((omt - om[left]).abs() <= (om[right] - omt).abs(), left, right)
+    Ttrain = surrogate.targets_from_C(g["C"])
+    rel_nn, _ = surrogate.relative_errors(Ttrain[nn], Tt)
+    line = {"impl": "ours", "metric": "surrogate coefficient relative error vs exact projection (median)",
+            "value": round(surrogate.summarize(rel_e)["median"], 5), "unit": "relative L2",
+            "higher_is_better": False, "data": "synthetic", "dtype": "bf16/f32",
+            "config": {"workload": f"MLP 2-256-256-256-{2 * k}, {M} training pairs from greedy on N={N} x M={M} "
+                                   f"chirps (seed 4, tol 1e-10, k={k}), {Mt} held-out (seed 5)",
+                       "epochs": args.epochs, "batch": 1024, "lr": 1e-3},
+            "mlp": surrogate.summarize(rel_e), "mlp_abs_waveform_err": surrogate.summarize(abs_e),
+            "nearest_training_column": surrogate.summarize(rel_nn), "zero_prediction": 1.0,
+            "final_train_loss": float(curve[-1]), "train_s": round(t_train, 2),
+            "infer_ms_per_16384": round(t_mlp, 3), "generate_plus_project_ms_per_16384": round(t_exact, 3)}
+    print(json.dumps(line), flush=True)
+    net.close()
+    c.close()
+
+
 def run_ours(args):
     import torch
     from paper_1805_06124_gb300 import rb, synth
@@ -215,7 +338,7 @@ def run_ours(args):
         Sh = torch.empty((M, N), dtype=torch.complex128, pin_memory=True)
         Sh.copy_(S)
         ctx_h = rb.RB(device=local, sweep=args.sweep, stream=stream)
-        del S
+        S = None
         torch.cuda.empty_cache()
         rh = ctx_h.greedy_host(Sh, TOL, KMAX)
         t0 = time.perf_counter()
@@ -231,6 +354,7 @@ def run_ours(args):
         e2e = {"value": round(byts / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": round(dt / nst * 1e3, 2)}
         ctx_h.close()
+        del Sh
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -239,6 +363,18 @@ def run_ours(args):
         cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"one full greedy on {CPU_SAMPLE_M} of {M} columns (N={N}, seed {SEED}, tol {TOL}), "
                          f"k={k_cpu}, {t_cpu:.1f} s"}
+
+    extra_split = extra_batched = None
+    if rank == 0 and world == 1:
+        ctx.close()
+        S = None
+        torch.cuda.empty_cache()
+        if not args.no_split:
+            extra_split = split_vs_fp64(torch, rb, synth, local, stream)
+            torch.cuda.empty_cache()
+        if not args.no_batched:
+            extra_batched = batched_run(torch, rb, synth, local, stream)
+            torch.cuda.empty_cache()
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -255,9 +391,11 @@ def run_ours(args):
                              "kernel": "k_sweep (fused dot + bookkeeping + argmax)",
                              "traffic": (round(tpb * per_launch) if tpb else None),
                              "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": round(sweep_ms, 4)},
-                "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}
+                "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
+                "split_vs_fp64": extra_split, "batched": extra_batched}
         print(json.dumps(line), flush=True)
-    ctx.close()
+    if not (rank == 0 and world == 1):
+        ctx.close()
     if dist:
         dist.destroy_process_group()
 
@@ -273,8 +411,14 @@ def main():
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate"])
+    ap.add_argument("--epochs", type=int, default=200)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.workload == "surrogate":
+        run_surrogate(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
