@@ -29,8 +29,8 @@
  *     are borrowed: the caller allocates them (outputs at capacity kmax) and
  *     keeps them valid until the call returns.  Inputs are never modified.
  *   - Calls are issued on the context's stream.  The greedy entry points
- *     synchronise that stream before returning (they return k and a status);
- *     rb_generate, rb_split and rb_project are asynchronous.
+ *     synchronise that stream before returning (they return k and a status),
+ *     as does rb_project; rb_generate and rb_split are asynchronous.
  *   - Return value: 0 = success, > 0 = warning (outputs valid), < 0 = error
  *     (outputs unspecified).  rb_last_error() describes the last failure.
  *     No call aborts the process or traps on the device; device-side waits
@@ -67,7 +67,8 @@ enum {
 };
 
 /* rb_options.flags */
-#define RB_FLAG_TIMING 1u   /* time every sweep launch with CUDA events (fills rb_result.ms_sweep) */
+#define RB_FLAG_TIMING 1u        /* time every sweep launch with CUDA events (fills rb_result.ms_sweep) */
+#define RB_FLAG_PROJECT_FP64 2u  /* rb_project on the plain-FP64 CUDA-core kernel instead of the tensor cores */
 
 typedef struct rb_options {
     int device;            /* CUDA device ordinal */
@@ -188,8 +189,13 @@ rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, l
 /* Projection onto a basis: C[l*ldC + j] = q_l^H x_j for l < k, j < Mx
  * (Sec. 2: a column is represented by its orthogonal projection onto the
  * span of the basis).  Q: complex128 N x k (ldQ >= N); X: complex128 N x Mx
- * (ldX >= N); C: complex128 row-major k x Mx (ldC >= Mx).  FP64-accurate.
- * Errors: RB_EINVAL, RB_ECUDA. */
+ * (ldX >= N); C: complex128 row-major k x Mx (ldC >= Mx).  FP64-accurate on
+ * the BF16 tensor cores: every value is split into seven 7-bit slices under a
+ * per-row power-of-two scale, the 28 leading slice products accumulate per
+ * level in TMEM (exact in FP32 over 512-term chunks) and are summed in
+ * double-float; error a few 2^-48 max|q_l| max|x_j| N.  Synchronises the
+ * stream (RB_FLAG_PROJECT_FP64 selects a plain FP64 kernel, asynchronous).
+ * Errors: RB_EINVAL, RB_ECUDA, RB_ENOMEM, RB_ETIMEOUT. */
 rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ,
                      const void *X, long long Mx, long long ldX, void *C, long long ldC);
 

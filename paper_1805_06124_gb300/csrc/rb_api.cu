@@ -204,9 +204,32 @@ rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long l
         !aligned(Q, 16) || !aligned(X, 16) || !aligned(C, 16))
         return fail(ctx, RB_EINVAL, "rb_project: bad arguments (N=%lld k=%d Mx=%lld)", N, k, Mx);
     RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    RB_CK(rbk::launch_project((const double2 *)Q, N, k, ldQ, (const double2 *)X, Mx, ldX, (double2 *)C, ldC,
-                              ctx->stream),
-          "project");
+    if (k == 0 || Mx == 0) return RB_OK;
+    if (ctx->opt.flags & RB_FLAG_PROJECT_FP64) {
+        RB_CK(rbk::launch_project((const double2 *)Q, N, k, ldQ, (const double2 *)X, Mx, ldX, (double2 *)C, ldC,
+                                  ctx->stream),
+              "project");
+        return RB_OK;
+    }
+    // tensor-core path, in column batches whose slice planes stay under ~4 GB
+    long long Mb = Mx;
+    while (Mb > 64 && rbk::oz_workspace(N, k, Mb) > (4ull << 30)) Mb = (Mb + 1) / 2;
+    const size_t need = rbk::oz_workspace(N, k, Mb) + 256;
+    rb_status s = ensure(ctx, &ctx->gen, &ctx->gen_cap, need);
+    if (s != RB_OK) return s;
+    int *err = (int *)((char *)ctx->gen + need - 256);
+    cudaStream_t sm = ctx->stream;
+    RB_CK(cudaMemsetAsync(err, 0, sizeof(int), sm), "memset flag");
+    for (long long c0 = 0; c0 < Mx; c0 += Mb) {
+        long long nb = Mx - c0 < Mb ? Mx - c0 : Mb;
+        RB_CK(rbk::launch_project_tc((const double2 *)Q, N, k, ldQ, (const double2 *)X + c0 * ldX, nb, ldX,
+                                     (double2 *)C, ldC, c0, ctx->gen, err, sm),
+              "project (tensor cores)");
+    }
+    int herr = 0;
+    RB_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, sm), "flag copy");
+    RB_CK(cudaStreamSynchronize(sm), "stream sync");
+    if (herr) return fail(ctx, RB_ETIMEOUT, "rb_project: a tensor-core wait ran out");
     return RB_OK;
 }
 
@@ -365,6 +388,7 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     size_t o_bc = L.add((size_t)G * 4), o_cd = L.add((size_t)cand_cap * 8), o_ce = L.add((size_t)cand_cap * 8);
     size_t o_C = out->C ? 0 : L.add((size_t)kcap * M * sizeof(double2));
     size_t o_st = L.add(sizeof(rbk::DevState));
+    size_t o_te = L.add(sizeof(int));
     rb_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.off);
     if (s != RB_OK) return s;
     char *w = (char *)ctx->ws;
@@ -411,11 +435,13 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     p.cand_err = (double *)(w + o_ce);
     p.cand_cap = cand_cap;
     p.switch_err = o.switch_err;
+    p.tc_err = (int *)(w + o_te);
 
     cudaStream_t sm = ctx->stream;
     int nlaunch = 0;
     RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
     RB_CK(cudaMemsetAsync(p.st, 0, sizeof(rbk::DevState), sm), "memset state");
+    RB_CK(cudaMemsetAsync(p.tc_err, 0, sizeof(int), sm), "memset tc flag");
     RB_CK(rbk::launch_split_init(p, sm), "split init");
     RB_CK(rbk::launch_init(p, G, sm), "init");
     nlaunch += 2;
@@ -450,6 +476,9 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     out->n_sweeps = hs.n_sweeps;
     out->ms_total = ms;
     out->ms_sweep = 0.0;
+    int tc_err = 0;
+    RB_CK(cudaMemcpy(&tc_err, p.tc_err, sizeof(int), cudaMemcpyDeviceToHost), "tc flag");
+    if (tc_err) return fail(ctx, RB_ETIMEOUT, "rb_greedy_split: a tensor-core wait ran out");
     const int n0 = hs.phase ? hs.switch_iter : hs.k;
     const int n1 = hs.n_sweeps - n0;
     out->sweep_bytes = (double)n0 * (8.0 * N * M + 16.0 * N + 41.0 * M) + (double)n1 * (16.0 * N * M + 16.0 * N + 41.0 * M);

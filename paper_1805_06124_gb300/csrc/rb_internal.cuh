@@ -85,6 +85,7 @@ struct Prob {
     int nblk_cand;     // blocks of the candidate kernels
     int cand_cap;
     double switch_err;
+    int *tc_err;       // set when a tensor-core wait ran out
 };
 
 // One problem of a batch (rb_greedy_batched): what the persistent sweep and
@@ -362,6 +363,10 @@ cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s
 cudaError_t launch_final_err(const Prob &p, double *final_err, cudaStream_t s);
 cudaError_t launch_split_init(const Prob &p, cudaStream_t s);
 cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
+size_t oz_workspace(long long N, int k, long long Mb);
+cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mb,
+                              long long ldX, double2 *C, long long ldC, long long col_off, void *ws, int *err,
+                              cudaStream_t s);
 cudaError_t launch_project(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mx,
                            long long ldX, double2 *C, long long ldC, cudaStream_t s);
 int sweep_grid(int variant, int device);

@@ -24,6 +24,7 @@
 //
 // Phase 1 (hi + lo, 16 bytes per element): the FP64 form's double-float sweep.
 #include "rb_internal.cuh"
+#include "rb_tc.cuh"
 
 namespace rbk {
 
@@ -71,6 +72,18 @@ __global__ void __launch_bounds__(kThreads) k_split_init(Prob p) {
 }
 
 // ------------------------------------------------------- phase 0 sweep
+// (sh, sl) += (ah + al) * b for an exact FP32 b: TwoProduct of ah*b by FMA,
+// the al*b term into the low part, TwoSum into the high part.
+__device__ __forceinline__ void df_mac1(float &sh, float &sl, float ah, float al, float b) {
+    float p = __fmul_rn(ah, b);
+    float e = __fmaf_rn(ah, b, -p);
+    e = __fmaf_rn(al, b, e);
+    float s, t;
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
 // c_hi = q^H hi with q = qh + ql (double-float), hi exact.
 __device__ __forceinline__ double2 col_dot_hi(const float2 *__restrict__ hcol, const float2 *__restrict__ qh,
                                               const float2 *__restrict__ ql, long long N, int lane) {
@@ -88,34 +101,34 @@ __device__ __forceinline__ double2 col_dot_hi(const float2 *__restrict__ hcol, c
 #pragma unroll
         for (int u = 0; u < U; u++) {
             float4 qa = __ldg(qh4 + t + 32 * u), qb = __ldg(ql4 + t + 32 * u);
-            df_mac(rh, rl, qa.x, qb.x, a[u].x, 0.f);
-            df_mac(rh, rl, qa.y, qb.y, a[u].y, 0.f);
-            df_mac(ih, il, qa.x, qb.x, a[u].y, 0.f);
-            df_mac(ih, il, -qa.y, -qb.y, a[u].x, 0.f);
-            df_mac(rh, rl, qa.z, qb.z, a[u].z, 0.f);
-            df_mac(rh, rl, qa.w, qb.w, a[u].w, 0.f);
-            df_mac(ih, il, qa.z, qb.z, a[u].w, 0.f);
-            df_mac(ih, il, -qa.w, -qb.w, a[u].z, 0.f);
+            df_mac1(rh, rl, qa.x, qb.x, a[u].x);
+            df_mac1(rh, rl, qa.y, qb.y, a[u].y);
+            df_mac1(ih, il, qa.x, qb.x, a[u].y);
+            df_mac1(ih, il, -qa.y, -qb.y, a[u].x);
+            df_mac1(rh, rl, qa.z, qb.z, a[u].z);
+            df_mac1(rh, rl, qa.w, qb.w, a[u].w);
+            df_mac1(ih, il, qa.z, qb.z, a[u].w);
+            df_mac1(ih, il, -qa.w, -qb.w, a[u].z);
         }
     }
     for (; t < n2; t += 32) {
         float4 a = ld_stream(h4 + t), qa = __ldg(qh4 + t), qb = __ldg(ql4 + t);
-        df_mac(rh, rl, qa.x, qb.x, a.x, 0.f);
-        df_mac(rh, rl, qa.y, qb.y, a.y, 0.f);
-        df_mac(ih, il, qa.x, qb.x, a.y, 0.f);
-        df_mac(ih, il, -qa.y, -qb.y, a.x, 0.f);
-        df_mac(rh, rl, qa.z, qb.z, a.z, 0.f);
-        df_mac(rh, rl, qa.w, qb.w, a.w, 0.f);
-        df_mac(ih, il, qa.z, qb.z, a.w, 0.f);
-        df_mac(ih, il, -qa.w, -qb.w, a.z, 0.f);
+        df_mac1(rh, rl, qa.x, qb.x, a.x);
+        df_mac1(rh, rl, qa.y, qb.y, a.y);
+        df_mac1(ih, il, qa.x, qb.x, a.y);
+        df_mac1(ih, il, -qa.y, -qb.y, a.x);
+        df_mac1(rh, rl, qa.z, qb.z, a.z);
+        df_mac1(rh, rl, qa.w, qb.w, a.w);
+        df_mac1(ih, il, qa.z, qb.z, a.w);
+        df_mac1(ih, il, -qa.w, -qb.w, a.z);
     }
     if ((N & 1) && lane == 0) {
         long long i = N - 1;
         float2 a = hcol[i], qa = qh[i], qb = ql[i];
-        df_mac(rh, rl, qa.x, qb.x, a.x, 0.f);
-        df_mac(rh, rl, qa.y, qb.y, a.y, 0.f);
-        df_mac(ih, il, qa.x, qb.x, a.y, 0.f);
-        df_mac(ih, il, -qa.y, -qb.y, a.x, 0.f);
+        df_mac1(rh, rl, qa.x, qb.x, a.x);
+        df_mac1(rh, rl, qa.y, qb.y, a.y);
+        df_mac1(ih, il, qa.x, qb.x, a.y);
+        df_mac1(ih, il, -qa.y, -qb.y, a.x);
     }
     warp_df_sum(rh, rl);
     warp_df_sum(ih, il);
@@ -260,39 +273,82 @@ __global__ void __launch_bounds__(kThreads) k_cand_write(Prob p) {
 }
 
 // Exact error of each candidate: err_j = ||hi_j + lo_j||^2 - sum_l |c_hi,lj + q_l^H lo_j|^2.
+// One block per candidate; the block sweeps the rows once per group of 8 basis
+// vectors (8 complex FP32 dots per thread), the candidate's lo column staying
+// in L1 between groups.
+constexpr int RG = 8;
+
 __global__ void __launch_bounds__(kThreads) k_recheck(Prob p) {
     DevState *st = p.st;
     if (!recheck_active(st)) return;
     __shared__ int s_total;
+    __shared__ float red[2 * RG][kThreads / 32];
+    __shared__ double s_acc;
+    __shared__ double vals[RG];
     if (threadIdx.x == 0) {
         int t = 0;
         for (int b = 0; b < p.nblk_cand; b++) t += __ldcg(p.bcount + b);
         s_total = t;
+        s_acc = 0.0;
     }
     __syncthreads();
     const int total = s_total;
     const int n = total < p.cand_cap ? total : p.cand_cap;
     const int k1 = st->k;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if ((int)blockIdx.x < n) {
         const long long j = p.cand[blockIdx.x];
         const float2 *lcol = p.lo + j * p.ldH;
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-        double accp = 0.0;
-        for (int l = w; l < k1; l += nwarp) {
-            const float2 *q = p.qh + (long long)l * p.qs_stride;
-            float re = 0.f, im = 0.f;
-            for (long long i = lane; i < p.N; i += 32) {
-                float2 a = q[i], b = lcol[i];
-                re = fmaf(a.x, b.x, fmaf(a.y, b.y, re));
-                im = fmaf(a.x, b.y, fmaf(-a.y, b.x, im));
+        for (int l0 = 0; l0 < k1; l0 += RG) {
+            float re[RG], im[RG];
+#pragma unroll
+            for (int g = 0; g < RG; g++) re[g] = im[g] = 0.f;
+            for (long long i = threadIdx.x; i < p.N; i += blockDim.x) {
+                float2 b = lcol[i];
+#pragma unroll
+                for (int g = 0; g < RG; g++) {
+                    if (l0 + g < k1) {
+                        float2 a = p.qh[(long long)(l0 + g) * p.qs_stride + i];
+                        re[g] = fmaf(a.x, b.x, fmaf(a.y, b.y, re[g]));
+                        im[g] = fmaf(a.x, b.y, fmaf(-a.y, b.x, im[g]));
+                    }
+                }
             }
-            double dre = warp_sum((double)re), dim = warp_sum((double)im);
-            double2 c = p.C[(long long)l * p.ldC + j];
-            double cr = c.x + dre, ci = c.y + dim;
-            accp += cr * cr + ci * ci;
+#pragma unroll
+            for (int g = 0; g < RG; g++) {
+                float r = re[g], m = im[g];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    r += __shfl_xor_sync(0xffffffffu, r, o);
+                    m += __shfl_xor_sync(0xffffffffu, m, o);
+                }
+                if (lane == 0) {
+                    red[2 * g][w] = r;
+                    red[2 * g + 1][w] = m;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < RG) {
+                int g = threadIdx.x;
+                double v = 0.0;
+                if (l0 + g < k1) {
+                    double dre = 0.0, dim = 0.0;
+                    for (int x = 0; x < (int)(blockDim.x >> 5); x++) {
+                        dre += (double)red[2 * g][x];
+                        dim += (double)red[2 * g + 1][x];
+                    }
+                    double2 c = p.C[(long long)(l0 + g) * p.ldC + j];
+                    double cr = c.x + dre, ci = c.y + dim;
+                    v = cr * cr + ci * ci;
+                }
+                vals[g] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int g = 0; g < RG; g++) s_acc += vals[g];  // fixed order
+            __syncthreads();
         }
-        double acc = block_sum(lane == 0 ? accp : 0.0);
-        if (threadIdx.x == 0) p.cand_err[blockIdx.x] = p.norm2[j] - acc;
+        if (threadIdx.x == 0) p.cand_err[blockIdx.x] = p.norm2[j] - s_acc;
     }
     if (!last_block(&st->ticket_aux)) return;
     double be = -INFINITY;
@@ -316,96 +372,159 @@ __global__ void __launch_bounds__(kThreads) k_recheck(Prob p) {
 }
 
 // ------------------------------------------------------- projection onto lo
-// d = Qh^H lo for the k1 basis vectors, C[l, j] += d, acc_j = sum_l |C[l, j]|^2,
-// then the exact argmax and the stopping rule.  Tiled FP32 complex GEMM:
-// a block owns 64 columns and up to 64 basis vectors at a time, staging 32
-// rows of both operands in shared memory.
-constexpr int RJ = 64, RL = 64, RK = 32;
+// d = Qh^H lo for the k1 basis vectors on the tensor cores, then C[l, j] += d.
+// As a real GEMM with K = 2N interleaved (re, im): A rows 2l = (a_i, b_i) and
+// 2l+1 = (-b_i, a_i) for q_l = a + ib; B row j = (u_i, v_i) for lo_j = u + iv.
+// Every FP32 value is split exactly into three BF16 pieces (x = x1 + x2 + x3);
+// the six piece products with s + t <= 4 accumulate into one FP32 TMEM
+// accumulator, which leaves a relative error of a few 2^-24 -- what d needs,
+// since |lo| <= 2^-24 |s|.
+constexpr int PT = 128;  // tile rows (A) and columns (B)
+constexpr int PKC = 64;  // K per stage
+constexpr int PSL = 3;   // BF16 pieces per FP32 value
 
-__global__ void __launch_bounds__(kThreads) k_rebase(Prob p) {
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 *o) {
+    __nv_bfloat16 x1 = __float2bfloat16_rn(x);
+    float r = x - __bfloat162float(x1);
+    __nv_bfloat16 x2 = __float2bfloat16_rn(r);
+    r -= __bfloat162float(x2);
+    o[0] = x1;
+    o[1] = x2;
+    o[2] = __float2bfloat16_rn(r);
+}
+
+// Stage 8 consecutive K entries (4 complex elements) of one tile row into the
+// three piece tiles: one 16-byte core-matrix row per piece.
+__device__ __forceinline__ void stage_row8(uint8_t *base, int r, int kk, const float v[8]) {
+    __nv_bfloat16 pc[PSL][8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        __nv_bfloat16 o[PSL];
+        split3(v[e], o);
+#pragma unroll
+        for (int s = 0; s < PSL; s++) pc[s][e] = o[s];
+    }
+#pragma unroll
+    for (int s = 0; s < PSL; s++)
+        *(uint4 *)(base + s * (PT * PKC * 2) + kmajor_off(r, kk, PKC)) = *(const uint4 *)pc[s];
+}
+
+__global__ void __launch_bounds__(128) k_lo_project_tc(Prob p, int *err) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop) || !ld_volatile(&st->switch_pending)) return;
     const int k1 = st->k;
-    __shared__ float2 qs[RL][RK + 1];
-    __shared__ float2 ls[RJ][RK + 1];
-    __shared__ double accs[RJ];
-    __shared__ double parts[16][RJ];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 4 columns x 4 vectors per thread
-    double be = -INFINITY;
-    long long bi = kNoIdx;
-    for (long long j0 = (long long)blockIdx.x * RJ; j0 < p.M; j0 += (long long)gridDim.x * RJ) {
-        if (threadIdx.x < RJ) accs[threadIdx.x] = 0.0;
-        for (int l0 = 0; l0 < k1; l0 += RL) {
-            float dr[4][4], di[4][4];
+    const int r0 = blockIdx.y * PT;  // first A row of this tile
+    if (r0 >= 2 * k1) return;
+    extern __shared__ __align__(1024) uint8_t dsm[];
+    uint8_t *sA = dsm, *sB = dsm + PSL * PT * PKC * 2;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    const int warp = threadIdx.x >> 5;
+    const long long j0 = (long long)blockIdx.x * PT;
+    if (warp == 0) tmem_alloc(&tslot, PT);
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    constexpr uint32_t idesc = idesc_bf16_f32(PT, PT);
+    const long long K = 2 * p.N;
+    uint32_t phase = 0;
+    bool ok = true;
+    int nst = 0;
+    for (long long k0 = 0; k0 < K; k0 += PKC, nst++) {
+        // A: 128 rows x 64 K; each thread fills (row, 8 K) pieces, 8 per thread
+        for (int t = threadIdx.x; t < PT * (PKC / 8); t += blockDim.x) {
+            int r = t / (PKC / 8), kk = (t % (PKC / 8)) * 8;
+            int gr = r0 + r;
+            float v[8];
+            long long i0 = (k0 + kk) >> 1;  // first complex element
 #pragma unroll
-            for (int a = 0; a < 4; a++)
-#pragma unroll
-                for (int b = 0; b < 4; b++) dr[a][b] = di[a][b] = 0.f;
-            for (long long i0 = 0; i0 < p.N; i0 += RK) {
-                __syncthreads();
-                for (int t = threadIdx.x; t < RL * RK; t += blockDim.x) {
-                    int r = t / RK, c = t % RK;
-                    long long i = i0 + c;
-                    qs[r][c] = (l0 + r < k1 && i < p.N) ? p.qh[(long long)(l0 + r) * p.qs_stride + i]
-                                                        : make_float2(0.f, 0.f);
-                    ls[r][c] = (j0 + r < p.M && i < p.N) ? p.lo[(j0 + r) * p.ldH + i] : make_float2(0.f, 0.f);
-                }
-                __syncthreads();
-#pragma unroll 4
-                for (int c = 0; c < RK; c++) {
-                    float2 q[4], x[4];
-#pragma unroll
-                    for (int a = 0; a < 4; a++) q[a] = qs[ty * 4 + a][c];
-#pragma unroll
-                    for (int b = 0; b < 4; b++) x[b] = ls[tx * 4 + b][c];
-#pragma unroll
-                    for (int a = 0; a < 4; a++)
-#pragma unroll
-                        for (int b = 0; b < 4; b++) {
-                            dr[a][b] = fmaf(q[a].x, x[b].x, fmaf(q[a].y, x[b].y, dr[a][b]));
-                            di[a][b] = fmaf(q[a].x, x[b].y, fmaf(-q[a].y, x[b].x, di[a][b]));
-                        }
-                }
+            for (int e = 0; e < 4; e++) {
+                long long i = i0 + e;
+                float2 q = (gr < 2 * k1 && i < p.N) ? p.qh[(long long)(gr >> 1) * p.qs_stride + i] : make_float2(0.f, 0.f);
+                if ((gr & 1) == 0) { v[2 * e] = q.x; v[2 * e + 1] = q.y; }
+                else { v[2 * e] = -q.y; v[2 * e + 1] = q.x; }
             }
-            // fold d into C and the per-column sums
+            stage_row8(sA, r, kk, v);
+        }
+        // B: 128 columns x 64 K from lo
+        for (int t = threadIdx.x; t < PT * (PKC / 8); t += blockDim.x) {
+            int r = t / (PKC / 8), kk = (t % (PKC / 8)) * 8;
+            long long j = j0 + r;
+            float v[8];
+            long long i0 = (k0 + kk) >> 1;
 #pragma unroll
-            for (int b = 0; b < 4; b++) {
-                long long j = j0 + tx * 4 + b;
-                double part = 0.0;
-                if (j < p.M) {
+            for (int e = 0; e < 4; e++) {
+                long long i = i0 + e;
+                float2 x = (j < p.M && i < p.N) ? p.lo[j * p.ldH + i] : make_float2(0.f, 0.f);
+                v[2 * e] = x.x;
+                v[2 * e + 1] = x.y;
+            }
+            stage_row8(sB, r, kk, v);
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            int first = 1;
 #pragma unroll
-                    for (int a = 0; a < 4; a++) {
-                        int l = l0 + ty * 4 + a;
-                        if (l < k1) {
-                            double2 *cp = p.C + (long long)l * p.ldC + j;
-                            double2 c = *cp;
-                            c.x += (double)dr[a][b];
-                            c.y += (double)di[a][b];
-                            *cp = c;
-                            part += c.x * c.x + c.y * c.y;
-                        }
+            for (int sa = 0; sa < PSL; sa++)
+#pragma unroll
+                for (int sb = 0; sb < PSL; sb++) {
+                    if (sa + sb > 2) continue;  // pieces s + t <= 4 (0-based sa + sb <= 2)
+#pragma unroll
+                    for (int kk = 0; kk < PKC / 16; kk++) {
+                        uint64_t ad = smem_desc(smem_u32(sA) + sa * (PT * PKC * 2) + kk * 256, 128, (PKC / 8) * 128);
+                        uint64_t bd = smem_desc(smem_u32(sB) + sb * (PT * PKC * 2) + kk * 256, 128, (PKC / 8) * 128);
+                        tc_mma_bf16(tmem, ad, bd, idesc, (nst > 0 || !first) ? 1u : 0u);
+                        first = 0;
                     }
                 }
-                parts[ty][tx * 4 + b] = part;
-            }
-            __syncthreads();
-            if (threadIdx.x < RJ) {
-                double a = accs[threadIdx.x];
-                for (int g = 0; g < 16; g++) a += parts[g][threadIdx.x];  // fixed order
-                accs[threadIdx.x] = a;
+            tc_commit(&mbar);
+        }
+        ok = mbar_wait(&mbar, phase) && ok;
+        phase ^= 1;
+        tc_fence_after();
+        __syncthreads();
+    }
+    if (!ok) atomicExch(err, 1);
+    // epilogue: thread = A row (TMEM lane); row 2l adds to Re C[l, j], row 2l+1 to Im
+    const int r = r0 + threadIdx.x;
+    for (int c0 = 0; c0 < PT; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (r < 2 * k1) {
+            double *crow = (double *)(p.C + (long long)(r >> 1) * p.ldC) + (r & 1);
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                long long j = j0 + c0 + e;
+                if (j < p.M) crow[2 * j] += (double)v[e];
             }
         }
-        __syncthreads();
-        if (threadIdx.x < RJ) {
-            long long j = j0 + threadIdx.x;
-            if (j < p.M) {
-                double a = accs[threadIdx.x];
-                p.acc[j] = a;
-                double e = p.norm2[j] - a;
-                if (!p.picked[j] && better(e, j, be, bi)) { be = e; bi = j; }
-            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, PT);
+}
+
+// acc_j = sum_l |C[l, j]|^2 after the projection onto lo, the exact argmax,
+// the switch to the hi + lo phase and the stopping rule.
+__global__ void __launch_bounds__(kThreads) k_rebase_finish(Prob p) {
+    DevState *st = p.st;
+    if (ld_volatile(&st->stop) || !ld_volatile(&st->switch_pending)) return;
+    const int k1 = st->k;
+    double be = -INFINITY;
+    long long bi = kNoIdx;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < p.M; j += (long long)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int l = 0; l < k1; l++) {
+            double2 c = p.C[(long long)l * p.ldC + j];
+            a += c.x * c.x + c.y * c.y;
         }
-        __syncthreads();
+        p.acc[j] = a;
+        double e = p.norm2[j] - a;
+        if (!p.picked[j] && better(e, j, be, bi)) { be = e; bi = j; }
     }
     block_best(be, bi);
     if (threadIdx.x == 0) {
@@ -458,10 +577,18 @@ cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int 
     k_cand_count<<<grid, kThreads, 0, s>>>(p);
     k_cand_write<<<grid, kThreads, 0, s>>>(p);
     k_recheck<<<p.cand_cap, kThreads, 0, s>>>(p);
-    long long rb = (p.M + RJ - 1) / RJ;
-    if (rb > grid) rb = grid;
-    k_rebase<<<(int)rb, kThreads, 0, s>>>(p);
-    if (nlaunch) *nlaunch += 6;
+    const size_t dsmem = 2 * PSL * PT * PKC * 2;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_lo_project_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+        attr_set = true;
+    }
+    dim3 pg((unsigned)((p.M + PT - 1) / PT), (unsigned)((2LL * (p.kmax > 0 ? p.kmax : 1) + PT - 1) / PT));
+    k_lo_project_tc<<<pg, 128, dsmem, s>>>(p, p.tc_err);
+    long long rf = (p.M + kThreads - 1) / kThreads;
+    if (rf > grid) rf = grid;
+    k_rebase_finish<<<(int)rf, kThreads, 0, s>>>(p);
+    if (nlaunch) *nlaunch += 7;
     return cudaGetLastError();
 }
 

@@ -150,14 +150,36 @@ def test_split_bit_exact(orc, rbm):
     c.close()
 
 
-def test_project_parity(orc, rbm):
-    c = rbm.RB(device=0)
+def _tc_bound(Q, X):
+    """Stated accuracy of the tensor-core projection: a few 2^-48 of
+    max|q_l| max|x_j| (2N) per coefficient (16 taken here)."""
+    return 16 * 2.0 ** -48 * np.max(np.abs(Q)) * np.max(np.abs(X)) * 2 * Q.shape[1]
+
+
+@pytest.mark.parametrize("path", ["tensor_cores", "fp64"])
+def test_project_parity(orc, rbm, path):
+    c = rbm.RB(device=0, project_fp64=(path == "fp64"))
     rng = np.random.default_rng(0)
     Q = rng.standard_normal((37, 517)) + 1j * rng.standard_normal((37, 517))
     X = rng.standard_normal((333, 517)) + 1j * rng.standard_normal((333, 517))
     Cg = c.project(upload(Q), upload(X)).cpu().numpy()
     Cr = orc.project(Q, X)
-    assert np.max(np.abs(Cg - Cr)) < 1e-12
+    tol = _tc_bound(Q, X) if path == "tensor_cores" else 1e-12
+    assert np.max(np.abs(Cg - Cr)) < tol, (np.max(np.abs(Cg - Cr)), tol)
+    c.close()
+
+
+def test_project_tc_chirps_ragged(orc, rbm):
+    """Basis of a chirp greedy projected onto held-out chirps: odd N, k not a
+    multiple of the tile, Mx not a multiple of 64; within 1e-12 of the oracle."""
+    c = rbm.RB(device=0)
+    S = synth.chirps(1999, 700, seed=3)
+    g = c.greedy(upload(S), 1e-10, 300)
+    Q = g["Q"].cpu().numpy()
+    X = synth.chirps(1999, 1111, seed=9)
+    Cg = c.project(g["Q"], upload(X)).cpu().numpy()
+    Cr = orc.project(Q, X)
+    assert np.max(np.abs(Cg - Cr)) < 1e-12, np.max(np.abs(Cg - Cr))
     c.close()
 
 
