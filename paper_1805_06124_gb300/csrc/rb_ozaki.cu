@@ -27,7 +27,7 @@ constexpr int OZ_BITS = 7;       // bits per slice
 constexpr int OZ_LV = OZ_S;      // levels 2..8 -> 7 accumulators
 constexpr int OZ_M = 128;        // A rows per tile
 constexpr int OZ_N = 64;         // B rows (columns of C) per tile
-constexpr int OZ_KS = 32;        // K per shared-memory stage
+constexpr int OZ_KS = 16;        // K per shared-memory stage (double-buffered)
 constexpr int OZ_DRAIN = 512;    // K per exact TMEM chunk
 constexpr int OZ_TCOLS = 512;    // TMEM columns allocated (7 levels x 64 used)
 
@@ -38,15 +38,55 @@ __device__ __forceinline__ int scale_exp(double mx) {
     return e + 1;   // max < 2^(E-1)
 }
 
-// value -> 7 balanced slices of 7 bits (FP64 arithmetic, exact steps)
-__device__ __forceinline__ void slice7(double v, int E, __nv_bfloat16 *out, long long stride) {
-    double t = ldexp(v, -E);
+__device__ __forceinline__ long long oz_fixed(double v, int E) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    long long X = 0;
+    if (e != 0) {
+        const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+        const int sh = e - 1026 - E;
+        if (sh >= 0) X = m << sh;
+        else if (sh > -64) X = (m + (1LL << (-sh - 1))) >> (-sh);
+        if (b >> 63) X = -X;
+    }
+    return X;
+}
+
+// Slices of a (re, im) pair stored as BF16x2 into each of the 7 planes.
+__device__ __forceinline__ void slice7_pair(double re, double im, int E, __nv_bfloat162 *out, long long stride2) {
+    long long X = oz_fixed(re, E), Y = oz_fixed(im, E);
 #pragma unroll
     for (int s = 0; s < OZ_S; s++) {
-        double y = t * 128.0;
-        double a = rint(y);
-        t = y - a;
-        out[s * stride] = __double2bfloat16((double)a);
+        const int sh = 49 - OZ_BITS * (s + 1);
+        long long a = (sh > 0) ? ((X + (1LL << (sh - 1))) >> sh) : X;
+        long long c = (sh > 0) ? ((Y + (1LL << (sh - 1))) >> sh) : Y;
+        X -= a << sh;
+        Y -= c << sh;
+        out[s * stride2] = __floats2bfloat162_rn((float)a, (float)c);
+    }
+}
+
+// value -> 7 balanced slices of 7 bits.  Integer arithmetic on the IEEE
+// bits (the FP64 pipe of this GPU is slow): X = round(v 2^(49-E)), an integer
+// below 2^48 in magnitude since |v| < 2^(E-1); then balanced base-128 digits
+// from the top, alpha_s = round(X / 2^(49-7s)), X -= alpha_s 2^(49-7s).
+__device__ __forceinline__ void slice7(double v, int E, __nv_bfloat16 *out, long long stride) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    long long X = 0;
+    if (e != 0) {  // zero and subnormal inputs give zero slices
+        const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+        const int sh = e - 1026 - E;  // v = m 2^(e-1075) -> X = m 2^(e-1075+49-E)
+        if (sh >= 0) X = m << sh;
+        else if (sh > -64) X = (m + (1LL << (-sh - 1))) >> (-sh);  // round half up
+        if (b >> 63) X = -X;
+    }
+#pragma unroll
+    for (int s = 0; s < OZ_S; s++) {
+        const int sh = 49 - OZ_BITS * (s + 1);
+        long long a = (sh > 0) ? ((X + (1LL << (sh - 1))) >> sh) : X;
+        X -= a << sh;
+        out[s * stride] = __float2bfloat16_rn((float)a);
     }
 }
 
@@ -73,12 +113,10 @@ __global__ void k_oz_slice_A(const double2 *__restrict__ Q, long long N, int k, 
     const long long sstride = Rp * Kp;
     for (long long i = threadIdx.x; i < N; i += blockDim.x) {
         double2 v = q[i];
-        __nv_bfloat16 *re = As + (long long)(2 * l) * Kp + 2 * i;
-        __nv_bfloat16 *im = As + (long long)(2 * l + 1) * Kp + 2 * i;
-        slice7(v.x, E, re, sstride);
-        slice7(v.y, E, re + 1, sstride);
-        slice7(-v.y, E, im, sstride);
-        slice7(v.x, E, im + 1, sstride);
+        __nv_bfloat162 *re = (__nv_bfloat162 *)(As + (long long)(2 * l) * Kp + 2 * i);
+        __nv_bfloat162 *im = (__nv_bfloat162 *)(As + (long long)(2 * l + 1) * Kp + 2 * i);
+        slice7_pair(v.x, v.y, E, re, sstride / 2);
+        slice7_pair(-v.y, v.x, E, im, sstride / 2);
     }
 }
 
@@ -105,23 +143,24 @@ __global__ void k_oz_slice_B(const double2 *__restrict__ X, long long N, long lo
     const long long sstride = Cp * Kp;
     for (long long i = threadIdx.x; i < N; i += blockDim.x) {
         double2 v = x[i];
-        __nv_bfloat16 *o = Bs + j * Kp + 2 * i;
-        slice7(v.x, E, o, sstride);
-        slice7(v.y, E, o + 1, sstride);
+        slice7_pair(v.x, v.y, E, (__nv_bfloat162 *)(Bs + j * Kp + 2 * i), sstride / 2);
     }
 }
 
-// stage rows [r0, r0+R) x K [k0, k0+OZ_KS) of the 7 slice planes (row-major,
-// K contiguous) into K-major shared tiles, 16 bytes (8 K) at a time
-__device__ __forceinline__ void oz_stage(uint8_t *dst, const __nv_bfloat16 *src, long long plane, long long Kp, int R,
-                                         long long r0, long long k0) {
+// Asynchronous copy of rows [r0, r0+R) x K [k0, k0+OZ_KS) of the 7 slice
+// planes (row-major, K contiguous) into K-major shared tiles, 16 bytes (one
+// core-matrix row) per cp.async.
+__device__ __forceinline__ void oz_stage_async(uint8_t *dst, const __nv_bfloat16 *src, long long plane, long long Kp,
+                                               int R, long long r0, long long k0) {
     constexpr int per_row = OZ_KS / 8;
     for (int t = threadIdx.x; t < OZ_S * R * per_row; t += blockDim.x) {
         int s = t / (R * per_row), rem = t % (R * per_row);
         int r = rem / per_row, kk = (rem % per_row) * 8;
-        uint4 v = *(const uint4 *)(src + s * plane + (r0 + r) * Kp + k0 + kk);
-        *(uint4 *)(dst + s * (R * OZ_KS * 2) + kmajor_off(r, kk, OZ_KS)) = v;
+        const void *g = src + s * plane + (r0 + r) * Kp + k0 + kk;
+        uint32_t d = smem_u32(dst + s * (R * OZ_KS * 2) + kmajor_off(r, kk, OZ_KS));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g));
     }
+    asm volatile("cp.async.commit_group;");
 }
 
 // (hi, lo) += x, both double-float
@@ -132,9 +171,10 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict
                                                  long long Kp, long long Rp, long long Cp, double2 *__restrict__ C,
                                                  long long ldC, long long col_off, int *err) {
     extern __shared__ __align__(1024) uint8_t dsm[];
-    uint8_t *sA = dsm;                                    // 7 x 128 x 32 bf16 = 56 KB
-    uint8_t *sB = sA + OZ_S * OZ_M * OZ_KS * 2;           // 7 x 64 x 32 bf16 = 28 KB
-    float *acc_h = (float *)(sB + OZ_S * OZ_N * OZ_KS * 2);  // 128 x 64 double-float running sums
+    constexpr int SA = OZ_S * OZ_M * OZ_KS * 2, SB = OZ_S * OZ_N * OZ_KS * 2;  // 28 KB, 14 KB per buffer
+    uint8_t *sAb[2] = {dsm, dsm + SA};
+    uint8_t *sBb[2] = {dsm + 2 * SA, dsm + 2 * SA + SB};
+    float *acc_h = (float *)(dsm + 2 * (SA + SB));  // 128 x 64 double-float running sums
     float *acc_l = acc_h + OZ_M * OZ_N;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
@@ -154,9 +194,18 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict
     const long long nst = Kp / OZ_KS;
     constexpr int per_drain = OZ_DRAIN / OZ_KS;
     const long long planeA = Rp * Kp, planeB = Cp * Kp;
+    oz_stage_async(sAb[0], As, planeA, Kp, OZ_M, r0, 0);
+    oz_stage_async(sBb[0], Bs, planeB, Kp, OZ_N, j0, 0);
     for (long long st = 0; st < nst; st++) {
-        oz_stage(sA, As, planeA, Kp, OZ_M, r0, st * OZ_KS);
-        oz_stage(sB, Bs, planeB, Kp, OZ_N, j0, st * OZ_KS);
+        const int cur = (int)(st & 1);
+        uint8_t *sA = sAb[cur], *sB = sBb[cur];
+        if (st + 1 < nst) {  // prefetch the next stage into the other buffer
+            oz_stage_async(sAb[cur ^ 1], As, planeA, Kp, OZ_M, r0, (st + 1) * OZ_KS);
+            oz_stage_async(sBb[cur ^ 1], Bs, planeB, Kp, OZ_N, j0, (st + 1) * OZ_KS);
+            asm volatile("cp.async.wait_group 2;");
+        } else {
+            asm volatile("cp.async.wait_group 0;");
+        }
         fence_async_smem();
         __syncthreads();
         const bool fresh = (st % per_drain) == 0;
@@ -254,7 +303,7 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
     if (e != cudaSuccess) return e;
     k_oz_slice_A<<<k, 256, 0, s>>>(Q, N, k, ldQ, Kp, Rp, As, Ea);
     k_oz_slice_B<<<(unsigned)Mb, 256, 0, s>>>(X, N, Mb, ldX, Kp, Cp, Bs, Eb);
-    const size_t dsm = (size_t)OZ_S * (OZ_M + OZ_N) * OZ_KS * 2 + (size_t)2 * OZ_M * OZ_N * 4;
+    const size_t dsm = (size_t)2 * OZ_S * (OZ_M + OZ_N) * OZ_KS * 2 + (size_t)2 * OZ_M * OZ_N * 4;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
