@@ -269,6 +269,43 @@ def run_surrogate(args):
     c.close()
 
 
+def run_split_once(args):
+    """One rb_greedy_split call (after one warm-up call) on chirps N x M, seed 2,
+    tol 1e-10 -- the command the split form's profiles are taken with."""
+    import torch
+    from paper_1805_06124_gb300 import rb, synth
+    c = rb.RB(device=0)
+    q, m = synth.chirp_params(args.M, 2)
+    S = c.generate(q, m, args.N)
+    hi, lo = c.split(S)
+    del S
+    r = c.greedy_split(hi, lo, 1e-10, 800)
+    if args.steps > 0:
+        r = c.greedy_split(hi, lo, 1e-10, 800)
+    print(json.dumps({"workload": f"split form, chirps N={args.N} x M={args.M} seed 2, tol 1e-10", "k": r["k"],
+                      "switch_iter": r["switch_iter"], "ms": round(r["ms_total"], 3)}), flush=True)
+
+
+def run_project_once(args):
+    """rb_project of a random k-vector basis onto M chirps of length N (tensor
+    cores unless --project-fp64); prints the time of the second call."""
+    import torch
+    from paper_1805_06124_gb300 import rb, synth
+    c = rb.RB(device=0, project_fp64=args.project_fp64)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    Q = torch.randn(args.k, args.N, dtype=torch.complex128, device="cuda", generator=g) / args.N ** 0.5
+    X = c.generate(*synth.chirp_params(args.M, 5), args.N)
+    C = c.project(Q, X)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    C = c.project(Q, X)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(json.dumps({"workload": f"rb_project k={args.k} N={args.N} M={args.M}",
+                      "path": "fp64" if args.project_fp64 else "tensor_cores", "ms": round(dt * 1e3, 3),
+                      "useful_TFLOPs": round(8.0 * args.k * args.N * args.M / dt / 1e12, 3)}), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_1805_06124_gb300 import rb, synth
@@ -413,11 +450,21 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate"])
+    ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate", "split", "project", "batched"])
     ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--k", type=int, default=53)
+    ap.add_argument("--project-fp64", action="store_true")
     args = ap.parse_args()
     if args.workload == "surrogate":
         run_surrogate(args)
+    elif args.workload == "split":
+        run_split_once(args)
+    elif args.workload == "project":
+        run_project_once(args)
+    elif args.workload == "batched":
+        import torch
+        from paper_1805_06124_gb300 import rb, synth
+        print(json.dumps(batched_run(torch, rb, synth, 0, torch.cuda.Stream())), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
