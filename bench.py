@@ -110,6 +110,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def reduce_across_ranks(dist, ms, nbytes):
+    """Replicas: the job's time is the slowest rank's, its work the sum over
+    ranks (timing and accounting only; no data moves between ranks)."""
+    if dist is None:
+        return ms, nbytes
+    import torch
+    t = torch.tensor([ms, nbytes], dtype=torch.float64)
+    m = t.clone()
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(m[0].item()), float(t[1].item())
+
+
 def cpu_oracle_run(m_sample: int, steps: int = 1):
     """Times the FP64 C oracle on an N x m_sample column sample (seed 1)."""
     from oracle import oracle
@@ -347,16 +360,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    sweep_bytes = sum(r["sweep_bytes"] for r in results)
-    if dist:
-        t = torch.tensor([sweep_bytes], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        sweep_bytes = float(t.item())
+    ms_max, sweep_bytes = reduce_across_ranks(dist, ms, sum(r["sweep_bytes"] for r in results))
     value = sweep_bytes / (ms_max * 1e-3) / 1e9
     k = results[-1]["k"]
     n_sw = sum(r["n_sweeps"] for r in results)

@@ -180,6 +180,13 @@ typedef struct rb_problem {
 rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, double tol, int kmax,
                             rb_result *outs);
 
+/* Self-test of the bounded device-side wait every tensor-core kernel uses:
+ * one thread waits on an mbarrier that nothing arrives on (arrive = 0) for at
+ * most `polls` polls, then records a time-out and the kernel returns normally.
+ * Returns RB_ETIMEOUT when the wait ran out (expected for arrive = 0), RB_OK
+ * when it completed (arrive = 1), RB_EINVAL for polls < 1. */
+rb_status rb_debug_wait_selftest(rb_ctx *ctx, long long polls, int arrive);
+
 /* Same as rb_greedy, but S, every output array of *out, and the result are in
  * HOST memory (pinned or pageable).  The call copies S to the device and the
  * outputs back inside the call; device workspace is owned by the context. */

@@ -71,6 +71,8 @@ struct Layout {
 };
 
 rb_status ensure(rb_ctx *ctx, void **buf, size_t *cap, size_t need) {
+    if (getenv("RB_TEST_FAIL_ALLOC"))  // fault injection for the tests (host side only)
+        return fail(ctx, RB_ENOMEM, "device allocation refused (RB_TEST_FAIL_ALLOC is set)");
     if (*cap >= need && *buf) return RB_OK;
     if (*buf) {
         cudaStreamSynchronize(ctx->stream);
@@ -816,6 +818,22 @@ rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long
         return fail(ctx, RB_EINVAL, "rb_greedy_split: lo required, ld must be even and hi/lo 16-byte aligned");
     RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     return greedy_split_device(ctx, hi, lo, N, M, ld, tol, kmax, out);
+}
+
+rb_status rb_debug_wait_selftest(rb_ctx *ctx, long long polls, int arrive) {
+    if (!ctx || polls < 1) return RB_EINVAL;
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    rb_status s = ensure(ctx, &ctx->gen, &ctx->gen_cap, 256);
+    if (s != RB_OK) return s;
+    int *flag = (int *)ctx->gen;
+    cudaStream_t sm = ctx->stream;
+    RB_CK(cudaMemsetAsync(flag, 0, sizeof(int), sm), "memset flag");
+    RB_CK(rbk::launch_wait_selftest(polls, arrive, flag, sm), "wait selftest");
+    int h = 0;
+    RB_CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, sm), "flag copy");
+    RB_CK(cudaStreamSynchronize(sm), "stream sync");
+    if (h) return fail(ctx, RB_ETIMEOUT, "bounded wait ran out after %lld polls (self-test)", polls);
+    return RB_OK;
 }
 
 rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol, int kmax,

@@ -364,6 +364,7 @@ cudaError_t launch_final_err(const Prob &p, double *final_err, cudaStream_t s);
 cudaError_t launch_split_init(const Prob &p, cudaStream_t s);
 cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
 size_t oz_workspace(long long N, int k, long long Mb);
+cudaError_t launch_wait_selftest(long long polls, int arrive, int *flag, cudaStream_t s);
 cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mb,
                               long long ldX, double2 *C, long long ldC, long long col_off, void *ws, int *err,
                               cudaStream_t s);

@@ -280,6 +280,27 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict
     if (warp == 0) tmem_dealloc(tmem, OZ_TCOLS);
 }
 
+// Self-test of the bounded mbarrier wait used by every tensor-core kernel: one
+// thread waits on a barrier that nothing arrives on (unless `arrive`), with a
+// budget of `polls`, and records a time-out in *flag.  No tensor-core work is
+// in flight, so running out of budget leaves nothing behind.
+__global__ void k_wait_selftest(long long polls, int arrive, int *flag) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        if (arrive) {
+            unsigned long long st;
+            asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(smem_u32(&bar)));
+        }
+        if (!mbar_wait(&bar, 0, polls)) *flag = 1;
+    }
+}
+
+cudaError_t launch_wait_selftest(long long polls, int arrive, int *flag, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(polls, arrive, flag);
+    return cudaGetLastError();
+}
+
 size_t oz_workspace(long long N, int k, long long Mb) {
     long long Kp = (2 * N + OZ_KS - 1) / OZ_KS * OZ_KS;
     long long Rp = (2LL * k + OZ_M - 1) / OZ_M * OZ_M;

@@ -224,3 +224,31 @@ def test_config2_full_size_sampled(orc, rbm, sweep):
     c.close()
     del S, g
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------- failure detection
+
+def test_allocation_failure_is_reported_and_recoverable(rbm, monkeypatch):
+    c = rbm.RB(device=0)
+    S = upload(synth.chirps(64, 80, seed=1))
+    monkeypatch.setenv("RB_TEST_FAIL_ALLOC", "1")
+    with pytest.raises(rbm.RBError) as e:
+        c.greedy(S, 1e-10, 50)
+    assert e.value.status == rbm.ENOMEM
+    monkeypatch.delenv("RB_TEST_FAIL_ALLOC")
+    g = c.greedy(S, 1e-10, 50)
+    assert g["k"] > 5
+    c.close()
+
+
+def test_bounded_wait_times_out_and_context_survives(rbm):
+    import ctypes
+    c = rbm.RB(device=0)
+    f = c.lib.rb_debug_wait_selftest
+    f.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]
+    f.restype = ctypes.c_int
+    assert f(c._h, 1000, 0) == rbm.ETIMEOUT       # nothing arrives: the wait runs out and returns
+    assert f(c._h, 1000, 1) == rbm.OK             # positive control
+    g = c.greedy(upload(synth.chirps(64, 80, seed=1)), 1e-10, 50)
+    assert g["k"] > 5                             # the context is still usable
+    c.close()
