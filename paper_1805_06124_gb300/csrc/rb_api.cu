@@ -382,6 +382,7 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     Layout L;
     size_t o_norm = L.add((size_t)M * 8), o_acc = L.add((size_t)M * 8), o_pick = L.add((size_t)M);
     size_t o_nh = L.add((size_t)M * 8), o_ln = L.add((size_t)M * 4);
+    size_t o_da = L.add((size_t)M * 8), o_dc = L.add((size_t)M * 4);
     size_t o_qh = L.add((size_t)kcap * qs * sizeof(float2)), o_ql = L.add((size_t)kcap * qs * sizeof(float2));
     size_t o_v = L.add((size_t)N * sizeof(double2));
     size_t o_hp = L.add((size_t)kcap * nchunk * sizeof(double2));
@@ -431,6 +432,8 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     p.st = (rbk::DevState *)(w + o_st);
     p.norm2_hi = (double *)(w + o_nh);
     p.lonrm = (float *)(w + o_ln);
+    p.dacc = (double *)(w + o_da);
+    p.dcnt = (int *)(w + o_dc);
     p.bcount = (int *)(w + o_bc);
     p.nblk_cand = G;
     p.cand = (long long *)(w + o_cd);

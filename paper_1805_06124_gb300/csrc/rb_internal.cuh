@@ -32,7 +32,7 @@ struct DevState {
     int cand_overflow;   // split form: a candidate list was truncated at its capacity
     int max_cand;        // split form: largest candidate list seen
     int force_stop;      // split form: stop right after the pending projection onto lo
-    int pad1;
+    int cand_total;      // split form: candidates counted in this iteration
     double Lmax;       // split form: largest certified lower bound of the error
     long long J;       // next pivot column (kNoIdx = none left)
     double errJ;       // its error
@@ -86,6 +86,8 @@ struct Prob {
     int cand_cap;
     double switch_err;
     int *tc_err;       // set when a tensor-core wait ran out
+    double *dacc;      // split form: D_j, the lo correction folded in so far
+    int *dcnt;         // split form: basis vectors covered by D_j
 };
 
 // One problem of a batch (rb_greedy_batched): what the persistent sweep and

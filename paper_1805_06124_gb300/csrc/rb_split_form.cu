@@ -67,6 +67,8 @@ __global__ void __launch_bounds__(kThreads) k_split_init(Prob p) {
             p.norm2[j] = n2;
             p.norm2_hi[j] = nh;
             p.lonrm[j] = (float)(sqrt(ls) * (1.0 + 1e-4));
+            p.dacc[j] = 0.0;
+            p.dcnt[j] = 0;
         }
     }
 }
@@ -87,7 +89,9 @@ __device__ __forceinline__ void df_mac1(float &sh, float &sl, float ah, float al
 // c_hi = q^H hi with q = qh + ql (double-float), hi exact.
 __device__ __forceinline__ double2 col_dot_hi(const float2 *__restrict__ hcol, const float2 *__restrict__ qh,
                                               const float2 *__restrict__ ql, long long N, int lane) {
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    // two independent (re, im) double-float chains (even / odd element of each
+    // 16-byte pair) so consecutive TwoSums do not wait on each other
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f, rh2 = 0.f, rl2 = 0.f, ih2 = 0.f, il2 = 0.f;
     const float4 *h4 = reinterpret_cast<const float4 *>(hcol);
     const float4 *qh4 = reinterpret_cast<const float4 *>(qh);
     const float4 *ql4 = reinterpret_cast<const float4 *>(ql);
@@ -102,25 +106,25 @@ __device__ __forceinline__ double2 col_dot_hi(const float2 *__restrict__ hcol, c
         for (int u = 0; u < U; u++) {
             float4 qa = __ldg(qh4 + t + 32 * u), qb = __ldg(ql4 + t + 32 * u);
             df_mac1(rh, rl, qa.x, qb.x, a[u].x);
-            df_mac1(rh, rl, qa.y, qb.y, a[u].y);
             df_mac1(ih, il, qa.x, qb.x, a[u].y);
+            df_mac1(rh2, rl2, qa.z, qb.z, a[u].z);
+            df_mac1(ih2, il2, qa.z, qb.z, a[u].w);
+            df_mac1(rh, rl, qa.y, qb.y, a[u].y);
             df_mac1(ih, il, -qa.y, -qb.y, a[u].x);
-            df_mac1(rh, rl, qa.z, qb.z, a[u].z);
-            df_mac1(rh, rl, qa.w, qb.w, a[u].w);
-            df_mac1(ih, il, qa.z, qb.z, a[u].w);
-            df_mac1(ih, il, -qa.w, -qb.w, a[u].z);
+            df_mac1(rh2, rl2, qa.w, qb.w, a[u].w);
+            df_mac1(ih2, il2, -qa.w, -qb.w, a[u].z);
         }
     }
     for (; t < n2; t += 32) {
         float4 a = ld_stream(h4 + t), qa = __ldg(qh4 + t), qb = __ldg(ql4 + t);
         df_mac1(rh, rl, qa.x, qb.x, a.x);
-        df_mac1(rh, rl, qa.y, qb.y, a.y);
         df_mac1(ih, il, qa.x, qb.x, a.y);
+        df_mac1(rh2, rl2, qa.z, qb.z, a.z);
+        df_mac1(ih2, il2, qa.z, qb.z, a.w);
+        df_mac1(rh, rl, qa.y, qb.y, a.y);
         df_mac1(ih, il, -qa.y, -qb.y, a.x);
-        df_mac1(rh, rl, qa.z, qb.z, a.z);
-        df_mac1(rh, rl, qa.w, qb.w, a.w);
-        df_mac1(ih, il, qa.z, qb.z, a.w);
-        df_mac1(ih, il, -qa.w, -qb.w, a.z);
+        df_mac1(rh2, rl2, qa.w, qb.w, a.w);
+        df_mac1(ih2, il2, -qa.w, -qb.w, a.z);
     }
     if ((N & 1) && lane == 0) {
         long long i = N - 1;
@@ -130,6 +134,8 @@ __device__ __forceinline__ double2 col_dot_hi(const float2 *__restrict__ hcol, c
         df_mac1(ih, il, qa.x, qb.x, a.y);
         df_mac1(ih, il, -qa.y, -qb.y, a.x);
     }
+    df_add(rh, rl, rh2, rl2);
+    df_add(ih, il, ih2, il2);
     warp_df_sum(rh, rl);
     warp_df_sum(ih, il);
     return make_double2((double)rh + (double)rl, (double)ih + (double)il);
@@ -232,6 +238,25 @@ __global__ void __launch_bounds__(kThreads) k_cand_count(Prob p) {
     for (long long j = j0 + threadIdx.x; j < j1; j += blockDim.x) c += is_candidate(p, j, k1, Lmax);
     c = (int)block_sum((double)c);
     if (threadIdx.x == 0) p.bcount[blockIdx.x] = c;
+    // the last block turns the counts into exclusive prefixes (bases of the
+    // write pass) and publishes the total, once, through shared memory
+    if (!last_block(&st->ticket_aux)) return;
+    __shared__ int sc[4096];
+    const int G = gridDim.x;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) sc[b] = __ldcg(p.bcount + b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < G; b++) {
+            int x = sc[b];
+            sc[b] = run;
+            run += x;
+        }
+        st->cand_total = run;
+        st->ticket_aux = 0;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < G; b += blockDim.x) p.bcount[b] = sc[b];
 }
 
 __global__ void __launch_bounds__(kThreads) k_cand_write(Prob p) {
@@ -239,14 +264,8 @@ __global__ void __launch_bounds__(kThreads) k_cand_write(Prob p) {
     if (!recheck_active(st)) return;
     const int k1 = st->k;
     const double Lmax = st->Lmax;
-    __shared__ int base;
     __shared__ int wcount[kThreads / 32];
-    if (threadIdx.x == 0) {
-        int b0 = 0;
-        for (int b = 0; b < (int)blockIdx.x; b++) b0 += p.bcount[b];
-        base = b0;
-    }
-    __syncthreads();
+    const int base = p.bcount[blockIdx.x];  // exclusive prefix from k_cand_count
     const long long per = (p.M + gridDim.x - 1) / gridDim.x;
     const long long j0 = blockIdx.x * per, j1 = j0 + per < p.M ? j0 + per : p.M;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -272,34 +291,32 @@ __global__ void __launch_bounds__(kThreads) k_cand_write(Prob p) {
     }
 }
 
-// Exact error of each candidate: err_j = ||hi_j + lo_j||^2 - sum_l |c_hi,lj + q_l^H lo_j|^2.
-// One block per candidate; the block sweeps the rows once per group of 8 basis
-// vectors (8 complex FP32 dots per thread), the candidate's lo column staying
-// in L1 between groups.
+// Exact error of each candidate: err_j = ||hi_j + lo_j||^2 - sum_l |c_hi,lj + q_l^H lo_j|^2
+// = norm2_j - acc_hi_j - D_j with D_j = sum_l (2 Re(conj(c_hi,lj) d_lj) + |d_lj|^2),
+// d_lj = q_l^H lo_j.  D_j is kept per column with the number of basis vectors it
+// covers, so a column that stays a candidate over many iterations only adds the
+// new vectors' terms.  One block per candidate; the block sweeps the rows once
+// per group of 8 basis vectors (8 complex FP32 dots per thread).
 constexpr int RG = 8;
 
 __global__ void __launch_bounds__(kThreads) k_recheck(Prob p) {
     DevState *st = p.st;
     if (!recheck_active(st)) return;
-    __shared__ int s_total;
     __shared__ float red[2 * RG][kThreads / 32];
     __shared__ double s_acc;
     __shared__ double vals[RG];
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int b = 0; b < p.nblk_cand; b++) t += __ldcg(p.bcount + b);
-        s_total = t;
-        s_acc = 0.0;
-    }
-    __syncthreads();
-    const int total = s_total;
+    const int total = st->cand_total;
     const int n = total < p.cand_cap ? total : p.cand_cap;
     const int k1 = st->k;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if ((int)blockIdx.x < n) {
         const long long j = p.cand[blockIdx.x];
         const float2 *lcol = p.lo + j * p.ldH;
-        for (int l0 = 0; l0 < k1; l0 += RG) {
+        // basis vectors already folded into D_j by earlier rechecks of this column
+        const int lstart = p.dcnt[j];
+        if (threadIdx.x == 0) s_acc = p.dacc[j];
+        __syncthreads();
+        for (int l0 = lstart; l0 < k1; l0 += RG) {
             float re[RG], im[RG];
 #pragma unroll
             for (int g = 0; g < RG; g++) re[g] = im[g] = 0.f;
@@ -337,9 +354,9 @@ __global__ void __launch_bounds__(kThreads) k_recheck(Prob p) {
                         dre += (double)red[2 * g][x];
                         dim += (double)red[2 * g + 1][x];
                     }
+                    // |c_hi + d|^2 - |c_hi|^2 = 2 Re(conj(c_hi) d) + |d|^2
                     double2 c = p.C[(long long)(l0 + g) * p.ldC + j];
-                    double cr = c.x + dre, ci = c.y + dim;
-                    v = cr * cr + ci * ci;
+                    v = 2.0 * (c.x * dre + c.y * dim) + (dre * dre + dim * dim);
                 }
                 vals[g] = v;
             }
@@ -348,7 +365,12 @@ __global__ void __launch_bounds__(kThreads) k_recheck(Prob p) {
                 for (int g = 0; g < RG; g++) s_acc += vals[g];  // fixed order
             __syncthreads();
         }
-        if (threadIdx.x == 0) p.cand_err[blockIdx.x] = p.norm2[j] - s_acc;
+        if (threadIdx.x == 0) {
+            p.dacc[j] = s_acc;
+            p.dcnt[j] = k1;
+            // err_j = ||hi + lo||^2 - sum_l |c_hi,lj + d_lj|^2 = norm2 - acc_hi - D_j
+            p.cand_err[blockIdx.x] = p.norm2[j] - p.acc[j] - s_acc;
+        }
     }
     if (!last_block(&st->ticket_aux)) return;
     double be = -INFINITY;
