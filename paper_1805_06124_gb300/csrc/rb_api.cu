@@ -376,19 +376,26 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     const int nchunk = (int)((N + chunk - 1) / chunk);
     const int gN = (int)((N + rbk::kThreads - 1) / rbk::kThreads);
     const int kcap = kmax > 0 ? kmax : 1;
+    const int lgcap = (kcap + 7) / 8;
     const long long qs = (long long)align_up((size_t)N, 64);
-    const int cand_cap = 1024;
 
     Layout L;
     size_t o_norm = L.add((size_t)M * 8), o_acc = L.add((size_t)M * 8), o_pick = L.add((size_t)M);
-    size_t o_nh = L.add((size_t)M * 8), o_ln = L.add((size_t)M * 4);
+    size_t o_nh = L.add((size_t)M * 8), o_ln = L.add((size_t)M * 4), o_sn = L.add((size_t)M * 64 * 4);
+    size_t o_sa = L.add((size_t)M * 8);
     size_t o_da = L.add((size_t)M * 8), o_dc = L.add((size_t)M * 4);
     size_t o_qh = L.add((size_t)kcap * qs * sizeof(float2)), o_ql = L.add((size_t)kcap * qs * sizeof(float2));
     size_t o_v = L.add((size_t)N * sizeof(double2));
     size_t o_hp = L.add((size_t)kcap * nchunk * sizeof(double2));
     size_t np = (size_t)(G > gN ? G : gN);
     size_t o_np = L.add(np * 8), o_be = L.add((size_t)G * 8), o_bi = L.add((size_t)G * 8);
-    size_t o_bc = L.add((size_t)G * 4), o_cd = L.add((size_t)cand_cap * 8), o_ce = L.add((size_t)cand_cap * 8);
+    size_t o_bc = L.add((size_t)G * 4), o_cd = L.add((size_t)M * 8), o_ce = L.add((size_t)M * 8);
+    size_t o_pv = L.add((size_t)M * lgcap * 8);
+    // BF16 pieces of the basis: row tiles of 128 x stages of 64 K x 48 KB
+    const size_t n_rt = (size_t)((2LL * kcap + 127) / 128), n_stg = (size_t)((2 * N + 63) / 64);
+    size_t o_ap = L.add(n_rt * n_stg * 3 * 128 * 64 * 2);
+    // re-check chunk partials and counters (2048 pairs x 8 chunks x 32 doubles)
+    size_t o_rp = L.add((size_t)2048 * 8 * 32 * 8), o_rt = L.add((size_t)2048 * 4);
     size_t o_C = out->C ? 0 : L.add((size_t)kcap * M * sizeof(double2));
     size_t o_st = L.add(sizeof(rbk::DevState));
     size_t o_te = L.add(sizeof(int));
@@ -432,14 +439,22 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     p.st = (rbk::DevState *)(w + o_st);
     p.norm2_hi = (double *)(w + o_nh);
     p.lonrm = (float *)(w + o_ln);
+    p.snorm = (float *)(w + o_sn);
+    p.sabs = (double *)(w + o_sa);
+    // bound on the hi-only sweep's rounding relative to ||hi_j||: 2^-46 sqrt(N)
+    // (measured maxima near 2^-42.4 at N = 16384, i.e. 2^-49.4 sqrt(N))
+    p.eta = std::ldexp(1.0, -46) * std::sqrt((double)N);
     p.dacc = (double *)(w + o_da);
     p.dcnt = (int *)(w + o_dc);
     p.bcount = (int *)(w + o_bc);
     p.nblk_cand = G;
     p.cand = (long long *)(w + o_cd);
     p.cand_err = (double *)(w + o_ce);
-    p.cand_cap = cand_cap;
-    p.switch_err = o.switch_err;
+    p.pv = (double *)(w + o_pv);
+    p.apieces = (uint8_t *)(w + o_ap);
+    p.rpart = (double *)(w + o_rp);
+    p.rtick = (int *)(w + o_rt);
+    p.lgcap = lgcap;
     p.tc_err = (int *)(w + o_te);
 
     cudaStream_t sm = ctx->stream;
@@ -447,17 +462,19 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
     RB_CK(cudaMemsetAsync(p.st, 0, sizeof(rbk::DevState), sm), "memset state");
     RB_CK(cudaMemsetAsync(p.tc_err, 0, sizeof(int), sm), "memset tc flag");
+    RB_CK(cudaMemsetAsync(p.rtick, 0, 2048 * sizeof(int), sm), "memset re-check counters");
     RB_CK(rbk::launch_split_init(p, sm), "split init");
     RB_CK(rbk::launch_init(p, G, sm), "init");
     nlaunch += 2;
     int it = 0;
     bool stopped = false;
-    // one more round than kmax: a loop that ends in the hi-only phase still
-    // queues its projection onto lo after the last sweep
+    // one more round than kmax: a loop that ends at kmax still queues its
+    // projection onto lo after the last sweep
     while (!stopped) {
         for (int t = 0; t < o.iters_per_sync && it <= kcap; t++, it++) {
             RB_CK(rbk::launch_imgs(p, G, true, sm, &nlaunch), "imgs");
             RB_CK(rbk::launch_split_iteration(p, G, sm, &nlaunch), "split iteration");
+            RB_CK(rbk::launch_split_finish(p, G, sm, &nlaunch), "split finish");
         }
         RB_CK(cudaMemcpyAsync(ctx->st_host, p.st, sizeof(rbk::DevState), cudaMemcpyDeviceToHost, sm), "state copy");
         RB_CK(cudaStreamSynchronize(sm), "stream sync");
@@ -484,9 +501,9 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     int tc_err = 0;
     RB_CK(cudaMemcpy(&tc_err, p.tc_err, sizeof(int), cudaMemcpyDeviceToHost), "tc flag");
     if (tc_err) return fail(ctx, RB_ETIMEOUT, "rb_greedy_split: a tensor-core wait ran out");
-    const int n0 = hs.phase ? hs.switch_iter : hs.k;
-    const int n1 = hs.n_sweeps - n0;
-    out->sweep_bytes = (double)n0 * (8.0 * N * M + 16.0 * N + 41.0 * M) + (double)n1 * (16.0 * N * M + 16.0 * N + 41.0 * M);
+    // per hi-only sweep: hi (8 N M), chain norms (256 M), q (16 N), the column
+    // scalars read and written (acc, sabs, C row, norm2, norm2_hi, lonrm, picked)
+    out->sweep_bytes = (double)hs.n_sweeps * (8.0 * N * M + 256.0 * M + 16.0 * N + 69.0 * M);
     if (hs.status < 0) {
         const char *why = hs.status == RB_ENONFINITE ? "NaN or Inf in hi/lo"
                           : hs.status == RB_EORTHO   ? "IMGS did not pass the kappa test within imgs_max_passes"
@@ -819,6 +836,7 @@ rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long
     if (!lo || (ld & 1) || !aligned(hi, 16) || !aligned(lo, 16) || !aligned(out->Q, 16) ||
         (out->C && !aligned(out->C, 16)))
         return fail(ctx, RB_EINVAL, "rb_greedy_split: lo required, ld must be even and hi/lo 16-byte aligned");
+    if (N > (1LL << 22)) return fail(ctx, RB_EINVAL, "rb_greedy_split: N must not exceed 2^22");
     RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     return greedy_split_device(ctx, hi, lo, N, M, ld, tol, kmax, out);
 }

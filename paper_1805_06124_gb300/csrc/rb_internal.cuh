@@ -24,14 +24,14 @@ struct DevState {
     int passes;        // IMGS passes in the current iteration
     int total_passes;  // IMGS passes over the whole call
     int nonfinite;     // a column norm was NaN/Inf
-    int phase;         // split form: 0 = hi-only sweeps, 1 = hi+lo sweeps
-    int switch_iter;   // split form: first iteration at phase 1 (-1 = never)
+    int phase;         // split form: 1 once C has been completed by the projection onto lo
+    int switch_iter;   // split form: basis size at that projection (-1 = none)
     int n_sweeps;      // sweep launches that did work
     int ncand;         // split form: candidates in the last recheck
-    int switch_pending;  // split form: rebase queued (hi+lo projection of the basis)
-    int cand_overflow;   // split form: a candidate list was truncated at its capacity
+    int switch_pending;  // split form: the loop has ended; the projection onto lo is queued
+    int pad0;
     int max_cand;        // split form: largest candidate list seen
-    int force_stop;      // split form: stop right after the pending projection onto lo
+    int force_stop;      // split form: exact rank reached (IMGS found a zero vector)
     int cand_total;      // split form: candidates counted in this iteration
     double Lmax;       // split form: largest certified lower bound of the error
     long long J;       // next pivot column (kNoIdx = none left)
@@ -77,17 +77,22 @@ struct Prob {
     DevState *st;
     // split form
     double *norm2_hi;  // ||hi_j||^2
-    float *lonrm;      // ||lo_j||
-    double *ehi;       // err of hi_j during the hi-only phase
-    long long *cand;   // candidate columns
+    float *lonrm;      // ||lo_j|| (rounded up)
+    float *snorm;      // [M][64] 2-norms of the 64 lane chains of hi_j (rounded up)
+    double *sabs;      // sum_l |c~_lj| of the hi-only sweep results
+    double eta;        // bound on |c~ - q^H hi| relative to ||hi_j|| for one sweep
+    long long *cand;   // candidate columns (capacity M)
     double *cand_err;  // their exact errors
+    double *pv;        // recheck partials [candidate][group of 8 basis vectors]
+    uint8_t *apieces;  // BF16 pieces of the basis for the projection onto lo
+    double *rpart;     // re-check row-chunk partials [pair][chunk][32]
+    int *rtick;        // re-check chunk counters per (candidate, group) pair
+    int lgcap;         // groups per candidate in pv
     int *bcount;       // per-block candidate counts
     int nblk_cand;     // blocks of the candidate kernels
-    int cand_cap;
-    double switch_err;
     int *tc_err;       // set when a tensor-core wait ran out
-    double *dacc;      // split form: D_j, the lo correction folded in so far
-    int *dcnt;         // split form: basis vectors covered by D_j
+    double *dacc;      // D_j = sum_l (|c_lj|^2 - |c~_lj|^2) over the rows re-checked so far
+    int *dcnt;         // rows covered by D_j
 };
 
 // One problem of a batch (rb_greedy_batched): what the persistent sweep and
@@ -365,6 +370,7 @@ cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s
 cudaError_t launch_final_err(const Prob &p, double *final_err, cudaStream_t s);
 cudaError_t launch_split_init(const Prob &p, cudaStream_t s);
 cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
+cudaError_t launch_split_finish(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
 size_t oz_workspace(long long N, int k, long long Mb);
 cudaError_t launch_wait_selftest(long long polls, int arrive, int *flag, cudaStream_t s);
 cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mb,
