@@ -75,7 +75,7 @@ typedef struct rb_options {
     int sweep;             /* RB_SWEEP_DF32 (default) or RB_SWEEP_FP64 */
     double imgs_kappa;     /* MGSCI kappa, > 1 (default 2.0) */
     int imgs_max_passes;   /* cap on IMGS passes per vector, >= 1 (default 4) */
-    double switch_err;     /* split form: sweeps read hi+lo once max err < switch_err (default 1e-6) */
+    double switch_err;     /* reserved (must be > 0; default 1e-6); the split form does not switch sweeps */
     int iters_per_sync;    /* iterations queued between host checks of the stop flag (default 8) */
     void *stream;          /* cudaStream_t; NULL = the context creates its own stream */
     unsigned flags;        /* RB_FLAG_* */
@@ -99,7 +99,7 @@ typedef struct rb_result {
     /* ---- filled by the call (host scalars) ---- */
     int k;                 /* number of basis vectors built */
     int imgs_passes;       /* total IMGS passes over all vectors */
-    int switch_iter;       /* split form: first iteration that read hi+lo (-1 = never) */
+    int switch_iter;       /* split form: basis size when C was completed on lo (-1 = not reached) */
     int n_launches;        /* kernels this call launched */
     int n_sweeps;          /* sweep launches that did work */
     double ms_total;       /* CUDA-event time of the call on its stream */
@@ -147,16 +147,20 @@ rb_status rb_greedy(rb_ctx *ctx, const void *S, long long N, long long M, long l
                     double tol, int kmax, rb_result *out);
 
 /* Split-precision RB-greedy on S stored as complex64 hi + lo (see rb_split;
- * column j at hi + j*ld and lo + j*ld, ld even, both 16-byte aligned).
- * Phase 0 reads hi only: c = q^H hi with exact FP32 products summed in
- * double-float, FP64 bookkeeping of the error of hi_j, and a certified bound
- * |sqrt(err_j) - sqrt(err_hi_j)| <= ||lo_j||; the columns whose bound reaches
- * the best lower bound are re-checked exactly and the exact argmax is the
- * pivot.  Once the max error falls below opt.switch_err (or the loop ends),
- * the basis is projected onto lo to make C and every error exact, and the
- * remaining sweeps read hi + lo (the FP64 form's sweep).  IMGS, norms, the
- * bookkeeping and the re-check stay FP64(-accurate).  Outputs and returns as
- * rb_greedy; out->switch_iter is the first iteration that read hi + lo. */
+ * column j at hi + j*ld and lo + j*ld, ld even, both 16-byte aligned; N <= 2^22).
+ * Every sweep reads hi only: c~ = q^H hi with FP32 FMAs summed against a
+ * fixed power-of-two offset per lane chain (rounding about 2^-42 ||hi_j|| at
+ * N = 16384), FP64 bookkeeping of the error of hi_j, and the certified bounds
+ * |err(hi_j) - bookkeeping| <= 2 eta ||hi_j|| sum_l |c~_lj| (eta = 2^-46 sqrt(N))
+ * and |sqrt(err_j) - sqrt(err(hi_j))| <= ||lo_j||.  The columns whose upper
+ * bound reaches the best lower bound are re-checked exactly (hi and lo,
+ * compensated) and the exact argmax is the pivot; the loop ends when every
+ * upper bound, or the exact pivot error, is below tol (or at kmax), and then
+ * one tensor-core projection of the basis onto lo completes C and the errors.
+ * IMGS, norms, the bookkeeping and the re-check stay FP64(-accurate).  Outputs
+ * and returns as rb_greedy; C is accurate to 2^-48 sqrt(N) ||s_j|| beyond the
+ * FP64 form's; out->switch_iter is the basis size at the projection onto lo;
+ * opt.switch_err is not used by this form. */
 rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long N, long long M, long long ld,
                           double tol, int kmax, rb_result *out);
 
