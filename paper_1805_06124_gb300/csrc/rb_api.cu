@@ -391,9 +391,8 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     size_t o_np = L.add(np * 8), o_be = L.add((size_t)G * 8), o_bi = L.add((size_t)G * 8);
     size_t o_bc = L.add((size_t)G * 4), o_cd = L.add((size_t)M * 8), o_ce = L.add((size_t)M * 8);
     size_t o_pv = L.add((size_t)M * lgcap * 8);
-    // BF16 pieces of the basis: row tiles of 128 x stages of 64 K x 48 KB
-    const size_t n_rt = (size_t)((2LL * kcap + 127) / 128), n_stg = (size_t)((2 * N + 63) / 64);
-    size_t o_ap = L.add(n_rt * n_stg * 3 * 128 * 64 * 2);
+    // BF16 pieces of the basis for the projection onto lo
+    size_t o_ap = L.add(rbk::lo_pieces_bytes(N, kcap));
     // re-check chunk partials and counters (2048 pairs x 8 chunks x 32 doubles)
     size_t o_rp = L.add((size_t)2048 * 8 * 32 * 8), o_rt = L.add((size_t)2048 * 4);
     size_t o_C = out->C ? 0 : L.add((size_t)kcap * M * sizeof(double2));

@@ -371,6 +371,7 @@ cudaError_t launch_final_err(const Prob &p, double *final_err, cudaStream_t s);
 cudaError_t launch_split_init(const Prob &p, cudaStream_t s);
 cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
 cudaError_t launch_split_finish(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
+size_t lo_pieces_bytes(long long N, int kcap);
 size_t oz_workspace(long long N, int k, long long Mb);
 cudaError_t launch_wait_selftest(long long polls, int arrive, int *flag, cudaStream_t s);
 cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mb,

@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(kThreads) k_recheck(Prob p) {
 // accumulator, which leaves a relative error of a few 2^-24 -- what d needs,
 // since |lo| <= 2^-24 |s|.  Blocks loop over (row tile, column tile) pairs.
 constexpr int PT = 128;  // tile rows (A) and columns (B)
-constexpr int PKC = 64;  // K per stage
+constexpr int PKC = 32;  // K per stage
 constexpr int PSL = 3;   // BF16 pieces per FP32 value
 
 __device__ __forceinline__ void split3(float x, __nv_bfloat16 *o) {
@@ -670,11 +670,20 @@ __global__ void __launch_bounds__(kThreads) k_qpieces(Prob p) {
 // registers: thread t holds units t + u * kThreads, each 8 K entries.
 constexpr int PBU = PT * (PKC / 8) / kThreads;
 
+// Unit t -> (row r, first K entry kk) such that the 8 threads of each quarter
+// warp store the 8 rows of one core matrix (128 contiguous bytes: no bank
+// conflicts), while each warp still reads whole 128-byte runs of lo.
+__device__ __forceinline__ void proj_unit(int t, int &r, int &kk) {
+    r = (t & 7) + 8 * (t / (8 * (PKC / 8)));
+    kk = ((t >> 3) % (PKC / 8)) * 8;
+}
+
 __device__ __forceinline__ void proj_load_b(const Prob &p, long long j0, long long stg, float4 bx[PBU], float4 by[PBU]) {
 #pragma unroll
     for (int u = 0; u < PBU; u++) {
         const int t = threadIdx.x + u * kThreads;
-        const int r = t / (PKC / 8), kk = (t % (PKC / 8)) * 8;
+        int r, kk;
+        proj_unit(t, r, kk);
         const long long j = j0 + r;
         const long long i0 = (stg * PKC + kk) >> 1;  // a multiple of 4
         if (j < p.M && i0 + 3 < p.N) {
@@ -700,7 +709,8 @@ __device__ __forceinline__ void proj_store_b(uint8_t *sB, const float4 bx[PBU], 
 #pragma unroll
     for (int u = 0; u < PBU; u++) {
         const int t = threadIdx.x + u * kThreads;
-        const int r = t / (PKC / 8), kk = (t % (PKC / 8)) * 8;
+        int r, kk;
+        proj_unit(t, r, kk);
         const float v[8] = {bx[u].x, bx[u].y, bx[u].z, bx[u].w, by[u].x, by[u].y, by[u].z, by[u].w};
         stage_row8(sB, r, kk, v);
     }
@@ -747,47 +757,54 @@ __global__ void __launch_bounds__(kThreads) k_lo_project_tc(Prob p, int *err) {
     const long long nstg = (2 * p.N + PKC - 1) / PKC;
     uint32_t phbits = 0u;  // bit b: the next completion parity of mbar[b]
     bool ok = true;
-    float4 bx[PBU], by[PBU];
+    // lo values of two stages ahead live in registers: set 0 for even
+    // stages, set 1 for odd ones
+    float4 bx0[PBU], by0[PBU], bx1[PBU], by1[PBU];
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int rt = (int)(tile % nrt);
         const long long j0 = (tile / nrt) * PT;
         const uint8_t *ga = p.apieces + (long long)rt * nstg * PTILE;
-        proj_load_b(p, j0, 0, bx, by);
+        proj_load_b(p, j0, 0, bx0, by0);
+        if (nstg > 1) proj_load_b(p, j0, 1, bx1, by1);
         proj_copy_a(dsm, ga);
+        // one stage: B(stg) from registers into buffer b, registers refilled with
+        // B(stg + 2), MMAs on buffer b, then buffer b^1 is refilled with A(stg + 1)
+        // once the MMAs of stage stg - 1 are done
+#define RB_PROJ_STAGE(b, BX, BY)                                                                                    \
+    do {                                                                                                            \
+        uint8_t *sAb = dsm + 2 * (b) * PTILE, *sBb = sAb + PTILE;                                                   \
+        proj_store_b(sBb, BX, BY);                                                                                  \
+        if (stg + 2 < nstg) proj_load_b(p, j0, stg + 2, BX, BY);                                                    \
+        asm volatile("cp.async.wait_all;");                                                                         \
+        fence_async_smem();                                                                                         \
+        __syncthreads();                                                                                            \
+        if (threadIdx.x == 0) {                                                                                     \
+            tc_fence_after();                                                                                       \
+            int first = 1;                                                                                          \
+            _Pragma("unroll") for (int sa = 0; sa < PSL; sa++)                                                      \
+            _Pragma("unroll") for (int sb = 0; sb < PSL; sb++) {                                                    \
+                if (sa + sb > 2) continue; /* pieces s + t <= 4 (0-based sa + sb <= 2) */                          \
+                _Pragma("unroll") for (int kk = 0; kk < PKC / 16; kk++) {                                           \
+                    uint64_t ad = smem_desc(smem_u32(sAb) + sa * (PT * PKC * 2) + kk * 256, 128, (PKC / 8) * 128);  \
+                    uint64_t bd = smem_desc(smem_u32(sBb) + sb * (PT * PKC * 2) + kk * 256, 128, (PKC / 8) * 128);  \
+                    tc_mma_bf16(tmem, ad, bd, idesc, (stg > 0 || !first) ? 1u : 0u);                                \
+                    first = 0;                                                                                      \
+                }                                                                                                   \
+            }                                                                                                       \
+            tc_commit(&mbar[b]);                                                                                    \
+        }                                                                                                           \
+        if (stg >= 1) {                                                                                             \
+            ok = mbar_wait(&mbar[(b) ^ 1], (phbits >> ((b) ^ 1)) & 1u) && ok;                                       \
+            phbits ^= 1u << ((b) ^ 1);                                                                              \
+        }                                                                                                           \
+        if (stg + 1 < nstg) proj_copy_a(dsm + 2 * ((b) ^ 1) * PTILE, ga + (stg + 1) * PTILE);                     \
+    } while (0)
         for (long long stg = 0; stg < nstg; stg++) {
-            const int b = (int)(stg & 1);
-            uint8_t *sAb = dsm + 2 * b * PTILE, *sBb = sAb + PTILE;
-            proj_store_b(sBb, bx, by);
-            if (stg + 1 < nstg) proj_load_b(p, j0, stg + 1, bx, by);
-            asm volatile("cp.async.wait_all;");
-            fence_async_smem();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                tc_fence_after();
-                int first = 1;
-#pragma unroll
-                for (int sa = 0; sa < PSL; sa++)
-#pragma unroll
-                    for (int sb = 0; sb < PSL; sb++) {
-                        if (sa + sb > 2) continue;  // pieces s + t <= 4 (0-based sa + sb <= 2)
-#pragma unroll
-                        for (int kk = 0; kk < PKC / 16; kk++) {
-                            uint64_t ad = smem_desc(smem_u32(sAb) + sa * (PT * PKC * 2) + kk * 256, 128, (PKC / 8) * 128);
-                            uint64_t bd = smem_desc(smem_u32(sBb) + sb * (PT * PKC * 2) + kk * 256, 128, (PKC / 8) * 128);
-                            tc_mma_bf16(tmem, ad, bd, idesc, (stg > 0 || !first) ? 1u : 0u);
-                            first = 0;
-                        }
-                    }
-                tc_commit(b ? &mbar[1] : &mbar[0]);
-            }
-            if (stg >= 1) {
-                // the MMAs of stage stg-1 read buffer b^1: wait before refilling it
-                const int o = b ^ 1;
-                ok = mbar_wait(o ? &mbar[1] : &mbar[0], (phbits >> o) & 1u) && ok;
-                phbits ^= 1u << o;
-            }
-            if (stg + 1 < nstg) proj_copy_a(dsm + 2 * (b ^ 1) * PTILE, ga + (stg + 1) * PTILE);
+            RB_PROJ_STAGE(0, bx0, by0);
+            if (++stg >= nstg) break;
+            RB_PROJ_STAGE(1, bx1, by1);
         }
+#undef RB_PROJ_STAGE
         // the last stage's MMAs
         {
             const int b = (int)((nstg - 1) & 1);
@@ -902,13 +919,22 @@ cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int 
 
 // Queued after every iteration; both kernels return at once unless the loop
 // has just ended.
+size_t lo_pieces_bytes(long long N, int kcap) {
+    const long long nrt = (2LL * kcap + PT - 1) / PT, nstg = (2 * N + PKC - 1) / PKC;
+    return (size_t)nrt * (size_t)nstg * PTILE;
+}
+
 cudaError_t launch_split_finish(const Prob &p, int grid, cudaStream_t s, int *nlaunch) {
     const size_t dsmem = 4 * PTILE;
     static int g_proj = 0;
     if (!g_proj) {
         cudaFuncSetAttribute(k_lo_project_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
         cudaFuncSetAttribute(k_lo_project_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        g_proj = resident_grid(k_lo_project_tc, kThreads, dsmem);
+        // two blocks per SM (96 KB of buffers each) interleave their stages
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g_proj = 2 * sms;
     }
     k_qpieces<<<grid, kThreads, 0, s>>>(p);
     k_lo_project_tc<<<g_proj, kThreads, dsmem, s>>>(p, p.tc_err);
