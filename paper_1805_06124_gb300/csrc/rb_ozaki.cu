@@ -149,13 +149,14 @@ __global__ void k_oz_slice_B(const double2 *__restrict__ X, long long N, long lo
 
 // Asynchronous copy of rows [r0, r0+R) x K [k0, k0+OZ_KS) of the 7 slice
 // planes (row-major, K contiguous) into K-major shared tiles, 16 bytes (one
-// core-matrix row) per cp.async.
+// core-matrix row) per cp.async.  The 8 threads of each quarter warp fill the
+// 8 rows of one core matrix (128 contiguous bytes, no bank conflicts).
 __device__ __forceinline__ void oz_stage_async(uint8_t *dst, const __nv_bfloat16 *src, long long plane, long long Kp,
                                                int R, long long r0, long long k0) {
     constexpr int per_row = OZ_KS / 8;
     for (int t = threadIdx.x; t < OZ_S * R * per_row; t += blockDim.x) {
         int s = t / (R * per_row), rem = t % (R * per_row);
-        int r = rem / per_row, kk = (rem % per_row) * 8;
+        int r = (rem & 7) + 8 * (rem / (8 * per_row)), kk = ((rem >> 3) % per_row) * 8;
         const void *g = src + s * plane + (r0 + r) * Kp + k0 + kk;
         uint32_t d = smem_u32(dst + s * (R * OZ_KS * 2) + kmajor_off(r, kk, OZ_KS));
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g));
