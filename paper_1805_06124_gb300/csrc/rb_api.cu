@@ -553,7 +553,9 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
         o_ql[b] = L.add((size_t)(N + 2) * 8);
         o_v[b] = L.add((size_t)N * 16);
         o_hp[b] = L.add((size_t)kcap * nchunk * 16);
-        o_np[b] = L.add((size_t)(G > gN ? G : gN) * 8);
+        const int gNmax = (int)((maxN + rbk::kThreads - 1) / rbk::kThreads);
+        const int np_b = G > gN ? G : gN;
+        o_np[b] = L.add((size_t)(np_b > gNmax ? np_b : gNmax) * 8);
         o_be[b] = L.add((size_t)G * 8);
         o_bi[b] = L.add((size_t)G * 8);
         o_st[b] = L.add(sizeof(rbk::DevState));
@@ -579,6 +581,7 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
             o_lo[b] = L.add((size_t)probs[b].M * ldHs[b] * sizeof(float2));
         }
     size_t o_P = L.add((size_t)nprob * sizeof(rbk::BProb));
+    size_t o_PP = L.add((size_t)nprob * sizeof(rbk::Prob));
     size_t o_ch = L.add((size_t)(nprob + 1) * 8), o_col = L.add((size_t)(nprob + 1) * 8);
     size_t o_pe = L.add((size_t)chunks_min_cw * 8), o_pi = L.add((size_t)chunks_min_cw * 8);
     rb_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.off);
@@ -652,12 +655,21 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
     long long *dch = (long long *)(w + o_ch), *dcol = (long long *)(w + o_col);
     double *dpe = (double *)(w + o_pe);
     long long *dpi = (long long *)(w + o_pi);
+    rbk::Prob *dPP = (rbk::Prob *)(w + o_PP);
     RB_CK(cudaMemcpyAsync(dP, bp.data(), nprob * sizeof(rbk::BProb), cudaMemcpyHostToDevice, sm), "copy problems");
+    RB_CK(cudaMemcpyAsync(dPP, pp.data(), nprob * sizeof(rbk::Prob), cudaMemcpyHostToDevice, sm), "copy problems");
     RB_CK(cudaMemcpyAsync(dcol, col0.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm), "copy prefix");
     auto chunk_prefix = [&](int CW) {
         std::vector<long long> c(nprob + 1, 0);
         for (int b = 0; b < nprob; b++) c[b + 1] = c[b] + (probs[b].M + CW - 1) / CW;
         return c;
+    };
+    // chunk prefix sums on the device
+    auto upload_chunks = [&](int CW) -> cudaError_t {
+        std::vector<long long> c = chunk_prefix(CW);
+        cudaError_t e1 = cudaMemcpyAsync(dch, c.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm);
+        if (e1 != cudaSuccess) return e1;
+        return cudaStreamSynchronize(sm);
     };
     // ---- autotune (dry sweeps of this batch), cached per batch shape
     const int v0 = presplit ? 6 : 0;
@@ -675,8 +687,7 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
     } else {
         float best_ms = 1e30f;
         for (int ci = 0; ci < 2; ci++) {
-            std::vector<long long> c = chunk_prefix(CWs[ci]);
-            RB_CK(cudaMemcpyAsync(dch, c.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm), "copy chunks");
+            RB_CK(upload_chunks(CWs[ci]), "copy chunks");
             for (int v = v0; v < v0 + 6; v++) {
                 int g = rbk::bsweep_grid(v, ctx->device);
                 float ms = 0.f;
@@ -699,10 +710,7 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
         }
         ctx->tune[key] = std::make_pair(best_v, best_cw);
     }
-    {
-        std::vector<long long> c = chunk_prefix(best_cw);
-        RB_CK(cudaMemcpyAsync(dch, c.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm), "copy chunks");
-    }
+    RB_CK(upload_chunks(best_cw), "copy chunks");
     const int gv = rbk::bsweep_grid(best_v, ctx->device);
     for (int b = 0; b < nprob; b++) RB_CK(cudaMemsetAsync(pp[b].st, 0, sizeof(rbk::DevState), sm), "memset state");
     RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
@@ -723,26 +731,16 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
         RB_CK(rbk::launch_init(pp[b], G, sm), "init");
         nlaunch++;
     }
-    // ---- capture one iteration: per-problem IMGS on 8 forked streams, then the sweep and reduction
-    const int NS = 8;
-    cudaStream_t cap = nullptr, br[NS] = {};
-    cudaEvent_t fork = nullptr, join[NS] = {};
+    // ---- capture one iteration: the IMGS steps of all problems (one launch per
+    // step, grid.y = problem), then the sweep and the per-problem reduction
+    cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-    for (int i = 0; i < NS && e == cudaSuccess; i++) e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    for (int i = 0; i < NS && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
     int per_iter = 0;
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaEventRecord(fork, cap);
-        for (int i = 0; i < NS; i++) cudaStreamWaitEvent(br[i], fork, 0);
-        for (int b = 0; b < nprob; b++) rbk::launch_imgs(pp[b], G, false, br[b % NS], &per_iter);
-        for (int i = 0; i < NS; i++) {
-            cudaEventRecord(join[i], br[i]);
-            cudaStreamWaitEvent(cap, join[i], 0);
-        }
+        rbk::launch_imgs_batched(dPP, nprob, maxN, o.imgs_max_passes, G, cap, &per_iter);
         rbk::launch_bsweep(best_v, gv, dP, nprob, dch, best_cw, dpe, dpi, 0, cap);
         rbk::launch_breduce(dP, nprob, dch, dpe, dpi, cap);
         per_iter += 2;
@@ -767,11 +765,6 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    for (int i = 0; i < NS; i++) {
-        if (join[i]) cudaEventDestroy(join[i]);
-        if (br[i]) cudaStreamDestroy(br[i]);
-    }
-    if (fork) cudaEventDestroy(fork);
     if (cap) cudaStreamDestroy(cap);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rb_greedy_batched loop");
     if (!all) return fail(ctx, RB_ESTATE, "rb_greedy_batched: a problem did not stop after kmax iterations");

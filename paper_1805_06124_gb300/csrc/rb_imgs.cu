@@ -15,8 +15,12 @@
 
 namespace rbk {
 
+// Every step is a device body over blockIdx.x / gridDim.x, launched either for
+// one problem (Prob by value) or for a batch (blockIdx.y selects the problem
+// in a device array), so a batch of problems takes one launch per step.
+
 // v = s_J (FP64 copy of the pivot column), reset the pass counters.
-__global__ void __launch_bounds__(kThreads) k_imgs_begin(Prob p, int from_split) {
+__device__ __forceinline__ void imgs_begin(const Prob &p, int from_split) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop)) return;
     long long J = st->J;
@@ -40,7 +44,7 @@ __global__ void __launch_bounds__(kThreads) k_imgs_begin(Prob p, int from_split)
 }
 
 // Partial h_l over one row chunk: hpart[l][c] = sum_{i in chunk c} conj(q_l[i]) v[i].
-__global__ void __launch_bounds__(kThreads) k_imgs_dot(Prob p) {
+__device__ __forceinline__ void imgs_dot(const Prob &p) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop) || ld_volatile(&st->accepted)) return;
     const int k = st->k;
@@ -63,7 +67,8 @@ __global__ void __launch_bounds__(kThreads) k_imgs_dot(Prob p) {
 }
 
 // v -= Q_k h with h_l = sum_c hpart[l][c]; ||v||^2; kappa test in the last block.
-__global__ void __launch_bounds__(kThreads) k_imgs_update(Prob p) {
+// One element per thread: gridDim.x * blockDim.x >= N.
+__device__ __forceinline__ void imgs_update(const Prob &p) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop) || ld_volatile(&st->accepted)) return;
     const int k = st->k;
@@ -125,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_imgs_update(Prob p) {
 }
 
 // q_k = v / ||v||; Q[:, k], its FP32 hi/lo split for the sweep, pivot, R(k,k).
-__global__ void __launch_bounds__(kThreads) k_imgs_finalize(Prob p) {
+__device__ __forceinline__ void imgs_finalize(const Prob &p) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop)) return;
     const int k = st->k;
@@ -166,6 +171,16 @@ __global__ void __launch_bounds__(kThreads) k_imgs_finalize(Prob p) {
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_imgs_begin(Prob p, int from_split) { imgs_begin(p, from_split); }
+__global__ void __launch_bounds__(kThreads) k_imgs_dot(Prob p) { imgs_dot(p); }
+__global__ void __launch_bounds__(kThreads) k_imgs_update(Prob p) { imgs_update(p); }
+__global__ void __launch_bounds__(kThreads) k_imgs_finalize(Prob p) { imgs_finalize(p); }
+
+__global__ void __launch_bounds__(kThreads) k_imgs_begin_b(const Prob *pp) { imgs_begin(pp[blockIdx.y], 0); }
+__global__ void __launch_bounds__(kThreads) k_imgs_dot_b(const Prob *pp) { imgs_dot(pp[blockIdx.y]); }
+__global__ void __launch_bounds__(kThreads) k_imgs_update_b(const Prob *pp) { imgs_update(pp[blockIdx.y]); }
+__global__ void __launch_bounds__(kThreads) k_imgs_finalize_b(const Prob *pp) { imgs_finalize(pp[blockIdx.y]); }
+
 cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s, int *nlaunch) {
     int gN = (int)((p.N + kThreads - 1) / kThreads);
     int gcopy = gN < grid ? gN : grid;
@@ -177,6 +192,29 @@ cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s
         n += 2;
     }
     k_imgs_finalize<<<gcopy, kThreads, 0, s>>>(p);
+    n += 1;
+    if (nlaunch) *nlaunch += n;
+    return cudaGetLastError();
+}
+
+// The same steps for nprob problems at once (complex128 input): grid.y is the
+// problem, grid.x is sized for the largest N (smaller problems leave the extra
+// blocks idle; every problem's npart must hold gridDim.x entries).
+cudaError_t launch_imgs_batched(const Prob *pp_dev, int nprob, long long maxN, int max_passes, int grid,
+                                cudaStream_t s, int *nlaunch) {
+    const int gN = (int)((maxN + kThreads - 1) / kThreads);
+    const int gcopy = gN < grid ? gN : grid;
+    k_imgs_begin_b<<<dim3(gcopy, nprob), kThreads, 0, s>>>(pp_dev);
+    int n = 1;
+    // the dot step's items are (basis vector, row chunk) pairs: k * nchunk,
+    // a few hundred at most per problem
+    const int gdot = grid < 128 ? grid : 128;
+    for (int pass = 0; pass < max_passes; pass++) {
+        k_imgs_dot_b<<<dim3(gdot, nprob), kThreads, 0, s>>>(pp_dev);
+        k_imgs_update_b<<<dim3(gN, nprob), kThreads, 0, s>>>(pp_dev);
+        n += 2;
+    }
+    k_imgs_finalize_b<<<dim3(gcopy, nprob), kThreads, 0, s>>>(pp_dev);
     n += 1;
     if (nlaunch) *nlaunch += n;
     return cudaGetLastError();

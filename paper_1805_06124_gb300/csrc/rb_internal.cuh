@@ -367,6 +367,8 @@ cudaError_t launch_norms(const double2 *S, long long N, long long M, long long l
 cudaError_t launch_init(const Prob &p, int grid, cudaStream_t s);
 cudaError_t launch_sweep(const Prob &p, int variant, int grid, cudaStream_t s);
 cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s, int *nlaunch);
+cudaError_t launch_imgs_batched(const Prob *pp_dev, int nprob, long long maxN, int max_passes, int grid,
+                                cudaStream_t s, int *nlaunch);
 cudaError_t launch_final_err(const Prob &p, double *final_err, cudaStream_t s);
 cudaError_t launch_split_init(const Prob &p, cudaStream_t s);
 cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
