@@ -62,7 +62,8 @@ __device__ __forceinline__ void slice7_pair(double re, double im, int E, __nv_bf
         long long c = (sh > 0) ? ((Y + (1LL << (sh - 1))) >> sh) : Y;
         X -= a << sh;
         Y -= c << sh;
-        out[s * stride2] = __floats2bfloat162_rn((float)a, (float)c);
+        // |a|, |c| <= 64: exact through a 32-bit conversion
+        out[s * stride2] = __floats2bfloat162_rn(__int2float_rn((int)a), __int2float_rn((int)c));
     }
 }
 
@@ -120,30 +121,45 @@ __global__ void k_oz_slice_A(const double2 *__restrict__ Q, long long N, int k, 
     }
 }
 
-// B: one block per column j of this batch.
+// B: one block per column j of this batch.  The scale comes from the largest
+// biased exponent (integer max over the IEEE bits, no FP64 work): max|x| <
+// 2^(e_max - 1022), so E = e_max - 1021, as frexp of the maximum would give.
+// K positions past 2N (padding to Kp) are written as zero slices here.
 __global__ void k_oz_slice_B(const double2 *__restrict__ X, long long N, long long Mb, long long ldX, long long Kp,
                              long long Cp, __nv_bfloat16 *__restrict__ Bs, int *__restrict__ Eb) {
     const long long j = blockIdx.x;
     if (j >= Mb) return;
     const double2 *x = X + j * ldX;
-    double mx = 0.0;
-    for (long long i = threadIdx.x; i < N; i += blockDim.x) mx = fmax(mx, fmax(fabs(x[i].x), fabs(x[i].y)));
-    __shared__ double sm[32];
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+    unsigned int em = 0;
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+        const double2 v = x[i];
+        const unsigned int a = ((unsigned int)(__double_as_longlong(v.x) >> 52)) & 0x7FFu;
+        const unsigned int b = ((unsigned int)(__double_as_longlong(v.y) >> 52)) & 0x7FFu;
+        em = max(em, max(a, b));
+    }
+    __shared__ unsigned int se[32];
+    for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+    if ((threadIdx.x & 31) == 0) se[threadIdx.x >> 5] = em;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmax(m, sm[w]);
-        sm[0] = m;
+        unsigned int m = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = max(m, se[w]);
+        se[0] = m;
     }
     __syncthreads();
-    const int E = scale_exp(sm[0]);
+    const int E = se[0] ? (int)se[0] - 1021 : 0;
     if (threadIdx.x == 0) Eb[j] = E;
     const long long sstride = Cp * Kp;
-    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-        double2 v = x[i];
-        slice7_pair(v.x, v.y, E, (__nv_bfloat162 *)(Bs + j * Kp + 2 * i), sstride / 2);
+    const __nv_bfloat162 z2 = __floats2bfloat162_rn(0.f, 0.f);
+    for (long long i = threadIdx.x; i < Kp / 2; i += blockDim.x) {
+        __nv_bfloat162 *o = (__nv_bfloat162 *)(Bs + j * Kp + 2 * i);
+        if (i < N) {
+            const double2 v = x[i];
+            slice7_pair(v.x, v.y, E, o, sstride / 2);
+        } else {
+#pragma unroll
+            for (int sl = 0; sl < OZ_S; sl++) o[sl * (sstride / 2)] = z2;
+        }
     }
 }
 
@@ -321,8 +337,15 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
     __nv_bfloat16 *Bs = As + (size_t)OZ_S * Rp * Kp;
     int *Ea = (int *)(Bs + (size_t)OZ_S * Cp * Kp);
     int *Eb = Ea + k;
-    cudaError_t e = cudaMemsetAsync(ws, 0, (size_t)OZ_S * (Rp + Cp) * Kp * 2, s);
+    // zero fill: the A planes (small) and the padded B rows Mb..Cp-1 of each
+    // plane; k_oz_slice_B writes every other B entry, K padding included
+    cudaError_t e = cudaMemsetAsync(As, 0, (size_t)OZ_S * Rp * Kp * 2, s);
     if (e != cudaSuccess) return e;
+    if (Cp > Mb)
+        for (int sl = 0; sl < OZ_S; sl++) {
+            e = cudaMemsetAsync(Bs + (size_t)sl * Cp * Kp + (size_t)Mb * Kp, 0, (size_t)(Cp - Mb) * Kp * 2, s);
+            if (e != cudaSuccess) return e;
+        }
     k_oz_slice_A<<<k, 256, 0, s>>>(Q, N, k, ldQ, Kp, Rp, As, Ea);
     k_oz_slice_B<<<(unsigned)Mb, 256, 0, s>>>(X, N, Mb, ldX, Kp, Cp, Bs, Eb);
     const size_t dsm = (size_t)2 * OZ_S * (OZ_M + OZ_N) * OZ_KS * 2 + (size_t)2 * OZ_M * OZ_N * 4;
