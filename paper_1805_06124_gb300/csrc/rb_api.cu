@@ -865,9 +865,14 @@ rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, l
     if (s != RB_OK) return s;
     char *w = (char *)ctx->stage;
     cudaStream_t sm = ctx->stream;
-    RB_CK(cudaMemcpy2DAsync(w + o_S, (size_t)N * 16, S, (size_t)ldS * 16, (size_t)N * 16, (size_t)M,
-                            cudaMemcpyHostToDevice, sm),
-          "copy S to device");
+    // a contiguous S goes in one linear copy (the 2D copy engine path is about
+    // 2.5x slower for a 34 GB transfer from pinned memory)
+    if (ldS == N)
+        RB_CK(cudaMemcpyAsync(w + o_S, S, (size_t)M * N * 16, cudaMemcpyHostToDevice, sm), "copy S to device");
+    else
+        RB_CK(cudaMemcpy2DAsync(w + o_S, (size_t)N * 16, S, (size_t)ldS * 16, (size_t)N * 16, (size_t)M,
+                                cudaMemcpyHostToDevice, sm),
+              "copy S to device");
     rb_result d = *out;
     d.Q = w + o_Q;
     d.ldQ = N;
@@ -885,7 +890,9 @@ rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, l
                                 cudaMemcpyDeviceToHost, sm),
               "copy Q");
         RB_CK(cudaMemcpyAsync(out->pivots, d.pivots, (size_t)k * 8, cudaMemcpyDeviceToHost, sm), "copy pivots");
-        if (out->C)
+        if (out->C && out->ldC == M)
+            RB_CK(cudaMemcpyAsync(out->C, d.C, (size_t)k * M * 16, cudaMemcpyDeviceToHost, sm), "copy C");
+        else if (out->C)
             RB_CK(cudaMemcpy2DAsync(out->C, (size_t)out->ldC * 16, d.C, (size_t)M * 16, (size_t)M * 16, (size_t)k,
                                     cudaMemcpyDeviceToHost, sm),
                   "copy C");

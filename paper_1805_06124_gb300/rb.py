@@ -264,23 +264,42 @@ class RB:
         st = self._check(self.lib.rb_greedy_batched(self._h, n, probs, float(tol), int(kmax), results))
         return [self._pack(results[b].status, results[b], keep[b]) for b in range(n)]
 
-    def greedy_host(self, S, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True):
+    @staticmethod
+    def host_outputs(N: int, M: int, kmax: int, want_C: bool = True, want_final_err: bool = True, pin: bool = True):
+        """Host output buffers for greedy_host, to be reused across calls
+        (pinned by default; allocating pinned memory is slow)."""
+        torch = _torch()
+        kc = max(kmax, 1)
+        # the library fills every entry that is returned (the first k rows, all
+        # M final errors), so the large buffers are not zeroed
+        bufs = dict(Q=torch.empty((kc, N), dtype=torch.complex128, pin_memory=pin),
+                    pivots=torch.empty((kc,), dtype=torch.int64, pin_memory=pin),
+                    err_curve=torch.empty((kc + 1,), dtype=torch.float64, pin_memory=pin),
+                    rdiag=torch.empty((kc,), dtype=torch.float64, pin_memory=pin))
+        if want_C:
+            bufs["C"] = torch.empty((kc, M), dtype=torch.complex128, pin_memory=pin)
+        if want_final_err:
+            bufs["final_err"] = torch.empty((M,), dtype=torch.float64, pin_memory=pin)
+        return bufs
+
+    def greedy_host(self, S, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True, out=None):
         """Same as greedy, with S and all outputs in host memory (CPU tensors;
-        pinned memory gives the fastest copies)."""
+        pinned memory gives the fastest copies).  ``out``: buffers from
+        host_outputs (reused; the returned tensors are views of them)."""
         torch = _torch()
         if S.dim() != 2 or S.dtype != torch.complex128 or S.is_cuda or S.stride(1) != 1:
             raise TypeError("S must be a 2-D complex128 CPU tensor with unit column stride")
         M, N = S.shape
         kc = max(kmax, 1)
-        pin = S.is_pinned()
-        bufs = dict(Q=torch.zeros((kc, N), dtype=torch.complex128, pin_memory=pin),
-                    pivots=torch.full((kc,), -1, dtype=torch.int64, pin_memory=pin),
-                    err_curve=torch.zeros((kc + 1,), dtype=torch.float64, pin_memory=pin),
-                    rdiag=torch.zeros((kc,), dtype=torch.float64, pin_memory=pin))
-        if want_C:
-            bufs["C"] = torch.zeros((kc, M), dtype=torch.complex128, pin_memory=pin)
-        if want_final_err:
-            bufs["final_err"] = torch.zeros((M,), dtype=torch.float64, pin_memory=pin)
+        if out is None:
+            bufs = self.host_outputs(N, M, kmax, want_C, want_final_err, pin=S.is_pinned())
+        else:
+            bufs = out
+            want_C, want_final_err = "C" in bufs, "final_err" in bufs
+            if (tuple(bufs["Q"].shape) != (kc, N) or bufs["pivots"].numel() < kc or bufs["err_curve"].numel() < kc + 1
+                    or bufs["rdiag"].numel() < kc or (want_C and tuple(bufs["C"].shape) != (kc, M))
+                    or (want_final_err and bufs["final_err"].numel() < M)):
+                raise ValueError("out buffers do not match (N, M, kmax); build them with host_outputs")
         r = Result()
         r.Q = bufs["Q"].data_ptr()
         r.ldQ = N

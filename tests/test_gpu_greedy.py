@@ -126,6 +126,19 @@ def test_host_entry_point_matches_device(ctx):
     assert d["k"] == h["k"]
     for key in ("pivots", "err_curve", "Q", "C", "final_err", "rdiag"):
         np.testing.assert_array_equal(d[key], h[key])
+    # padded host rows (ld > N) take the strided copy; pageable memory works too
+    P = torch.zeros((500, 307), dtype=torch.complex128)
+    P[:, :300] = torch.from_numpy(S)
+    h2 = npy(ctx.greedy_host(P[:, :300], 1e-10, 100))
+    for key in ("pivots", "err_curve", "Q", "C", "final_err", "rdiag"):
+        np.testing.assert_array_equal(d[key], h2[key])
+    # caller-owned output buffers, reused by two calls in a row
+    out = ctx.host_outputs(300, 500, 100)
+    Sp = torch.from_numpy(S).pin_memory()
+    for _ in range(2):
+        h3 = npy(ctx.greedy_host(Sp, 1e-10, 100, out=out))
+        for key in ("pivots", "err_curve", "Q", "C", "final_err", "rdiag"):
+            np.testing.assert_array_equal(d[key], h3[key])
 
 
 # ------------------------------------------------------- generator / split
