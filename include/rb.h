@@ -79,6 +79,10 @@ typedef struct rb_options {
     int iters_per_sync;    /* iterations queued between host checks of the stop flag (default 8) */
     void *stream;          /* cudaStream_t; NULL = the context creates its own stream */
     unsigned flags;        /* RB_FLAG_* */
+    int recompute_period;  /* FP64 form (rb_greedy, rb_greedy_host): every recompute_period iterations
+                              acc_j = sum_l |C[l, j]|^2 is rebuilt from the stored coefficients with
+                              compensated summation before the sweep (the periodic exact recompute of the
+                              bookkeeping); 0 = off.  >= 0 (default 16) */
 } rb_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -115,6 +115,7 @@ void rb_default_options(rb_options *opt) {
     opt->imgs_max_passes = 4;
     opt->switch_err = 1e-6;
     opt->iters_per_sync = 8;
+    opt->recompute_period = 16;
     opt->stream = nullptr;
     opt->flags = 0;
 }
@@ -127,7 +128,7 @@ rb_status rb_create(const rb_options *opt, rb_ctx **out) {
         o = *opt;
     else
         rb_default_options(&o);
-    if (!(o.imgs_kappa > 1.0) || o.imgs_max_passes < 1 || o.iters_per_sync < 1 ||
+    if (!(o.imgs_kappa > 1.0) || o.imgs_max_passes < 1 || o.iters_per_sync < 1 || o.recompute_period < 0 ||
         (o.sweep != RB_SWEEP_DF32 && o.sweep != RB_SWEEP_FP64) || !(o.switch_err > 0.0))
         return RB_EINVAL;
     rb_ctx *ctx = new (std::nothrow) rb_ctx();
@@ -260,6 +261,10 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     size_t np = (size_t)(G > gN ? G : gN);
     size_t o_np = L.add(np * 8), o_be = L.add((size_t)G * 8), o_bi = L.add((size_t)G * 8);
     size_t o_st = L.add(sizeof(rbk::DevState));
+    // the periodic recompute reads the stored coefficients: keep them in the
+    // workspace when the caller does not ask for C
+    const bool ws_C = !out->C && o.recompute_period > 0;
+    size_t o_C = ws_C ? L.add((size_t)kcap * M * sizeof(double2)) : 0;
     rb_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.off);
     if (s != RB_OK) return s;
     char *w = (char *)ctx->ws;
@@ -270,7 +275,7 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     p.ldS = ldS;
     p.ldH = ldH;
     p.ldQ = out->ldQ;
-    p.ldC = out->ldC;
+    p.ldC = ws_C ? M : out->ldC;
     p.minNM = N < M ? N : M;
     p.kmax = kmax;
     p.max_passes = o.imgs_max_passes;
@@ -284,7 +289,7 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     p.Q = (double2 *)out->Q;
     p.pivots = out->pivots;
     p.err_curve = out->err_curve;
-    p.C = (double2 *)out->C;
+    p.C = ws_C ? (double2 *)(w + o_C) : (double2 *)out->C;
     p.rdiag = out->rdiag;
     p.norm2 = (double *)(w + o_norm);
     p.acc = (double *)(w + o_acc);
@@ -322,6 +327,10 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     while (!stopped) {
         for (int t = 0; t < o.iters_per_sync && it < kcap; t++, it++) {
             RB_CK(rbk::launch_imgs(p, G, false, sm, &nlaunch), "imgs");
+            if (o.recompute_period > 0) {
+                RB_CK(rbk::launch_recompute(p, o.recompute_period, G, sm), "recompute");
+                nlaunch += 1;
+            }
             if (timing) RB_CK(cudaEventRecord(ctx->sweep_ev[2 * it], sm), "cudaEventRecord");
             RB_CK(rbk::launch_sweep(p, variant, G, sm), "sweep");
             if (timing) RB_CK(cudaEventRecord(ctx->sweep_ev[2 * it + 1], sm), "cudaEventRecord");

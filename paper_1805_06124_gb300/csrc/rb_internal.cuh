@@ -366,6 +366,7 @@ cudaError_t launch_norms(const double2 *S, long long N, long long M, long long l
                          cudaStream_t s);
 cudaError_t launch_init(const Prob &p, int grid, cudaStream_t s);
 cudaError_t launch_sweep(const Prob &p, int variant, int grid, cudaStream_t s);
+cudaError_t launch_recompute(const Prob &p, int period, int grid, cudaStream_t s);
 cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s, int *nlaunch);
 cudaError_t launch_imgs_batched(const Prob *pp_dev, int nprob, long long maxN, int max_passes, int grid,
                                 cudaStream_t s, int *nlaunch);

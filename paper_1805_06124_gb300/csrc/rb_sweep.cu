@@ -117,6 +117,43 @@ int sweep_grid(int variant, int device) {
     return sms * per;
 }
 
+// Periodic exact recompute of the bookkeeping: before the sweep of iteration
+// k (k a positive multiple of `period`), acc_j = sum_{l<k} |C[l, j]|^2 is
+// rebuilt from the stored coefficients with error-free products (FMA) and a
+// compensated (TwoSum) running sum, replacing the k rounded updates of Eq.
+// (Residual)'s running sum by one sum accurate to about one unit in the last
+// place.  In exact arithmetic nothing changes.
+__global__ void __launch_bounds__(kThreads) k_recompute(Prob p, int period) {
+    DevState *st = p.st;
+    if (ld_volatile(&st->stop)) return;
+    const int k = st->k;
+    if (k == 0 || k % period != 0) return;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < p.M;
+         j += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0, e = 0.0;
+        for (int l = 0; l < k; l++) {
+            const double2 c = p.C[(long long)l * p.ldC + j];
+            const double x = c.x * c.x, ex = fma(c.x, c.x, -x);
+            const double y = c.y * c.y, ey = fma(c.y, c.y, -y);
+            double t = s + x, b = t - s;
+            e += ((s - (t - b)) + (x - b)) + ex;
+            s = t;
+            t = s + y;
+            b = t - s;
+            e += ((s - (t - b)) + (y - b)) + ey;
+            s = t;
+        }
+        p.acc[j] = s + e;
+    }
+}
+
+cudaError_t launch_recompute(const Prob &p, int period, int grid, cudaStream_t s) {
+    long long g = (p.M + kThreads - 1) / kThreads;
+    if (g > grid) g = grid;
+    k_recompute<<<(int)g, kThreads, 0, s>>>(p, period);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep(const Prob &p, int variant, int grid, cudaStream_t s) {
     if (variant == SWEEP_DF32)
         k_sweep<SWEEP_DF32><<<grid, kThreads, 0, s>>>(p);

@@ -64,6 +64,19 @@ def test_config1_parity(orc, ctx):
         assert e - rep["second_max"][d] <= max(1e-12 * e, parity.delta(d, S.shape[1], rep["err_curve"][0]))
 
 
+@pytest.mark.parametrize("period", [0, 3])
+def test_recompute_period_parity(orc, rbm, period):
+    """The periodic exact recompute of acc_j (every `period` iterations; 0 =
+    off) keeps the replay protocol and the tolerances; C is not requested, so
+    the recompute reads the workspace copy of the coefficients."""
+    S = synth.chirps(1024, 2048, seed=0)
+    c = rbm.RB(device=0, recompute_period=period)
+    g = npy(c.greedy(upload(S), 1e-10, 300, want_C=(period == 0)))
+    rep = parity.replay_and_check(orc, S, g, 1e-10, 300)
+    parity.compare(g, rep, S)
+    c.close()
+
+
 @pytest.mark.parametrize("shape", [(777, 1031, 800), (33, 65, 33), (1, 7, 1), (64, 1, 64), (257, 300, 263)])
 def test_ragged_shapes_parity(orc, ctx, shape):
     """Odd N (ragged 128-bit tail), padded leading dimension, M not a
