@@ -195,6 +195,29 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
  * when it completed (arrive = 1), RB_EINVAL for polls < 1. */
 rb_status rb_debug_wait_selftest(rb_ctx *ctx, long long polls, int arrive);
 
+/* Reconstruction (Alg. 4, Sec. 5.2.2): from a greedy basis Q_j and its
+ * coefficients C = Q_j^H S (= R(1:j, 1:M) up to the column order), the SVD
+ * C = V Sigma W^H (left factor only) and the enriched basis X_k = Q_j V(:, 1:k)
+ * with k = #{i : sigma_i > tau2} (sigma_{k+1} < tau2 < sigma_k).  By Theorem
+ * 5.6 / 5.8, ||S - X_i X_i^H S||_2 lies between sigma_{i+1}(S) (equal for an
+ * exact-rank S) and sigma_{i+1}(C) + ||S - Q_j C||_2.
+ *   Q: device complex128 N x j, column-major (ldQ >= N) -- rb_result.Q;
+ *   C: device complex128 j x M, row l at C + l*ldC (ldC >= M) -- rb_result.C;
+ *   X: device complex128 N x j capacity, column-major (ldX >= N); the first k
+ *      columns are written;
+ *   sigma: device double[j], the singular values of C in decreasing order;
+ *   V: device complex128 j x j row-major (V[l*j + c] = component l of vector c),
+ *      or NULL; each column's entry of largest magnitude (lowest row among
+ *      equals) is made real and positive;
+ *   *k_out: host.
+ * The SVD is taken through the Gram matrix in two Jacobi passes (FP64;
+ * singular values to about 1e-11 relative down to 1e-6 sigma_1).  j <=
+ * RB_RECON_MAX_J.  Synchronises the stream.  Errors: RB_EINVAL, RB_ENOMEM,
+ * RB_ECUDA. */
+#define RB_RECON_MAX_J 112
+rb_status rb_reconstruct(rb_ctx *ctx, const void *Q, long long N, int j, long long ldQ, const void *C, long long M,
+                         long long ldC, double tau2, void *X, long long ldX, double *sigma, void *V, int *k_out);
+
 /* Same as rb_greedy, but S, every output array of *out, and the result are in
  * HOST memory (pinned or pageable).  The call copies S to the device and the
  * outputs back inside the call; device workspace is owned by the context. */

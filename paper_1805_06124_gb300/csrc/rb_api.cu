@@ -236,6 +236,35 @@ rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long l
     return RB_OK;
 }
 
+rb_status rb_reconstruct(rb_ctx *ctx, const void *Q, long long N, int j, long long ldQ, const void *C, long long M,
+                         long long ldC, double tau2, void *X, long long ldX, double *sigma, void *V, int *k_out) {
+    if (!ctx) return RB_EINVAL;
+    if (N < 1 || M < 1 || j < 0 || j > RB_RECON_MAX_J || ldQ < N || ldC < M || ldX < N || !k_out ||
+        !(tau2 >= 0.0) || (j > 0 && (!Q || !C || !X || !sigma)) || !aligned(Q, 16) || !aligned(C, 16) ||
+        !aligned(X, 16) || !aligned(V, 16))
+        return fail(ctx, RB_EINVAL, "rb_reconstruct: bad arguments (N=%lld M=%lld j=%d, j <= %d)", N, M, j,
+                    RB_RECON_MAX_J);
+    *k_out = 0;
+    if (j == 0) return RB_OK;
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t wsb = (rbk::recon_workspace(j, M) + 255) & ~(size_t)255;
+    const size_t vbytes = (size_t)j * j * 16;
+    rb_status s = ensure(ctx, &ctx->gen, &ctx->gen_cap, wsb + vbytes + 256);
+    if (s != RB_OK) return s;
+    double2 *Vw = V ? (double2 *)V : (double2 *)((char *)ctx->gen + wsb);
+    cudaStream_t sm = ctx->stream;
+    RB_CK(rbk::launch_recon_svd((const double2 *)C, ldC, j, M, ctx->gen, sigma, Vw, nullptr, sm), "reconstruct svd");
+    std::vector<double> hs(j);
+    RB_CK(cudaMemcpyAsync(hs.data(), sigma, (size_t)j * 8, cudaMemcpyDeviceToHost, sm), "sigma copy");
+    RB_CK(cudaStreamSynchronize(sm), "stream sync");
+    int k = 0;
+    while (k < j && hs[k] > tau2) k++;
+    RB_CK(rbk::launch_recon_basis((const double2 *)Q, ldQ, N, j, Vw, k, (double2 *)X, ldX, sm), "reconstruct basis");
+    RB_CK(cudaStreamSynchronize(sm), "stream sync");
+    *k_out = k;
+    return RB_OK;
+}
+
 static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol,
                                int kmax, rb_result *out) {
     const rb_options &o = ctx->opt;

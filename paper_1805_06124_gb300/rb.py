@@ -85,10 +85,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.rb_greedy_split.argtypes = [c_void_p, c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int,
                                     ctypes.POINTER(Result)]
     lib.rb_project.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_void_p, c_ll]
+    lib.rb_reconstruct.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_double, c_void_p,
+                                   c_ll, c_void_p, c_void_p, ctypes.POINTER(c_int)]
     lib.rb_greedy_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(Problem), c_double, c_int,
                                       ctypes.POINTER(Result)]
     lib.rb_greedy_batched.restype = c_int
-    for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_greedy_split", "rb_project"):
+    for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_greedy_split", "rb_project",
+              "rb_reconstruct"):
         getattr(lib, f).restype = c_int
     _LIB = lib
     return lib
@@ -330,6 +333,30 @@ class RB:
         self._check(self.lib.rb_project(self._h, Q.data_ptr(), N, k, _ld(Q), X.data_ptr(), Mx, _ld(X),
                                         C.data_ptr(), Mx))
         return C[:k]
+
+    def reconstruct(self, Q, C, tau2: float):
+        """Reconstruction (Alg. 4): SVD of C (j, M) = V Sigma W^H and the enriched
+        basis X = rows x_c = sum_l V[l, c] q_l for the k singular values above
+        tau2.  Q (j, N) and C as returned by greedy.  Returns a dict with sigma
+        (j,) float64, V (j, j) complex128 (column c = left singular vector c, its
+        largest-magnitude entry real positive), k, and X (k, N)."""
+        torch = _torch()
+        _check2d(Q, torch.complex128, "Q")
+        _check2d(C, torch.complex128, "C")
+        j, N = Q.shape
+        if C.shape[0] != j:
+            raise ValueError("Q and C disagree on j")
+        M = C.shape[1]
+        dev = Q.device
+        with torch.cuda.stream(self.stream):
+            X = torch.empty((max(j, 1), N), dtype=torch.complex128, device=dev)
+            sigma = torch.empty(max(j, 1), dtype=torch.float64, device=dev)
+            V = torch.empty((max(j, 1), max(j, 1)), dtype=torch.complex128, device=dev)
+        k = c_int(0)
+        self._check(self.lib.rb_reconstruct(self._h, Q.data_ptr(), N, j, _ld(Q) if j else N, C.data_ptr(), M,
+                                            _ld(C) if j else M, float(tau2), X.data_ptr(), N, sigma.data_ptr(),
+                                            V.data_ptr(), ctypes.byref(k)))
+        return dict(sigma=sigma[:j], V=V[:j, :j], k=int(k.value), X=X[:k.value])
 
 
 class MLP:
