@@ -327,6 +327,62 @@ def run_project_once(args):
                       "useful_TFLOPs": round(8.0 * args.k * args.N * args.M / dt / 1e12, 3)}), flush=True)
 
 
+def run_recon_once(args):
+    """The reconstruction step (Alg. 4) on the FP64 greedy's output for chirps
+    N x M (seed 1, tol 1e-12): one warm-up call, then --steps timed calls of
+    rb_reconstruct with tau2 = 0 (k = j).  Total time from the host around the
+    synchronous call; phase times from the library's CUDA events on its own
+    stream; rooflines of the two heaviest phases:
+      transform  B = V1^H C in double-float: 48 FP32 operations per complex
+                 multiply-add, j^2 M of them, against 152 SMs x 128 FP32
+                 lanes x the sampled SM clock;
+      pass-2 Jacobi (one block): 42 j FP64 operations per rotation applied
+                 (rows and columns of G, columns of V), against one SM's FP64
+                 rate (2 per clock)."""
+    import statistics
+    import torch
+    from paper_1805_06124_gb300 import rb, synth
+    c = rb.RB(device=0, timing=True)
+    q, m = synth.chirp_params(args.M, 1)
+    S = c.generate(q, m, args.N)
+    g = c.greedy(S, 1e-12, 800)
+    del S
+    torch.cuda.empty_cache()
+    j = g["k"]
+    out = c.reconstruct(g["Q"], g["C"], 0.0)
+    ts, phases = [], []
+    with Clocks(0) as clk:
+        for _ in range(max(args.steps, 1)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = c.reconstruct(g["Q"], g["C"], 0.0)
+            ts.append(time.perf_counter() - t0)
+            phases.append(c.reconstruct_stats())
+    clocks = clk.summary()
+    st = phases[-1]
+    ms = {k: round(statistics.median(p["ms"][k] for p in phases), 4) for k in rb.RB.RECON_PHASES}
+    mhz = clocks.get("sm_mhz") or 1920.0
+    fp32_peak = 152 * 128 * mhz * 1e6 / 1e12            # T instructions/s
+    fp64_sm_peak = 2 * mhz * 1e6 / 1e9                   # G FP64 ops/s on one SM
+    t_ops = 48.0 * j * j * args.M
+    jac_ops = 42.0 * j * st["rotations"][1]
+    print(json.dumps({
+        "workload": f"reconstruction after the greedy, chirps N={args.N} x M={args.M} seed 1, tol 1e-12",
+        "j": j, "k": out["k"], "greedy_ms": round(g["ms_total"], 3),
+        "recon_ms_median": round(1e3 * sorted(ts)[len(ts) // 2], 3), "recon_ms_min": round(1e3 * min(ts), 3),
+        "phase_ms": ms, "jacobi_sweeps": st["sweeps"], "jacobi_rotations": st["rotations"],
+        "roofline": {
+            "transform_df32": {"bound": "alu", "achieved": round(t_ops / (ms["transform_df32"] * 1e-3) / 1e12, 3),
+                               "peak": round(fp32_peak, 2), "unit": "T FP32 ops/s",
+                               "frac": round(t_ops / (ms["transform_df32"] * 1e-3) / 1e12 / fp32_peak, 3)},
+            "jacobi2_fp64": {"bound": "alu (one SM)",
+                             "achieved": round(jac_ops / (ms["jacobi2_fp64"] * 1e-3) / 1e9, 3),
+                             "peak": round(fp64_sm_peak, 2), "unit": "G FP64 ops/s",
+                             "frac": round(jac_ops / (ms["jacobi2_fp64"] * 1e-3) / 1e9 / fp64_sm_peak, 3)}},
+        "clocks": clocks,
+        "sigma_1": float(out["sigma"][0]), "sigma_j": float(out["sigma"][j - 1])}), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_1805_06124_gb300 import rb, synth
@@ -464,7 +520,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate", "split", "project", "batched"])
+    ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate", "split", "project", "batched",
+                                                                "recon"])
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--k", type=int, default=53)
     ap.add_argument("--project-fp64", action="store_true")
@@ -475,6 +532,8 @@ def main():
         run_split_once(args)
     elif args.workload == "project":
         run_project_once(args)
+    elif args.workload == "recon":
+        run_recon_once(args)
     elif args.workload == "batched":
         import torch
         from paper_1805_06124_gb300 import rb, synth

@@ -218,6 +218,15 @@ rb_status rb_debug_wait_selftest(rb_ctx *ctx, long long polls, int arrive);
 rb_status rb_reconstruct(rb_ctx *ctx, const void *Q, long long N, int j, long long ldQ, const void *C, long long M,
                          long long ldC, double tau2, void *X, long long ldX, double *sigma, void *V, int *k_out);
 
+/* What the last rb_reconstruct on ctx did (host arrays, either may be NULL):
+ *   ms[7]     CUDA-event times in ms of its phases (zeros unless the context
+ *             was created with RB_FLAG_TIMING): pass-1 Gram (FP32), pass-1
+ *             Jacobi (FP32), Newton-Schulz steps, transform B = V1^H C,
+ *             pass-2 Gram, pass-2 Jacobi (FP64) + ordering, basis X_k;
+ *   counts[4] Jacobi sweeps and rotations applied in pass 1 and in pass 2.
+ * Errors: RB_EINVAL (ctx NULL). */
+rb_status rb_reconstruct_stats(const rb_ctx *ctx, double *ms, int *counts);
+
 /* Same as rb_greedy, but S, every output array of *out, and the result are in
  * HOST memory (pinned or pageable).  The call copies S to the device and the
  * outputs back inside the call; device workspace is owned by the context. */

@@ -33,6 +33,9 @@ struct rb_ctx {
     rbk::DevState *st_host = nullptr;  // pinned copy of the device state
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> sweep_ev;
+    std::vector<cudaEvent_t> recon_ev;  // phase events of rb_reconstruct (RB_FLAG_TIMING)
+    double recon_ms[7] = {0};           // phase times of the last rb_reconstruct
+    int recon_counts[4] = {0};          // Jacobi sweeps / rotations, pass 1 and pass 2
     int grid_cache[2] = {0, 0};
     std::map<std::tuple<int, long long, long long>, std::pair<int, int>> tune;  // batch shape -> (variant, CW)
 };
@@ -162,6 +165,7 @@ void rb_destroy(rb_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t ev : ctx->sweep_ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : ctx->recon_ev) cudaEventDestroy(ev);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ws) cudaFree(ctx->ws);
@@ -245,23 +249,49 @@ rb_status rb_reconstruct(rb_ctx *ctx, const void *Q, long long N, int j, long lo
         return fail(ctx, RB_EINVAL, "rb_reconstruct: bad arguments (N=%lld M=%lld j=%d, j <= %d)", N, M, j,
                     RB_RECON_MAX_J);
     *k_out = 0;
+    for (double &t : ctx->recon_ms) t = 0.0;
+    for (int &c : ctx->recon_counts) c = 0;
     if (j == 0) return RB_OK;
     RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     const size_t wsb = (rbk::recon_workspace(j, M) + 255) & ~(size_t)255;
-    const size_t vbytes = (size_t)j * j * 16;
+    const size_t vbytes = ((size_t)j * j * 16 + 255) & ~(size_t)255;
     rb_status s = ensure(ctx, &ctx->gen, &ctx->gen_cap, wsb + vbytes + 256);
     if (s != RB_OK) return s;
     double2 *Vw = V ? (double2 *)V : (double2 *)((char *)ctx->gen + wsb);
+    int *stats = (int *)((char *)ctx->gen + wsb + vbytes);
+    const bool timing = (ctx->opt.flags & RB_FLAG_TIMING) != 0;
+    if (timing && ctx->recon_ev.empty()) {
+        ctx->recon_ev.resize(8);
+        for (cudaEvent_t &ev : ctx->recon_ev) RB_CK(cudaEventCreate(&ev), "cudaEventCreate");
+    }
+    cudaEvent_t *ev = timing ? ctx->recon_ev.data() : nullptr;
     cudaStream_t sm = ctx->stream;
-    RB_CK(rbk::launch_recon_svd((const double2 *)C, ldC, j, M, ctx->gen, sigma, Vw, nullptr, sm), "reconstruct svd");
+    RB_CK(rbk::launch_recon_svd((const double2 *)C, ldC, j, M, ctx->gen, sigma, Vw, stats, ev, sm), "reconstruct svd");
     std::vector<double> hs(j);
     RB_CK(cudaMemcpyAsync(hs.data(), sigma, (size_t)j * 8, cudaMemcpyDeviceToHost, sm), "sigma copy");
+    RB_CK(cudaMemcpyAsync(ctx->recon_counts, stats, 4 * sizeof(int), cudaMemcpyDeviceToHost, sm), "stats copy");
     RB_CK(cudaStreamSynchronize(sm), "stream sync");
     int k = 0;
     while (k < j && hs[k] > tau2) k++;
     RB_CK(rbk::launch_recon_basis((const double2 *)Q, ldQ, N, j, Vw, k, (double2 *)X, ldX, sm), "reconstruct basis");
+    if (ev) RB_CK(cudaEventRecord(ev[7], sm), "cudaEventRecord");
     RB_CK(cudaStreamSynchronize(sm), "stream sync");
+    if (ev)
+        for (int i = 0; i < 7; i++) {
+            float t = 0.f;
+            RB_CK(cudaEventElapsedTime(&t, ev[i], ev[i + 1]), "cudaEventElapsedTime");
+            ctx->recon_ms[i] = t;
+        }
     *k_out = k;
+    return RB_OK;
+}
+
+rb_status rb_reconstruct_stats(const rb_ctx *ctx, double *ms, int *counts) {
+    if (!ctx) return RB_EINVAL;
+    if (ms)
+        for (int i = 0; i < 7; i++) ms[i] = ctx->recon_ms[i];
+    if (counts)
+        for (int i = 0; i < 4; i++) counts[i] = ctx->recon_counts[i];
     return RB_OK;
 }
 

@@ -377,7 +377,7 @@ cudaError_t launch_split_finish(const Prob &p, int grid, cudaStream_t s, int *nl
 size_t lo_pieces_bytes(long long N, int kcap);
 size_t recon_workspace(int j, long long M);
 cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M, void *ws, double *sigma, double2 *V,
-                             int *sweeps, cudaStream_t s);
+                             int *stats, cudaEvent_t *ev, cudaStream_t s);
 cudaError_t launch_recon_basis(const double2 *Q, long long ldQ, long long N, int j, const double2 *V, int k,
                                double2 *X, long long ldX, cudaStream_t s);
 size_t oz_workspace(long long N, int k, long long Mb);

@@ -3,277 +3,433 @@
 // X_k = Q_j V(:, 1:k).
 //
 // Only the left factor of C (j x M, j small, M large) is needed, so the SVD is
-// taken through the j x j Gram matrix G = C C^H = V Sigma^2 V^H, in two passes:
-// pass 1 diagonalises G with Jacobi rotations; pass 2 forms B = V^H C, whose
-// rows are already nearly orthogonal, and diagonalises B B^H again.  Pass 1
-// alone loses the small singular values to the squaring (relative error
-// ~ u sigma_1^2 / sigma_i^2); pass 2 restores relative accuracy (the Jacobi
-// method is relatively accurate on a nearly diagonal positive matrix).
+// taken through j x j Gram matrices, in two passes:
+//   pass 1  G1 = C C^H in FP32, Jacobi in FP32 -> V1, then made unitary to
+//           FP64 precision by Newton-Schulz steps V <- V (3I - V^H V) / 2;
+//   pass 2  B = V1^H C and G2 = B B^H in double-float (FP32 pairs, about 48
+//           bits, every product relative to its own operands), Jacobi in FP64
+//           on G2 with V accumulated on top of V1 -> V = V1 V2, lambda = diag.
+// G2 is nearly diagonal with off-diagonal entries small relative to
+// sqrt(G2_aa G2_bb), so pass 2 takes two or three sweeps and, with the
+// relative rotation threshold below, keeps the small singular values to high
+// relative accuracy (the squaring in a one-pass Gram method would lose them).
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, so
+// everything of size O(j^2 M) is FP32 or double-float; FP64 is left to the
+// j x j work.
 //
 // Jacobi: cyclic, parallel ("round robin") ordering -- every step rotates
-// npad/2 disjoint index pairs at once, left updates of all pairs, a barrier,
-// right updates, a barrier.  One block; G and V live in global memory (L1/L2).
-// For a pair (p, q) with g = G_pq = |g| e^{i phi}: tau = (G_qq - G_pp) / (2|g|),
-// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c, and
-// J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] on columns (p, q); G <- J^H G J,
-// V <- V J (the Hermitian form of the symmetric Schur rotation).
+// npad/2 disjoint index pairs at once: left updates of all pairs, a barrier,
+// right updates, a barrier; G (and V where it fits) in shared memory, one
+// block.  For a pair (p, q) with g = G_pq = |g| e^{i phi}: tau = (G_qq -
+// G_pp) / (2|g|), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 +
+// t^2), s = t c, J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] on columns (p, q);
+// G <- J^H G J, V <- V J.  A pair is rotated only while |g| > eps
+// sqrt(|G_pp G_qq|) (the relative criterion of Demmel and Veselic); a sweep
+// with no rotation ends the iteration.
 //
-// All arithmetic is FP64.  Sums run in a fixed order; results are
-// deterministic.
+// C is scaled by a power of two 2^-E (max |c| < 1) before any FP32 work so
+// that no square over- or underflows for representable inputs; sigma is
+// scaled back.  All sums run in a fixed order: results are deterministic.
 #include "rb_internal.cuh"
 
 namespace rbk {
 
-constexpr int RT = 32;   // Gram tile (rows and columns)
-constexpr int RTW = 32;  // columns of A per shared-memory step
-constexpr long long kGramChunk = 4096;  // columns of A per partial Gram sum
+constexpr int RG_T = 32;          // columns per staged tile
+constexpr int RG_THREADS = 512;   // Gram block (triangle of entries)
+constexpr int RG_MAXE = 13;       // entries per thread: ceil(112 * 113 / 2 / 512)
+constexpr int RJ_THREADS = 512;   // Jacobi block
+constexpr int RJ_PAIRS = 64;      // index pairs per step (j <= 128)
+constexpr int RT_THREADS = 256;   // transform block
+constexpr int RT_ROWS = 14;       // output rows per warp: ceil(112 / 8)
+constexpr int kMaxJ = 112;
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
-    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+// Largest biased exponent over C (integer max on the IEEE bits).
+__global__ void k_max_exp(const double2 *__restrict__ A, long long ldA, int j, long long M, int *__restrict__ emax) {
+    unsigned int e = 0;
+    for (int r = blockIdx.y; r < j; r += gridDim.y)
+        for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
+            const double2 v = A[(long long)r * ldA + m];
+            e = max(e, max((unsigned int)(__double_as_longlong(v.x) >> 52) & 0x7FFu,
+                           (unsigned int)(__double_as_longlong(v.y) >> 52) & 0x7FFu));
+        }
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0 && e) atomicMax(emax, (int)e);
 }
 
-// Partial Gram tiles: part[chunk][a][b] = sum_{m in chunk} A[a][m] conj(A[b][m])
-// for the tile (a0, b0) = (blockIdx.y, blockIdx.z) * RT with a0 <= b0.
-// A is j x M, row a at A + a * ldA.  Thread (ty, tx) owns a = a0 + ty and
-// b = b0 + 4 tx + e, e < 4.
-__global__ void __launch_bounds__(256) k_gram_part(const double2 *__restrict__ A, long long ldA, int j, long long M,
-                                                   long long chunk, double2 *__restrict__ part) {
-    const int a0 = blockIdx.y * RT, b0 = blockIdx.z * RT;
-    if (b0 < a0) return;
-    __shared__ double2 sa[RT][RTW + 1], sb[RT][RTW + 1];
-    const int ty = threadIdx.x >> 3, tx = threadIdx.x & 7;
-    const long long m0 = (long long)blockIdx.x * chunk, m1 = m0 + chunk < M ? m0 + chunk : M;
-    double2 acc[4];
+// 2^-E with E = e_max - 1022 (max |c| < 2^E); 1 for an all-zero C.
+__device__ __forceinline__ double c_scale(const int *emax) {
+    const int e = *emax;
+    return e ? ldexp(1.0, 1022 - e) : 1.0;
+}
+
+__device__ __forceinline__ float4 split_c(double2 v) {
+    float4 r;
+    split_rn(v.x, r.x, r.z);
+    split_rn(v.y, r.y, r.w);
+    return r;  // (re hi, im hi, re lo, im lo)
+}
+
+// Partial Gram sums over one column chunk: part[(chunk * j + a) * j + b] =
+// sum_{m in chunk} A[a][m] conj(A[b][m]) (times the scale^2) for a <= b.
+// The block stages RG_T columns of all j rows in shared memory; thread t
+// owns the upper-triangle entries e = t + RG_THREADS i (row-major order).
+// DF: double-float products and sums; otherwise FP32.
+template <bool DF>
+__global__ void __launch_bounds__(RG_THREADS) k_gram_tri(const double2 *__restrict__ A, long long ldA, int j,
+                                                          long long M, long long chunk, const int *__restrict__ emax,
+                                                          double2 *__restrict__ part) {
+    extern __shared__ float4 st[];  // j x (RG_T + 1)
+    const int ne = j * (j + 1) / 2;
+    const double sc = emax ? c_scale(emax) : 1.0;
+    int eab[RG_MAXE];  // row offsets of a (low 16 bits) and b (high 16 bits) in the tile
+    float acc[RG_MAXE][4];
 #pragma unroll
-    for (int e = 0; e < 4; e++) acc[e] = make_double2(0.0, 0.0);
-    for (long long mt = m0; mt < m1; mt += RTW) {
-        for (int u = threadIdx.x; u < RT * RTW; u += blockDim.x) {
-            const int r = u / RTW, cc = u % RTW;
-            const long long m = mt + cc;
-            const bool in = m < m1;
-            sa[r][cc] = (in && a0 + r < j) ? A[(long long)(a0 + r) * ldA + m] : make_double2(0.0, 0.0);
-            sb[r][cc] = (in && b0 + r < j) ? A[(long long)(b0 + r) * ldA + m] : make_double2(0.0, 0.0);
+    for (int i = 0; i < RG_MAXE; i++) {
+        int e = threadIdx.x + RG_THREADS * i, a = 0;
+        while (a < j && e >= j - a) {
+            e -= j - a;
+            a++;
+        }
+        eab[i] = a < j ? (a * (RG_T + 1)) | ((a + e) * (RG_T + 1)) << 16 : 0;
+        acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    }
+    const long long m0 = (long long)blockIdx.x * chunk, m1 = m0 + chunk < M ? m0 + chunk : M;
+    for (long long mt = m0; mt < m1; mt += RG_T) {
+        __syncthreads();
+        for (int u = threadIdx.x; u < j * RG_T; u += RG_THREADS) {
+            const int r = u / RG_T, c = u % RG_T;
+            const long long m = mt + c;
+            double2 v = m < m1 ? A[(long long)r * ldA + m] : make_double2(0.0, 0.0);
+            v.x *= sc;
+            v.y *= sc;
+            st[r * (RG_T + 1) + c] =
+                DF ? split_c(v) : make_float4(__double2float_rn(v.x), __double2float_rn(v.y), 0.f, 0.f);
         }
         __syncthreads();
-#pragma unroll 4
-        for (int cc = 0; cc < RTW; cc++) {
-            const double2 x = sa[ty][cc];
+        const int nc = m1 - mt < RG_T ? (int)(m1 - mt) : RG_T;
+        for (int c = 0; c < nc; c++) {
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const double2 y = sb[4 * tx + e][cc];
-                acc[e].x = fma(x.x, y.x, fma(x.y, y.y, acc[e].x));
-                acc[e].y = fma(x.y, y.x, fma(-x.x, y.y, acc[e].y));
+            for (int i = 0; i < RG_MAXE; i++) {
+                if (RG_THREADS * i >= ne) break;
+                if ((int)threadIdx.x + RG_THREADS * i < ne) {
+                    const float4 x = st[(eab[i] & 0xFFFF) + c], y = st[(eab[i] >> 16) + c];
+                    if (DF) {
+                        // x conj(y) = conj(y) x
+                        df_cmac(acc[i][0], acc[i][1], acc[i][2], acc[i][3], y.x, y.y, y.z, y.w, x.x, x.y, x.z, x.w);
+                    } else {
+                        acc[i][0] = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[i][0]));
+                        acc[i][2] = fmaf(x.y, y.x, fmaf(-x.x, y.y, acc[i][2]));
+                    }
+                }
             }
         }
-        __syncthreads();
     }
-    const int a = a0 + ty;
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-        const int b = b0 + 4 * tx + e;
-        if (a < j && b < j) part[((long long)blockIdx.x * j + a) * j + b] = acc[e];
+    for (int i = 0; i < RG_MAXE; i++) {
+        if ((int)threadIdx.x + RG_THREADS * i < ne)
+            part[((long long)blockIdx.x * j + (eab[i] & 0xFFFF) / (RG_T + 1)) * j + (eab[i] >> 16) / (RG_T + 1)] =
+                make_double2((double)acc[i][0] + (double)acc[i][1], (double)acc[i][2] + (double)acc[i][3]);
     }
 }
 
-// G[a][b] = sum over chunks in order (a <= b), G[b][a] = conj(G[a][b]).
+// G[a][b] = sum over the chunks' partial sums (a <= b), G[b][a] =
+// conj(G[a][b]).  One warp per entry: lane l adds chunks l, l + 32, ... in
+// order, then a fixed butterfly combines the lanes (deterministic).
 __global__ void k_gram_reduce(const double2 *__restrict__ part, int j, int nchunk, double2 *__restrict__ G) {
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < j * j; u += gridDim.x * blockDim.x) {
-        const int a = u / j, b = u % j;
-        if (a > b) continue;
-        double2 s = make_double2(0.0, 0.0);
-        for (int c = 0; c < nchunk; c++) {
-            const double2 x = part[((long long)c * j + a) * j + b];
-            s.x += x.x;
-            s.y += x.y;
+    const int ne = j * (j + 1) / 2, lane = threadIdx.x & 31;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ne; w += (gridDim.x * blockDim.x) >> 5) {
+        int e = w, a = 0;
+        while (e >= j - a) {
+            e -= j - a;
+            a++;
         }
-        if (a == b) s.y = 0.0;
-        G[a * j + b] = s;
-        G[b * j + a] = make_double2(s.x, -s.y);
-    }
-}
-
-// Jacobi eigen-decomposition of the Hermitian G (j x j, row-major), V <- V J
-// accumulated on top of the identity.  On return G's diagonal holds the
-// eigenvalues.  One block of 256 threads; *sweeps = sweeps taken.
-__global__ void __launch_bounds__(256) k_jacobi(double2 *__restrict__ G, double2 *__restrict__ V, int j,
-                                                int max_sweeps, int *sweeps) {
-    __shared__ int sp[128], sq[128];
-    __shared__ double sc[128], ss[128], sre[128], sim[128];
-    __shared__ double red[2][8];
-    __shared__ int s_stop;
-    const int npad = j + (j & 1), np2 = npad / 2;
-    for (int u = threadIdx.x; u < j * j; u += blockDim.x)
-        V[u] = make_double2((u / j) == (u % j) ? 1.0 : 0.0, 0.0);
-    __syncthreads();
-    int sw = 0;
-    for (; sw < max_sweeps; sw++) {
-        // convergence: off-diagonal Frobenius mass against the total
-        double off = 0.0, tot = 0.0;
-        for (int u = threadIdx.x; u < j * j; u += blockDim.x) {
-            const double2 g = G[u];
-            const double m2 = g.x * g.x + g.y * g.y;
-            tot += m2;
-            if ((u / j) != (u % j)) off += m2;
+        const int b = a + e;
+        double sx = 0.0, sy = 0.0;
+        for (int c = lane; c < nchunk; c += 32) {
+            const double2 x = part[((long long)c * j + a) * j + b];
+            sx += x.x;
+            sy += x.y;
         }
         for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, o);
-            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
         }
-        if ((threadIdx.x & 31) == 0) {
-            red[0][threadIdx.x >> 5] = off;
-            red[1][threadIdx.x >> 5] = tot;
+        if (lane == 0) {
+            if (a == b) sy = 0.0;
+            G[a * j + b] = make_double2(sx, sy);
+            G[b * j + a] = make_double2(sx, -sy);
         }
+    }
+}
+
+// ------------------------------------------------------------------ Jacobi
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+template <typename T> __device__ __forceinline__ T cx(double re, double im);
+template <> __device__ __forceinline__ float2 cx<float2>(double re, double im) {
+    return make_float2((float)re, (float)im);
+}
+template <> __device__ __forceinline__ double2 cx<double2>(double re, double im) { return make_double2(re, im); }
+
+template <typename T> __device__ __forceinline__ T cmul_t(T a, T b) {  // a b
+    T r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename T> __device__ __forceinline__ T cmulc_t(T a, T b) {  // a conj(b)
+    T r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+
+// Hermitian Jacobi on G (j x j, FP64 input, row-major) in precision R.
+// V starts as the identity (Vinit == nullptr) or as Vinit and ends in Vg
+// (FP64).  VS: V in shared memory (else in Vg, global; R = double only).
+// The eigenvalues (diag of the rotated G) go to lam; stats (optional) gets
+// the sweeps and the rotations applied.  Dynamic shared memory: G (j^2
+// complex R) followed by V when VS.
+template <typename R, bool VS>
+__global__ void __launch_bounds__(RJ_THREADS) k_jacobi(const double2 *__restrict__ Gin, const double2 *__restrict__ Vinit,
+                                                       double2 *__restrict__ Vg, int j, double eps, int max_sweeps,
+                                                       double *__restrict__ lam, int *__restrict__ stats) {
+    using T = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char jsm[];
+    T *G = reinterpret_cast<T *>(jsm);
+    T *Vs = G + j * j;
+    __shared__ int sp[RJ_PAIRS], sq[RJ_PAIRS];
+    __shared__ R sc[RJ_PAIRS], ss[RJ_PAIRS];
+    __shared__ T sph[RJ_PAIRS];
+    __shared__ int s_rot;
+    const int npad = j + (j & 1), np2 = npad / 2;
+    for (int u = threadIdx.x; u < j * j; u += blockDim.x) {
+        const double2 g = Gin[u];
+        G[u] = cx<T>(g.x, g.y);
+        const bool d = (u / j) == (u % j);
+        const double2 v = Vinit ? Vinit[u] : make_double2(d ? 1.0 : 0.0, 0.0);
+        if (VS) Vs[u] = cx<T>(v.x, v.y);
+        else Vg[u] = v;
+    }
+    __syncthreads();
+    T *V = VS ? Vs : reinterpret_cast<T *>(Vg);
+    const R e = (R)eps;
+    int sw = 0, nrot = 0;
+    for (; sw < max_sweeps; sw++) {
+        if (threadIdx.x == 0) s_rot = 0;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double o2 = 0.0, t2 = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-                o2 += red[0][w];
-                t2 += red[1][w];
-            }
-            s_stop = !(o2 > 1e-30 * t2);
-        }
-        __syncthreads();
-        if (s_stop) break;
         for (int step = 0; step < npad - 1; step++) {
             // round robin: position 0 fixed, the others rotate by one per step
-            if (threadIdx.x < np2) {
+            if ((int)threadIdx.x < np2) {
                 const int i = threadIdx.x;
                 auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (npad - 1); };
                 int p = at(i), q = at(npad - 1 - i);
-                if (p > q) { int t = p; p = q; q = t; }
-                double c = 1.0, s = 0.0, pr = 1.0, pi = 0.0;
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                R c = 1, s = 0;
+                T ph = cx<T>(1.0, 0.0);
                 if (q < j) {
-                    const double2 g = G[p * j + q];
-                    const double ag = sqrt(g.x * g.x + g.y * g.y);
-                    const double a = G[p * j + p].x, b = G[q * j + q].x;
-                    if (ag > 0.0 && ag > 1e-18 * sqrt(fabs(a * b))) {
-                        const double tau = (b - a) / (2.0 * ag);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                    const T g = G[p * j + q];
+                    const R ag = sqrt(g.x * g.x + g.y * g.y);
+                    const R a = G[p * j + p].x, b = G[q * j + q].x;
+                    if (ag > (R)0 && ag > e * sqrt(fabs(a * b))) {
+                        const R tau = (b - a) / (2 * ag);
+                        const R at_ = fabs(tau);
+                        R t = at_ > (R)1e15 ? (R)0.5 / at_ : (R)1 / (at_ + sqrt((R)1 + tau * tau));
+                        if (tau < (R)0) t = -t;
+                        c = (R)1 / sqrt((R)1 + t * t);
                         s = t * c;
-                        pr = g.x / ag;
-                        pi = g.y / ag;
+                        ph.x = g.x / ag;
+                        ph.y = g.y / ag;
+                        if (s != (R)0) atomicAdd(&s_rot, 1);
                     }
                 }
                 sp[i] = p;
                 sq[i] = q;
                 sc[i] = c;
                 ss[i] = s;
-                sre[i] = pr;
-                sim[i] = pi;
+                sph[i] = ph;
             }
             __syncthreads();
             // left: rows p, q of G <- J^H (rows)
             for (int u = threadIdx.x; u < np2 * j; u += blockDim.x) {
                 const int i = u / j, r = u % j;
+                const R s = ss[i];
+                if (s == (R)0) continue;
                 const int p = sp[i], q = sq[i];
-                if (q >= j || ss[i] == 0.0) continue;
-                const double c = sc[i], s = ss[i];
-                const double2 ph = make_double2(sre[i], sim[i]);
-                const double2 gp = G[p * j + r], gq = G[q * j + r];
-                const double2 e1 = cmul(ph, gq);                        // e^{i phi} G_qr
-                const double2 e2 = cmulc(gp, ph);                       // e^{-i phi} G_pr
-                G[p * j + r] = make_double2(c * gp.x - s * e1.x, c * gp.y - s * e1.y);
-                G[q * j + r] = make_double2(s * e2.x + c * gq.x, s * e2.y + c * gq.y);
+                const R c = sc[i];
+                const T ph = sph[i];
+                const T gp = G[p * j + r], gq = G[q * j + r];
+                const T e1 = cmul_t(ph, gq);   // e^{i phi} G_qr
+                const T e2 = cmulc_t(gp, ph);  // e^{-i phi} G_pr
+                T np, nq;
+                np.x = c * gp.x - s * e1.x;
+                np.y = c * gp.y - s * e1.y;
+                nq.x = s * e2.x + c * gq.x;
+                nq.y = s * e2.y + c * gq.y;
+                G[p * j + r] = np;
+                G[q * j + r] = nq;
             }
             __syncthreads();
             // right: columns p, q of G and V <- (.) J
-            for (int u = threadIdx.x; u < np2 * j; u += blockDim.x) {
-                const int i = u / j, r = u % j;
+            for (int u = threadIdx.x; u < 2 * np2 * j; u += blockDim.x) {
+                const int w = u / (np2 * j), uu = u % (np2 * j);
+                const int i = uu / j, r = uu % j;
+                const R s = ss[i];
+                if (s == (R)0) continue;
                 const int p = sp[i], q = sq[i];
-                if (q >= j || ss[i] == 0.0) continue;
-                const double c = sc[i], s = ss[i];
-                const double2 ph = make_double2(sre[i], sim[i]);
-#pragma unroll
-                for (int w = 0; w < 2; w++) {
-                    double2 *Mx = w ? V : G;
-                    const double2 xp = Mx[r * j + p], xq = Mx[r * j + q];
-                    const double2 f1 = cmulc(xq, ph);                   // e^{-i phi} x_q
-                    const double2 f2 = cmul(ph, xp);                    // e^{i phi} x_p
-                    Mx[r * j + p] = make_double2(c * xp.x - s * f1.x, c * xp.y - s * f1.y);
-                    Mx[r * j + q] = make_double2(s * f2.x + c * xq.x, s * f2.y + c * xq.y);
-                }
+                const R c = sc[i];
+                const T ph = sph[i];
+                T *Mx = w ? V : G;
+                const T xp = Mx[r * j + p], xq = Mx[r * j + q];
+                const T f1 = cmulc_t(xq, ph);  // e^{-i phi} x_q
+                const T f2 = cmul_t(ph, xp);   // e^{i phi} x_p
+                T np, nq;
+                np.x = c * xp.x - s * f1.x;
+                np.y = c * xp.y - s * f1.y;
+                nq.x = s * f2.x + c * xq.x;
+                nq.y = s * f2.y + c * xq.y;
+                Mx[r * j + p] = np;
+                Mx[r * j + q] = nq;
             }
             __syncthreads();
         }
+        const int any = s_rot;
+        nrot += any;
+        __syncthreads();
+        if (!any) break;
     }
-    if (threadIdx.x == 0 && sweeps) *sweeps = sw;
+    if (VS)
+        for (int u = threadIdx.x; u < j * j; u += blockDim.x) Vg[u] = make_double2((double)Vs[u].x, (double)Vs[u].y);
+    for (int a = threadIdx.x; a < j; a += blockDim.x) lam[a] = (double)G[a * j + a].x;
+    if (threadIdx.x == 0 && stats) {
+        stats[0] = sw;    // sweeps with at least one rotation
+        stats[1] = nrot;  // rotations applied
+    }
 }
 
-// B = W^H A for W (j x j) and A (j x M): B[a][m] = sum_l conj(W[l][a]) A[l][m].
-__global__ void __launch_bounds__(256) k_transform(const double2 *__restrict__ W, const double2 *__restrict__ A,
-                                                   long long ldA, int j, long long M, double2 *__restrict__ B,
-                                                   long long ldB) {
-    extern __shared__ double2 sw[];  // j x j
-    for (int u = threadIdx.x; u < j * j; u += blockDim.x) sw[u] = W[u];
-    __syncthreads();
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
-        for (int a0 = 0; a0 < j; a0 += 8) {
-            double2 acc[8];
+// ----------------------------------------------------- Newton-Schulz step
+// E = V^H V: E[r][c] = sum_l conj(V[l][r]) V[l][c].  Block r, thread c.
+__global__ void k_vhv(const double2 *__restrict__ V, int j, double2 *__restrict__ E) {
+    const int r = blockIdx.x, c = threadIdx.x;
+    if (c >= j) return;
+    double sx = 0.0, sy = 0.0;
+    for (int l = 0; l < j; l++) {
+        const double2 a = V[l * j + r], b = V[l * j + c];
+        sx = fma(a.x, b.x, fma(a.y, b.y, sx));
+        sy = fma(a.x, b.y, fma(-a.y, b.x, sy));
+    }
+    E[r * j + c] = make_double2(sx, sy);
+}
+
+// Vn = V (3I - E) / 2: Vn[r][c] = 1.5 V[r][c] - 0.5 sum_l V[r][l] E[l][c].
+// With Vs != nullptr the result is also written split into FP32 pairs.
+__global__ void k_ns_update(const double2 *__restrict__ V, const double2 *__restrict__ E, int j,
+                            double2 *__restrict__ Vn, float4 *__restrict__ Vs) {
+    const int r = blockIdx.x, c = threadIdx.x;
+    if (c >= j) return;
+    double sx = 0.0, sy = 0.0;
+    for (int l = 0; l < j; l++) {
+        const double2 a = V[r * j + l], b = E[l * j + c];
+        sx = fma(a.x, b.x, fma(-a.y, b.y, sx));
+        sy = fma(a.x, b.y, fma(a.y, b.x, sy));
+    }
+    const double2 v = V[r * j + c];
+    const double2 o = make_double2(1.5 * v.x - 0.5 * sx, 1.5 * v.y - 0.5 * sy);
+    Vn[r * j + c] = o;
+    if (Vs) Vs[r * j + c] = split_c(o);
+}
+
+// ------------------------------------------------------------- transform
+// B[a][m] = sum_l conj(V[l][a]) C[l][m] (times the scale) in double-float.
+// Lane = column within a tile of 32, warp w = rows a = w + 8 i.  The C tile
+// (j x 32, split) sits in shared memory; V (split) is read with warp-wide
+// broadcast loads.
+__global__ void __launch_bounds__(RT_THREADS) k_transform_df(const float4 *__restrict__ Vsp, const double2 *__restrict__ C,
+                                                             long long ldC, int j, long long M,
+                                                             const int *__restrict__ emax, double2 *__restrict__ B,
+                                                             long long ldB) {
+    extern __shared__ float4 tsm[];  // j x 32
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double sc = c_scale(emax);
+    for (long long mt = (long long)blockIdx.x * 32; mt < M; mt += (long long)gridDim.x * 32) {
+        __syncthreads();
+        for (int u = threadIdx.x; u < j * 32; u += RT_THREADS) {
+            const int r = u >> 5, c = u & 31;
+            const long long m = mt + c;
+            double2 v = m < M ? C[(long long)r * ldC + m] : make_double2(0.0, 0.0);
+            v.x *= sc;
+            v.y *= sc;
+            tsm[u] = split_c(v);
+        }
+        __syncthreads();
+        float acc[RT_ROWS][4];
 #pragma unroll
-            for (int e = 0; e < 8; e++) acc[e] = make_double2(0.0, 0.0);
-            for (int l = 0; l < j; l++) {
-                const double2 x = A[(long long)l * ldA + m];
+        for (int i = 0; i < RT_ROWS; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+        for (int l = 0; l < j; l++) {
+            const float4 x = tsm[l * 32 + lane];
 #pragma unroll
-                for (int e = 0; e < 8; e++) {
-                    if (a0 + e < j) {
-                        const double2 w = sw[l * j + a0 + e];
-                        acc[e].x = fma(w.x, x.x, fma(w.y, x.y, acc[e].x));
-                        acc[e].y = fma(w.x, x.y, fma(-w.y, x.x, acc[e].y));
-                    }
+            for (int i = 0; i < RT_ROWS; i++) {
+                const int a = w + 8 * i;
+                if (a < j) {
+                    const float4 v = __ldg(Vsp + l * j + a);
+                    df_cmac(acc[i][0], acc[i][1], acc[i][2], acc[i][3], v.x, v.y, v.z, v.w, x.x, x.y, x.z, x.w);
                 }
             }
+        }
+        const long long m = mt + lane;
+        if (m < M) {
 #pragma unroll
-            for (int e = 0; e < 8; e++)
-                if (a0 + e < j) B[(long long)(a0 + e) * ldB + m] = acc[e];
+            for (int i = 0; i < RT_ROWS; i++) {
+                const int a = w + 8 * i;
+                if (a < j)
+                    B[(long long)a * ldB + m] =
+                        make_double2((double)acc[i][0] + (double)acc[i][1], (double)acc[i][2] + (double)acc[i][3]);
+            }
         }
     }
 }
 
-// After pass 2: V = V1 V2, eigenvalues lam = diag(G2); order by decreasing
-// eigenvalue (ties: lower index first), sigma = sqrt(max(lam, 0)), and each
-// column of V scaled so that its entry of largest magnitude (lowest row among
-// equals) is real and positive.  One block.
-__global__ void __launch_bounds__(256) k_recon_finish(const double2 *__restrict__ V1, const double2 *__restrict__ V2,
-                                                      const double2 *__restrict__ G2, int j, double2 *__restrict__ Vout,
+// ---------------------------------------------------------------- finish
+// Order by decreasing eigenvalue (ties: lower index first), sigma =
+// sqrt(max(lam, 0)) 2^E, and each column of V scaled so that its entry of
+// largest magnitude (lowest row among equals) is real and positive.
+__global__ void __launch_bounds__(256) k_recon_finish(const double *__restrict__ lam, const double2 *__restrict__ Vin,
+                                                      int j, const int *__restrict__ emax, double2 *__restrict__ Vout,
                                                       double *__restrict__ sigma, int *__restrict__ perm) {
     for (int i = threadIdx.x; i < j; i += blockDim.x) {
-        const double li = G2[i * j + i].x;
+        const double li = lam[i];
         int rank = 0;
         for (int t = 0; t < j; t++) {
-            const double lt = G2[t * j + t].x;
+            const double lt = lam[t];
             rank += (lt > li) || (lt == li && t < i);
         }
         perm[rank] = i;
     }
     __syncthreads();
+    const double unscale = 1.0 / c_scale(emax);  // 2^E, exact
     for (int c = threadIdx.x; c < j; c += blockDim.x) {
         const int src = perm[c];
-        const double lam = G2[src * j + src].x;
-        sigma[c] = sqrt(lam > 0.0 ? lam : 0.0);
-        // column src of V1 V2, then its phase
+        const double l = lam[src];
+        sigma[c] = sqrt(l > 0.0 ? l : 0.0) * unscale;
         int pbest = 0;
         double abest = -1.0;
         for (int r = 0; r < j; r++) {
-            double2 s = make_double2(0.0, 0.0);
-            for (int l = 0; l < j; l++) {
-                const double2 x = cmul(V1[r * j + l], V2[l * j + src]);
-                s.x += x.x;
-                s.y += x.y;
-            }
-            Vout[r * j + c] = s;
-            const double a = sqrt(s.x * s.x + s.y * s.y);
+            const double2 v = Vin[r * j + src];
+            const double a = sqrt(v.x * v.x + v.y * v.y);
             if (a > abest) {
                 abest = a;
                 pbest = r;
             }
         }
-        const double2 vp = Vout[pbest * j + c];
+        const double2 vp = Vin[pbest * j + src];
         const double2 f = abest > 0.0 ? make_double2(vp.x / abest, -vp.y / abest) : make_double2(1.0, 0.0);
-        for (int r = 0; r < j; r++) Vout[r * j + c] = cmul(Vout[r * j + c], f);
+        for (int r = 0; r < j; r++) Vout[r * j + c] = cmul_t(Vin[r * j + src], f);
         Vout[pbest * j + c] = make_double2(abest, 0.0);
     }
 }
@@ -286,7 +442,7 @@ __global__ void __launch_bounds__(256) k_recon_basis(const double2 *__restrict__
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         double2 s = make_double2(0.0, 0.0);
         for (int l = 0; l < j; l++) {
-            const double2 x = cmul(Q[(long long)l * ldQ + i], V[l * j + c]);
+            const double2 x = cmul_t(Q[(long long)l * ldQ + i], V[l * j + c]);
             s.x += x.x;
             s.y += x.y;
         }
@@ -294,43 +450,144 @@ __global__ void __launch_bounds__(256) k_recon_basis(const double2 *__restrict__
     }
 }
 
-size_t recon_workspace(int j, long long M) {
-    const long long nchunk = (M + kGramChunk - 1) / kGramChunk;
-    return (size_t)nchunk * j * j * 16 + (size_t)j * M * 16 + (size_t)6 * j * j * 16 + (size_t)j * 4 + 4096;
+// ---------------------------------------------------------------- host side
+namespace {
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+        n = 148;
+    return n;
+}
+long long gram_chunk(long long M, int nsm) {
+    const long long nchunk = 2LL * nsm;
+    long long ch = (M + nchunk - 1) / nchunk;
+    ch = (ch + RG_T - 1) / RG_T * RG_T;
+    return ch < RG_T ? RG_T : ch;
+}
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct ReconWs {
+    int *emax, *stats;
+    double2 *part, *B, *G1, *G2, *Va, *Vb, *E;
+    float4 *Vsp;
+    double *lam;
+    int *perm;
+    size_t total;
+};
+ReconWs carve(void *base, int j, long long M, int nsm) {
+    const long long chunk = gram_chunk(M, nsm);
+    const long long nchunk = (M + chunk - 1) / chunk;
+    const size_t jj = (size_t)j * j;
+    ReconWs w;
+    char *p = (char *)base;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *r = p ? p + off : nullptr;
+        off += up256(bytes);
+        return r;
+    };
+    w.emax = (int *)take(16);
+    w.stats = (int *)take(16);
+    w.part = (double2 *)take((size_t)nchunk * jj * 16);
+    w.B = (double2 *)take((size_t)j * M * 16);
+    w.G1 = (double2 *)take(jj * 16);
+    w.G2 = (double2 *)take(jj * 16);
+    w.Va = (double2 *)take(jj * 16);
+    w.Vb = (double2 *)take(jj * 16);
+    w.E = (double2 *)take(jj * 16);
+    w.Vsp = (float4 *)take(jj * 16);
+    w.lam = (double *)take((size_t)j * 8);
+    w.perm = (int *)take((size_t)j * 4);
+    w.total = off;
+    return w;
 }
 
-// Pass 1 + pass 2 on C; sigma and the phase-normalised V land in sigma / V.
-cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M, void *ws, double *sigma,
-                             double2 *V, int *sweeps, cudaStream_t s) {
-    const long long chunk = kGramChunk;
-    const int nchunk = (int)((M + chunk - 1) / chunk);
-    char *w = (char *)ws;
-    double2 *part = (double2 *)w;
-    w += (size_t)nchunk * j * j * 16;
-    double2 *B = (double2 *)w;
-    w += (size_t)j * M * 16;
-    double2 *G1 = (double2 *)w, *V1 = G1 + j * j, *G2 = V1 + j * j, *V2 = G2 + j * j;
-    w += (size_t)6 * j * j * 16;
-    int *perm = (int *)w;
-    const int nt = (j + RT - 1) / RT;
-    dim3 gg(nchunk, nt, nt);
-    const int gr = (j * j + 255) / 256;
-    k_gram_part<<<gg, 256, 0, s>>>(C, ldC, j, M, chunk, part);
-    k_gram_reduce<<<gr, 256, 0, s>>>(part, j, nchunk, G1);
-    k_jacobi<<<1, 256, 0, s>>>(G1, V1, j, 40, sweeps);
-    const size_t tsm = (size_t)j * j * 16;
-    if (tsm > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
-        if (e != cudaSuccess) return e;
-    }
-    long long gt = (M + 255) / 256;
-    if (gt > 152 * 4) gt = 152 * 4;
-    k_transform<<<(int)gt, 256, tsm, s>>>(V1, C, ldC, j, M, B, M);
-    k_gram_part<<<gg, 256, 0, s>>>(B, M, j, M, chunk, part);
-    k_gram_reduce<<<gr, 256, 0, s>>>(part, j, nchunk, G2);
-    k_jacobi<<<1, 256, 0, s>>>(G2, V2, j, 40, sweeps ? sweeps + 1 : nullptr);
-    k_recon_finish<<<1, 256, 0, s>>>(V1, V2, G2, j, V, sigma, perm);
+template <typename R, bool VS> size_t jacobi_smem(int j) {
+    return (size_t)j * j * sizeof(typename Cx<R>::T) * (VS ? 2 : 1);
+}
+
+template <typename R, bool VS>
+cudaError_t launch_jacobi(const double2 *G, const double2 *Vinit, double2 *Vg, int j, double eps, double *lam, int *sw,
+                          cudaStream_t s) {
+    const size_t sm = jacobi_smem<R, VS>(j);
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi<R, VS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_jacobi<R, VS><<<1, RJ_THREADS, sm, s>>>(G, Vinit, Vg, j, eps, 60, lam, sw);
     return cudaGetLastError();
+}
+}  // namespace
+
+size_t recon_workspace(int j, long long M) { return carve(nullptr, j, M, sm_count()).total; }
+
+// Pass 1 + pass 2 on C; sigma and the phase-normalised V land in sigma / V.
+// stats (optional, device, 4 ints): sweeps and rotations of the pass-1 and
+// pass-2 Jacobi iterations.  ev (optional, 7 events) is recorded at the start
+// and after each phase: pass-1 Gram, pass-1 Jacobi, Newton-Schulz, transform,
+// pass-2 Gram, pass-2 Jacobi + ordering.
+cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M, void *ws, double *sigma,
+                             double2 *V, int *stats, cudaEvent_t *ev, cudaStream_t s) {
+    if (j < 1 || j > kMaxJ) return cudaErrorInvalidValue;
+    const int nsm = sm_count();
+    const ReconWs w = carve(ws, j, M, nsm);
+    const long long chunk = gram_chunk(M, nsm);
+    const int nchunk = (int)((M + chunk - 1) / chunk);
+    const int gr = (j * (j + 1) / 2 + 7) / 8;  // one warp per entry, 8 warps per block
+    const size_t gsm = (size_t)j * (RG_T + 1) * 16;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_gram_tri<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_gram_tri<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)) !=
+            cudaSuccess)
+        return e;
+    auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+    if ((e = mark(0)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.emax, 0, 16, s)) != cudaSuccess) return e;
+    long long gx = (M + 255) / 256;
+    if (gx > 2LL * nsm) gx = 2LL * nsm;
+    k_max_exp<<<dim3((unsigned)gx, (unsigned)(j < 8 ? j : 8)), 256, 0, s>>>(C, ldC, j, M, w.emax);
+    // pass 1: FP32 Gram and Jacobi
+    k_gram_tri<false><<<nchunk, RG_THREADS, gsm, s>>>(C, ldC, j, M, chunk, w.emax, w.part);
+    k_gram_reduce<<<gr, 256, 0, s>>>(w.part, j, nchunk, w.G1);
+    if ((e = mark(1)) != cudaSuccess) return e;
+    if ((e = launch_jacobi<float, true>(w.G1, nullptr, w.Va, j, 0x1p-22, w.lam, w.stats, s)) != cudaSuccess) return e;
+    if ((e = mark(2)) != cudaSuccess) return e;
+    // V1 unitary to FP64 precision: three Newton-Schulz steps (the FP32
+    // Jacobi leaves ||V^H V - I|| near 1e-5; each step squares it)
+    double2 *cur = w.Va, *nxt = w.Vb;
+    const int nt = (j + 31) / 32 * 32;
+    for (int it = 0; it < 3; it++) {
+        k_vhv<<<j, nt, 0, s>>>(cur, j, w.E);
+        k_ns_update<<<j, nt, 0, s>>>(cur, w.E, j, nxt, it == 2 ? w.Vsp : nullptr);
+        double2 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if ((e = mark(3)) != cudaSuccess) return e;
+    // pass 2: B = V1^H C, G2 = B B^H in double-float, Jacobi in FP64 from V1
+    const size_t tsm = (size_t)j * 32 * 16;
+    if ((e = cudaFuncSetAttribute(k_transform_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) != cudaSuccess)
+        return e;
+    long long gt = (M + 31) / 32;
+    if (gt > 4LL * nsm) gt = 4LL * nsm;
+    k_transform_df<<<(unsigned)gt, RT_THREADS, tsm, s>>>(w.Vsp, C, ldC, j, M, w.emax, w.B, M);
+    if ((e = mark(4)) != cudaSuccess) return e;
+    k_gram_tri<true><<<nchunk, RG_THREADS, gsm, s>>>(w.B, M, j, M, chunk, nullptr, w.part);
+    k_gram_reduce<<<gr, 256, 0, s>>>(w.part, j, nchunk, w.G2);
+    if ((e = mark(5)) != cudaSuccess) return e;
+    int dev = 0, maxsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return e;
+    const bool vs = jacobi_smem<double, true>(j) + 8192 <= (size_t)maxsm;
+    e = vs ? launch_jacobi<double, true>(w.G2, cur, nxt, j, 0x1p-52, w.lam, w.stats + 2, s)
+           : launch_jacobi<double, false>(w.G2, cur, nxt, j, 0x1p-52, w.lam, w.stats + 2, s);
+    if (e != cudaSuccess) return e;
+    k_recon_finish<<<1, 256, 0, s>>>(w.lam, nxt, j, w.emax, V, sigma, w.perm);
+    if (stats && (e = cudaMemcpyAsync(stats, w.stats, 4 * sizeof(int), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return mark(6);
 }
 
 cudaError_t launch_recon_basis(const double2 *Q, long long ldQ, long long N, int j, const double2 *V, int k,

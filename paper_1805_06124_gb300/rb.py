@@ -87,11 +87,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.rb_project.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_void_p, c_ll]
     lib.rb_reconstruct.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_double, c_void_p,
                                    c_ll, c_void_p, c_void_p, ctypes.POINTER(c_int)]
+    lib.rb_reconstruct_stats.argtypes = [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]
     lib.rb_greedy_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(Problem), c_double, c_int,
                                       ctypes.POINTER(Result)]
     lib.rb_greedy_batched.restype = c_int
     for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_greedy_split", "rb_project",
-              "rb_reconstruct"):
+              "rb_reconstruct", "rb_reconstruct_stats"):
         getattr(lib, f).restype = c_int
     _LIB = lib
     return lib
@@ -357,6 +358,17 @@ class RB:
                                             _ld(C) if j else M, float(tau2), X.data_ptr(), N, sigma.data_ptr(),
                                             V.data_ptr(), ctypes.byref(k)))
         return dict(sigma=sigma[:j], V=V[:j, :j], k=int(k.value), X=X[:k.value])
+
+    RECON_PHASES = ("gram1_fp32", "jacobi1_fp32", "newton_schulz", "transform_df32", "gram2_df32",
+                    "jacobi2_fp64", "basis")
+
+    def reconstruct_stats(self):
+        """Phase times (ms; needs timing=True) and Jacobi sweeps/rotations of
+        the last reconstruct call."""
+        ms = (c_double * 7)()
+        cnt = (c_int * 4)()
+        self._check(self.lib.rb_reconstruct_stats(self._h, ms, cnt))
+        return dict(ms=dict(zip(self.RECON_PHASES, list(ms))), sweeps=(cnt[0], cnt[2]), rotations=(cnt[1], cnt[3]))
 
 
 class MLP:

@@ -193,3 +193,20 @@ def test_full_size_sampled(ctx):
     out = check_against_oracle(c, Q, C, 20)
     assert out["k"] == 20
     c.close()
+
+
+def test_phase_timing_and_counts():
+    """With timing on, every phase of the last call has a CUDA-event time and
+    the Jacobi counts are consistent (pass 2 starts from the pass-1 basis and
+    needs few sweeps)."""
+    from paper_1805_06124_gb300 import rb
+    c = rb.RB(device=0, timing=True)
+    S = synth.chirps(1024, 2048, seed=0)
+    Q, C, g = greedy_on_gpu(c, S, 1e-10, 300)
+    j = g["k"]
+    c.reconstruct(Q, C, 0.0)
+    st = c.reconstruct_stats()
+    assert all(v > 0.0 for v in st["ms"].values()), st
+    assert 1 <= st["sweeps"][0] <= 60 and 1 <= st["sweeps"][1] <= 8, st
+    assert st["rotations"][0] >= j * (j - 1) // 2 and st["rotations"][1] > 0, st
+    c.close()
