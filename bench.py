@@ -383,6 +383,47 @@ def run_recon_once(args):
         "sigma_1": float(out["sigma"][0]), "sigma_j": float(out["sigma"][j - 1])}), flush=True)
 
 
+def run_eim_once(args):
+    """Empirical interpolation and out-of-sample validation on the FP64
+    greedy's basis for chirps N x M (seed 1, tol 1e-12): rb_eim (nodes, V, B,
+    V^-1) and rb_validate on 65,536 chirps of seed 7 (projection through the
+    tensor-core path, then the per-snapshot errors); one warm-up call each,
+    medians of --steps timed calls (host clock around the synchronous calls)."""
+    import statistics
+    import torch
+    from paper_1805_06124_gb300 import rb, synth
+    c = rb.RB(device=0)
+    S = c.generate(*synth.chirp_params(args.M, 1), args.N)
+    g = c.greedy(S, 1e-12, 800)
+    del S
+    torch.cuda.empty_cache()
+    Q = g["Q"]
+    Mt = 65536
+    T = c.generate(*synth.chirp_params(Mt, 7), args.N)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(max(args.steps, 1)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return r, 1e3 * statistics.median(ts)
+
+    e, t_eim = timed(lambda: c.eim(Q))
+    v, t_val = timed(lambda: c.validate(Q, T, e["nodes"], e["Vinv"]))
+    ep, ee = v["err_proj"], v["err_eim"]
+    print(json.dumps({
+        "workload": f"EIM nodes + validation on the greedy basis, chirps N={args.N} x M={args.M} seed 1, tol 1e-12; "
+                    f"validation set {Mt} chirps seed 7",
+        "k": int(Q.shape[0]), "eim_ms": round(t_eim, 3), "validate_ms": round(t_val, 3),
+        "validate_GBps": round(16.0 * args.N * Mt / (t_val * 1e-3) / 1e9, 1),
+        "max_err_proj": float(ep.max()), "max_err_eim": float(ee.max()),
+        "median_err_eim_over_proj": float((ee / ep.clamp_min(1e-300)).median())}), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_1805_06124_gb300 import rb, synth
@@ -521,7 +562,7 @@ def main():
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate", "split", "project", "batched",
-                                                                "recon"])
+                                                                "recon", "eim"])
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--k", type=int, default=53)
     ap.add_argument("--project-fp64", action="store_true")
@@ -534,6 +575,8 @@ def main():
         run_project_once(args)
     elif args.workload == "recon":
         run_recon_once(args)
+    elif args.workload == "eim":
+        run_eim_once(args)
     elif args.workload == "batched":
         import torch
         from paper_1805_06124_gb300 import rb, synth

@@ -227,6 +227,40 @@ rb_status rb_reconstruct(rb_ctx *ctx, const void *Q, long long N, int j, long lo
  * Errors: RB_EINVAL (ctx NULL). */
 rb_status rb_reconstruct_stats(const rb_ctx *ctx, double *ms, int *counts);
 
+/* Empirical interpolation (EI) nodes of a basis: the greedy EIM / DEIM rule
+ * that the paper's software applies after the greedy (Sec. 6.1; the algorithm
+ * is the cited one, not printed in the paper).  p_1 = argmax_x |q_1(x)|; for
+ * i > 1, p_i = argmax over the grid points not yet chosen of the residual of
+ * q_i after interpolating it on p_1..p_{i-1} with q_1..q_{i-1} (lowest index
+ * among equal maxima).  Computed as Gaussian elimination with partial
+ * pivoting on the N x k basis matrix, FP64.
+ *   Q: device complex128 N x k column-major (ldQ >= N) -- rb_result.Q, 1 <= k <= N;
+ *   nodes: device int64[k] (grid indices p_1..p_k);
+ *   V: device complex128 k x k row-major, V[m*k + l] = q_l(p_m), or NULL;
+ *   B: device complex128 N x k column-major (ldB >= N), or NULL: the
+ *      interpolant I[f](x) = sum_m B[x + m*ldB] f(p_m), with B V = Q;
+ *   Vinv: device complex128 k x k row-major, V^{-1} (= Q^H B, valid for an
+ *      orthonormal Q), or NULL -- the input of rb_validate.
+ * Synchronises the stream.  Errors: RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_ESTATE
+ * (a residual vanished on every free grid point: the basis is dependent). */
+rb_status rb_eim(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ, long long *nodes, void *V, void *B,
+                 long long ldB, void *Vinv);
+
+/* Out-of-sample validation of a basis and its interpolant (Sec. 6.1) on Mt
+ * snapshots T (device complex128, N x Mt column-major, ldT >= N):
+ *   err_proj[j] = ||t_j - Q Q^H t_j||^2, formed as ||t_j||^2 - ||Q^H t_j||^2
+ *                 (Eq. (Residual)) with Q^H T from rb_project;
+ *   err_eim[j]  = ||t_j - I[t_j]||^2 for the EI nodes and V^{-1} of rb_eim,
+ *                 formed as err_proj[j] + ||V^{-1} t_j(P) - Q^H t_j||^2 (exact
+ *                 for an orthonormal Q: I reproduces span(Q) and t - Q Q^H t
+ *                 is orthogonal to it), or NULL for projection errors only.
+ * Outputs are device double[Mt].  k <= RB_VALIDATE_MAX_K when err_eim is
+ * requested.  Synchronises the stream.  Errors: RB_EINVAL, RB_ENOMEM,
+ * RB_ECUDA, RB_ETIMEOUT (tensor-core wait, from the projection). */
+#define RB_VALIDATE_MAX_K 3000
+rb_status rb_validate(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ, const long long *nodes,
+                      const void *Vinv, const void *T, long long Mt, long long ldT, double *err_proj, double *err_eim);
+
 /* Same as rb_greedy, but S, every output array of *out, and the result are in
  * HOST memory (pinned or pageable).  The call copies S to the device and the
  * outputs back inside the call; device workspace is owned by the context. */

@@ -45,13 +45,13 @@ def eim(E, forced=None) -> dict:
 
     With ``forced`` (a node sequence from another implementation) step i uses
     forced[i] as p_i; the oracle still reports its own argmax ``own[i]`` and
-    the squared residuals at both (``r2_own[i]``, ``r2_forced[i]``) so that a
-    caller can judge near ties.  Returns nodes, V (k, k), B (N, k), and the
+    the squared residuals at both (``r2_own[i]``, ``r2_forced[i]``) and the
+    runner-up (``r2_second[i]``) so that a caller can judge near ties.  Returns nodes, V (k, k), B (N, k), and the
     squared residual maxima."""
     E = np.asarray(E, dtype=np.complex128)
     k, N = E.shape
     P: list[int] = []
-    own, r2_own, r2_forced = [], [], []
+    own, r2_own, r2_second, r2_forced = [], [], [], []
     for i in range(k):
         e = E[i]
         if i == 0:
@@ -64,13 +64,14 @@ def eim(E, forced=None) -> dict:
         p_own = _argmax_free(a, P)
         own.append(p_own)
         r2_own.append(float(a[p_own]))
+        r2_second.append(float(a[_argmax_free(a, P + [p_own])]) if N - len(P) > 1 else -1.0)
         p = p_own if forced is None else int(forced[i])
         r2_forced.append(float(a[p]))
         P.append(p)
     V = E[:, P].T if k else np.zeros((0, 0), np.complex128)  # V[m, l] = e_l(p_m)
     B = np.linalg.solve(V.T, E).T if k else np.zeros((N, 0), np.complex128)
     return dict(nodes=np.asarray(P, dtype=np.int64), V=V, B=B, own=np.asarray(own, dtype=np.int64),
-                r2_own=np.asarray(r2_own), r2_forced=np.asarray(r2_forced))
+                r2_own=np.asarray(r2_own), r2_second=np.asarray(r2_second), r2_forced=np.asarray(r2_forced))
 
 
 def interpolate(B, nodes, F) -> np.ndarray:

@@ -30,6 +30,8 @@ struct rb_ctx {
     size_t stage_cap = 0;
     void *gen = nullptr;         // rb_generate tables
     size_t gen_cap = 0;
+    void *aux = nullptr;         // rb_validate coefficients
+    size_t aux_cap = 0;
     rbk::DevState *st_host = nullptr;  // pinned copy of the device state
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> sweep_ev;
@@ -171,6 +173,7 @@ void rb_destroy(rb_ctx *ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->gen) cudaFree(ctx->gen);
+    if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -283,6 +286,58 @@ rb_status rb_reconstruct(rb_ctx *ctx, const void *Q, long long N, int j, long lo
             ctx->recon_ms[i] = t;
         }
     *k_out = k;
+    return RB_OK;
+}
+
+rb_status rb_eim(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ, long long *nodes, void *V, void *B,
+                 long long ldB, void *Vinv) {
+    if (!ctx) return RB_EINVAL;
+    if (N < 1 || k < 0 || k > N || ldQ < N || (k > 0 && (!Q || !nodes)) || (B && ldB < N) || !aligned(Q, 16) ||
+        !aligned(V, 16) || !aligned(B, 16) || !aligned(Vinv, 16) || !aligned(nodes, 8))
+        return fail(ctx, RB_EINVAL, "rb_eim: bad arguments (N=%lld k=%d ldQ=%lld ldB=%lld)", N, k, ldQ, ldB);
+    if (k == 0) return RB_OK;
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t wsb = (rbk::eim_workspace(N, k) + 255) & ~(size_t)255;
+    const size_t bws = (!B && Vinv) ? (((size_t)N * k * 16 + 255) & ~(size_t)255) : 0;
+    rb_status s = ensure(ctx, &ctx->gen, &ctx->gen_cap, wsb + bws + 256);
+    if (s != RB_OK) return s;
+    double2 *Bw = B ? (double2 *)B : (Vinv ? (double2 *)((char *)ctx->gen + wsb) : nullptr);
+    const long long ldBw = B ? ldB : N;
+    int *flag = (int *)((char *)ctx->gen + wsb + bws);
+    cudaStream_t sm = ctx->stream;
+    RB_CK(cudaMemsetAsync(flag, 0, sizeof(int), sm), "memset flag");
+    RB_CK(rbk::launch_eim((const double2 *)Q, N, k, ldQ, ctx->gen, nodes, (double2 *)V, Bw, ldBw, flag, sm), "eim");
+    if (Vinv)  // V^{-1} = Q^H B for an orthonormal basis
+        RB_CK(rbk::launch_project((const double2 *)Q, N, k, ldQ, Bw, k, ldBw, (double2 *)Vinv, k, sm), "eim V^-1");
+    int hf = 0;
+    RB_CK(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, sm), "flag copy");
+    RB_CK(cudaStreamSynchronize(sm), "stream sync");
+    if (hf) return fail(ctx, RB_ESTATE, "rb_eim: a residual vanished on every free grid point (dependent basis)");
+    return RB_OK;
+}
+
+rb_status rb_validate(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ, const long long *nodes,
+                      const void *Vinv, const void *T, long long Mt, long long ldT, double *err_proj, double *err_eim) {
+    if (!ctx) return RB_EINVAL;
+    if (N < 1 || k < 0 || Mt < 0 || ldQ < N || ldT < N || (Mt > 0 && (!T || !err_proj)) || (k > 0 && !Q) ||
+        (err_eim && k > 0 && (!nodes || !Vinv)) || (err_eim && k > RB_VALIDATE_MAX_K) || !aligned(Q, 16) ||
+        !aligned(T, 16) || !aligned(Vinv, 16))
+        return fail(ctx, RB_EINVAL, "rb_validate: bad arguments (N=%lld k=%d Mt=%lld)", N, k, Mt);
+    if (Mt == 0) return RB_OK;
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    double2 *Cv = nullptr;
+    if (k > 0) {
+        rb_status s = ensure(ctx, &ctx->aux, &ctx->aux_cap, (size_t)k * Mt * 16);
+        if (s != RB_OK) return s;
+        Cv = (double2 *)ctx->aux;
+        s = rb_project(ctx, Q, N, k, ldQ, T, Mt, ldT, Cv, Mt);
+        if (s != RB_OK) return s;
+    }
+    cudaStream_t sm = ctx->stream;
+    RB_CK(rbk::launch_validate((const double2 *)T, N, Mt, ldT, Cv, Mt, k, nodes, (const double2 *)Vinv, err_proj,
+                               err_eim, sm),
+          "validate");
+    RB_CK(cudaStreamSynchronize(sm), "stream sync");
     return RB_OK;
 }
 

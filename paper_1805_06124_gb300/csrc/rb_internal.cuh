@@ -376,6 +376,13 @@ cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int 
 cudaError_t launch_split_finish(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
 size_t lo_pieces_bytes(long long N, int kcap);
 size_t recon_workspace(int j, long long M);
+long long eim_blocks(long long N);
+size_t eim_workspace(long long N, int k);
+cudaError_t launch_eim(const double2 *Q, long long N, int k, long long ldQ, void *ws, long long *nodes, double2 *V,
+                       double2 *B, long long ldB, int *flag, cudaStream_t s);
+cudaError_t launch_validate(const double2 *T, long long N, long long Mt, long long ldT, const double2 *C, long long ldC,
+                            int k, const long long *nodes, const double2 *Vinv, double *err_proj, double *err_eim,
+                            cudaStream_t s);
 cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M, void *ws, double *sigma, double2 *V,
                              int *stats, cudaEvent_t *ev, cudaStream_t s);
 cudaError_t launch_recon_basis(const double2 *Q, long long ldQ, long long N, int j, const double2 *V, int k,

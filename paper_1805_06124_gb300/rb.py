@@ -88,11 +88,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.rb_reconstruct.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_double, c_void_p,
                                    c_ll, c_void_p, c_void_p, ctypes.POINTER(c_int)]
     lib.rb_reconstruct_stats.argtypes = [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]
+    lib.rb_eim.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_void_p, c_void_p, c_ll, c_void_p]
+    lib.rb_validate.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_void_p, c_void_p, c_ll, c_ll,
+                                c_void_p, c_void_p]
     lib.rb_greedy_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(Problem), c_double, c_int,
                                       ctypes.POINTER(Result)]
     lib.rb_greedy_batched.restype = c_int
     for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_greedy_split", "rb_project",
-              "rb_reconstruct", "rb_reconstruct_stats"):
+              "rb_reconstruct", "rb_reconstruct_stats", "rb_eim", "rb_validate"):
         getattr(lib, f).restype = c_int
     _LIB = lib
     return lib
@@ -358,6 +361,60 @@ class RB:
                                             _ld(C) if j else M, float(tau2), X.data_ptr(), N, sigma.data_ptr(),
                                             V.data_ptr(), ctypes.byref(k)))
         return dict(sigma=sigma[:j], V=V[:j, :j], k=int(k.value), X=X[:k.value])
+
+    def eim(self, Q, want_V: bool = True, want_B: bool = True, want_Vinv: bool = True):
+        """Empirical interpolation nodes of the basis rows of Q (k, N): nodes
+        (k,) int64, V (k, k) with V[m, l] = q_l(p_m), B (k, N) with row m =
+        the interpolant's m-th cardinal function (I[f] = sum_m f(p_m) B[m]),
+        Vinv (k, k) = V^{-1}."""
+        torch = _torch()
+        _check2d(Q, torch.complex128, "Q")
+        k, N = Q.shape
+        dev = Q.device
+        kk = max(k, 1)
+        with torch.cuda.stream(self.stream):
+            nodes = torch.empty(kk, dtype=torch.int64, device=dev)
+            V = torch.empty((kk, kk), dtype=torch.complex128, device=dev) if want_V else None
+            B = torch.empty((kk, N), dtype=torch.complex128, device=dev) if want_B else None
+            Vi = torch.empty((kk, kk), dtype=torch.complex128, device=dev) if want_Vinv else None
+        ptr = lambda t: t.data_ptr() if t is not None else None
+        self._check(self.lib.rb_eim(self._h, Q.data_ptr(), N, k, _ld(Q) if k else N, nodes.data_ptr(), ptr(V),
+                                    ptr(B), N, ptr(Vi)))
+        out = dict(nodes=nodes[:k])
+        if want_V:
+            out["V"] = V[:k, :k]
+        if want_B:
+            out["B"] = B[:k]
+        if want_Vinv:
+            out["Vinv"] = Vi[:k, :k]
+        return out
+
+    def validate(self, Q, T, nodes=None, Vinv=None):
+        """Out-of-sample errors of the basis rows of Q (k, N) on the snapshot
+        rows of T (Mt, N): err_proj and, given rb_eim's nodes and Vinv,
+        err_eim (squared 2-norms, float64 (Mt,))."""
+        torch = _torch()
+        _check2d(T, torch.complex128, "T")
+        Mt, N = T.shape
+        k = 0 if Q is None else Q.shape[0]
+        if k:
+            _check2d(Q, torch.complex128, "Q")
+            if Q.shape[1] != N:
+                raise ValueError("Q and T disagree on N")
+        want_eim = nodes is not None
+        if want_eim and k and (Vinv is None or nodes.numel() != k):
+            raise ValueError("err_eim needs the k nodes and Vinv of rb_eim")
+        with torch.cuda.stream(self.stream):
+            ep = torch.empty(max(Mt, 1), dtype=torch.float64, device=T.device)
+            ee = torch.empty(max(Mt, 1), dtype=torch.float64, device=T.device) if want_eim else None
+        self._check(self.lib.rb_validate(self._h, Q.data_ptr() if k else None, N, k, _ld(Q) if k else N,
+                                         nodes.data_ptr() if (want_eim and k) else None,
+                                         Vinv.data_ptr() if (want_eim and k) else None, T.data_ptr(), Mt,
+                                         _ld(T) if Mt else N, ep.data_ptr(), ee.data_ptr() if want_eim else None))
+        out = dict(err_proj=ep[:Mt])
+        if want_eim:
+            out["err_eim"] = ee[:Mt]
+        return out
 
     RECON_PHASES = ("gram1_fp32", "jacobi1_fp32", "newton_schulz", "transform_df32", "gram2_df32",
                     "jacobi2_fp64", "basis")

@@ -69,3 +69,5 @@ def test_bad_options_rejected_before_any_device_call(lib):
     assert L.rb_project(None, None, 1, 1, 1, None, 1, 1, None, 1) == rb.EINVAL
     k = ctypes.c_int(-1)
     assert L.rb_reconstruct(None, None, 1, 1, 1, None, 1, 1, 0.0, None, 1, None, None, ctypes.byref(k)) == rb.EINVAL
+    assert L.rb_eim(None, None, 1, 1, 1, None, None, None, 1, None) == rb.EINVAL
+    assert L.rb_validate(None, None, 1, 1, 1, None, None, None, 1, 1, None, None) == rb.EINVAL
