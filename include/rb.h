@@ -150,6 +150,22 @@ rb_status rb_split(rb_ctx *ctx, const void *S, long long N, long long M, long lo
 rb_status rb_greedy(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS,
                     double tol, int kmax, rb_result *out);
 
+/* rb_greedy resumed from a checkpoint: the first k0 entries of out->Q (rows),
+ * out->pivots, out->C (rows, columns 0..Mc-1), out->err_curve and out->rdiag
+ * hold an earlier call's results (a saved checkpoint, or the same buffers
+ * after a call that stopped at kmax = k0), and the loop continues from basis
+ * size k0 with the same outputs, status and stopping rule as rb_greedy.
+ * Columns Mc..M-1 of S are new (the iterative enrichment of the paper's
+ * software, Sec. 6.1: snapshots added after a validation pass): their first
+ * k0 coefficients are computed with rb_project before the loop.  The error
+ * bookkeeping of Eq. (Residual) is rebuilt from C with error-free squares and
+ * a compensated sum, so a resumed run may differ from an uninterrupted one
+ * in the last bits of the errors (and hence at exact pivot ties).  Requires
+ * out->C; 0 <= k0 <= min(kmax, N, M); the pivots must be distinct columns of
+ * S.  k0 = 0 is rb_greedy.  Returns as rb_greedy. */
+rb_status rb_greedy_resume(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol, int kmax,
+                           int k0, long long Mc, rb_result *out);
+
 /* Split-precision RB-greedy on S stored as complex64 hi + lo (see rb_split;
  * column j at hi + j*ld and lo + j*ld, ld even, both 16-byte aligned; N <= 2^22).
  * Every sweep reads hi only: c~ = q^H hi with FP32 FMAs summed against a

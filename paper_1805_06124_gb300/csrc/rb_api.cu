@@ -5,6 +5,7 @@
 // iters_per_sync iterations (IMGS launches + one sweep each), then reads the
 // 100-byte device state once.  Kernels queued after the stop flag was set
 // return immediately.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -350,8 +351,10 @@ rb_status rb_reconstruct_stats(const rb_ctx *ctx, double *ms, int *counts) {
     return RB_OK;
 }
 
+// k0 > 0: resume from a checkpoint of k0 vectors held in out (Q, pivots, C,
+// err_curve, rdiag rows 0..k0-1; C complete for all M columns).
 static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol,
-                               int kmax, rb_result *out) {
+                               int kmax, rb_result *out, int k0 = 0) {
     const rb_options &o = ctx->opt;
     const int variant = o.sweep;
     const bool df = (variant == RB_SWEEP_DF32);
@@ -433,10 +436,15 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
         RB_CK(rbk::launch_split(p.S, N, M, ldS, (float2 *)p.hi, (float2 *)p.lo, ldH, p.norm2, sm), "split");
     else
         RB_CK(rbk::launch_norms(p.S, N, M, ldS, p.norm2, sm), "norms");
-    RB_CK(rbk::launch_init(p, G, sm), "init");
-    nlaunch += 2;
+    if (k0 > 0) {
+        RB_CK(rbk::launch_resume(p, k0, G, sm), "resume");
+        nlaunch += 4;
+    } else {
+        RB_CK(rbk::launch_init(p, G, sm), "init");
+        nlaunch += 2;
+    }
 
-    int it = 0;
+    int it = k0;
     bool stopped = false;
     while (!stopped) {
         for (int t = 0; t < o.iters_per_sync && it < kcap; t++, it++) {
@@ -473,7 +481,7 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     out->ms_total = ms;
     out->ms_sweep = 0.0;
     if (timing) {
-        for (int i = 0; i < hs.n_sweeps && i < it; i++) {
+        for (int i = k0; i < k0 + hs.n_sweeps && i < it; i++) {
             float t = 0.f;
             cudaEventElapsedTime(&t, ctx->sweep_ev[2 * i], ctx->sweep_ev[2 * i + 1]);
             out->ms_sweep += t;
@@ -942,6 +950,35 @@ rb_status rb_greedy(rb_ctx *ctx, const void *S, long long N, long long M, long l
         return fail(ctx, RB_EINVAL, "complex128 arrays must be 16-byte aligned");
     RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     return greedy_device(ctx, S, N, M, ldS, tol, kmax, out);
+}
+
+rb_status rb_greedy_resume(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol, int kmax,
+                           int k0, long long Mc, rb_result *out) {
+    rb_status s = check_greedy_args(ctx, S, N, M, ldS, tol, kmax, out);
+    if (s != RB_OK) return s;
+    const long long minNM = N < M ? N : M;
+    if (k0 < 0 || k0 > kmax || k0 > minNM || Mc < 0 || Mc > M || (k0 > 0 && !out->C))
+        return fail(ctx, RB_EINVAL, "rb_greedy_resume: need 0 <= k0 <= min(kmax, N, M), 0 <= Mc <= M and C (k0=%d)", k0);
+    if (!aligned(S, 16) || !aligned(out->Q, 16) || (out->C && !aligned(out->C, 16)))
+        return fail(ctx, RB_EINVAL, "complex128 arrays must be 16-byte aligned");
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (k0 == 0) return greedy_device(ctx, S, N, M, ldS, tol, kmax, out);
+    // the checkpoint's pivots: distinct columns of S
+    std::vector<long long> piv(k0);
+    RB_CK(cudaMemcpyAsync(piv.data(), out->pivots, (size_t)k0 * 8, cudaMemcpyDeviceToHost, ctx->stream), "pivot copy");
+    RB_CK(cudaStreamSynchronize(ctx->stream), "stream sync");
+    std::vector<long long> sorted(piv);
+    std::sort(sorted.begin(), sorted.end());
+    for (int l = 0; l < k0; l++)
+        if (sorted[l] < 0 || sorted[l] >= M || (l > 0 && sorted[l] == sorted[l - 1]))
+            return fail(ctx, RB_EINVAL, "rb_greedy_resume: checkpoint pivots must be distinct columns of S");
+    // coefficients of the columns the checkpoint has not seen
+    if (Mc < M) {
+        s = rb_project(ctx, out->Q, N, k0, out->ldQ, (const double2 *)S + Mc * ldS, M - Mc, ldS,
+                       (double2 *)out->C + Mc, out->ldC);
+        if (s != RB_OK) return s;
+    }
+    return greedy_device(ctx, S, N, M, ldS, tol, kmax, out, k0);
 }
 
 rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long N, long long M, long long ld,

@@ -162,6 +162,93 @@ __global__ void __launch_bounds__(kThreads) k_init(Prob p) {
     }
 }
 
+// Resume from a checkpoint of k0 basis vectors (Q rows, pivots and C rows
+// 0..k0-1 given): acc_j is rebuilt from C with error-free squares and a
+// compensated sum (the k_recompute formula), picked is cleared, and norms are
+// checked.
+__global__ void __launch_bounds__(kThreads) k_resume_acc(Prob p, int k0) {
+    DevState *st = p.st;
+    int bad = 0;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < p.M;
+         j += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0, e = 0.0;
+        for (int l = 0; l < k0; l++) {
+            const double2 c = p.C[(long long)l * p.ldC + j];
+            const double x = c.x * c.x, ex = fma(c.x, c.x, -x);
+            const double y = c.y * c.y, ey = fma(c.y, c.y, -y);
+            double t = s + x, b = t - s;
+            e += ((s - (t - b)) + (x - b)) + ex;
+            s = t;
+            t = s + y;
+            b = t - s;
+            e += ((s - (t - b)) + (y - b)) + ey;
+            s = t;
+        }
+        p.acc[j] = s + e;
+        p.picked[j] = 0;
+        if (!isfinite(p.norm2[j]) || !isfinite(s + e)) bad = 1;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->nonfinite, 1);
+}
+
+// Mark the checkpoint's pivots (validated on the host: distinct, in [0, M)).
+__global__ void k_resume_mark(Prob p, int k0) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < k0; l += gridDim.x * blockDim.x) p.picked[p.pivots[l]] = 1;
+}
+
+// After k_resume_mark: the argmax of err_j = ||s_j||^2 - acc_j over unpicked
+// columns, err_curve[k0], the next pivot and the stopping rule, as the last
+// block of a sweep would leave them after iteration k0 - 1.
+__global__ void __launch_bounds__(kThreads) k_resume_pick(Prob p, int k0) {
+    DevState *st = p.st;
+    double be = -INFINITY;
+    long long bi = kNoIdx;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < p.M;
+         j += (long long)gridDim.x * blockDim.x) {
+        const double e = p.norm2[j] - p.acc[j];
+        if (!p.picked[j] && better(e, j, be, bi)) {
+            be = e;
+            bi = j;
+        }
+    }
+    block_best(be, bi);
+    if (threadIdx.x == 0) {
+        p.bpart_err[blockIdx.x] = be;
+        p.bpart_idx[blockIdx.x] = bi;
+    }
+    if (!last_block(&st->ticket_init)) return;
+    be = -INFINITY;
+    bi = kNoIdx;
+    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        double e = __ldcg(p.bpart_err + b);
+        long long i = __ldcg(p.bpart_idx + b);
+        if (better(e, i, be, bi)) { be = e; bi = i; }
+    }
+    block_best(be, bi);
+    if (threadIdx.x == 0) {
+        st->ticket_init = 0;
+        st->k = k0;
+        st->switch_iter = -1;
+        const double emax = bi == kNoIdx ? 0.0 : be;
+        p.err_curve[k0] = emax;
+        st->J = bi;
+        st->errJ = emax;
+        if (ld_volatile(&st->nonfinite)) {
+            st->status = RB_ENONFINITE;
+            st->stop = 1;
+        } else if (bi == kNoIdx || emax < p.tol) {
+            st->status = RB_OK;
+            st->stop = 1;
+        } else if (k0 >= p.kmax) {
+            st->status = RB_KMAX_REACHED;
+            st->stop = 1;
+        } else if (k0 >= p.minNM) {
+            st->status = RB_OK;
+            st->stop = 1;
+        }
+    }
+}
+
 __global__ void k_final_err(Prob p, double *final_err) {
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < p.M;
          j += (long long)gridDim.x * blockDim.x)
@@ -204,6 +291,14 @@ cudaError_t launch_norms(const double2 *S, long long N, long long M, long long l
 cudaError_t launch_init(const Prob &p, int grid, cudaStream_t s) {
     int g = grid_for(p.M, kThreads, grid);
     k_init<<<g, kThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resume(const Prob &p, int k0, int grid, cudaStream_t s) {
+    const int g = grid_for(p.M, kThreads, grid);
+    k_resume_acc<<<g, kThreads, 0, s>>>(p, k0);
+    k_resume_mark<<<(k0 + 255) / 256, 256, 0, s>>>(p, k0);
+    k_resume_pick<<<g, kThreads, 0, s>>>(p, k0);
     return cudaGetLastError();
 }
 

@@ -365,6 +365,7 @@ cudaError_t launch_split(const double2 *S, long long N, long long M, long long l
 cudaError_t launch_norms(const double2 *S, long long N, long long M, long long ldS, double *norm2,
                          cudaStream_t s);
 cudaError_t launch_init(const Prob &p, int grid, cudaStream_t s);
+cudaError_t launch_resume(const Prob &p, int k0, int grid, cudaStream_t s);
 cudaError_t launch_sweep(const Prob &p, int variant, int grid, cudaStream_t s);
 cudaError_t launch_recompute(const Prob &p, int period, int grid, cudaStream_t s);
 cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s, int *nlaunch);

@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.rb_reconstruct.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_double, c_void_p,
                                    c_ll, c_void_p, c_void_p, ctypes.POINTER(c_int)]
     lib.rb_reconstruct_stats.argtypes = [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]
+    lib.rb_greedy_resume.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int, c_int, c_ll,
+                                     ctypes.POINTER(Result)]
     lib.rb_eim.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_void_p, c_void_p, c_ll, c_void_p]
     lib.rb_validate.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_void_p, c_void_p, c_ll, c_ll,
                                 c_void_p, c_void_p]
@@ -95,7 +97,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                       ctypes.POINTER(Result)]
     lib.rb_greedy_batched.restype = c_int
     for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_greedy_split", "rb_project",
-              "rb_reconstruct", "rb_reconstruct_stats", "rb_eim", "rb_validate"):
+              "rb_reconstruct", "rb_reconstruct_stats", "rb_eim", "rb_validate", "rb_greedy_resume"):
         getattr(lib, f).restype = c_int
     _LIB = lib
     return lib
@@ -237,6 +239,38 @@ class RB:
             r, bufs = self._alloc_result(N, M, kmax, S.device, want_C, want_final_err)
         st = self._check(self.lib.rb_greedy(self._h, S.data_ptr(), N, M, _ld(S), float(tol), int(kmax),
                                             ctypes.byref(r)))
+        return self._pack(st, r, bufs)
+
+    def greedy_resume(self, S, tol: float, kmax: int, checkpoint: dict, Mc: int | None = None,
+                      want_final_err: bool = True):
+        """RB-greedy on device snapshots S (M, N) continued from ``checkpoint``
+        (a result dict or a loaded checkpoint: Q (k0, N), pivots (k0,), C (k0,
+        Mc), err_curve (k0 + 1,), rdiag (k0,); arrays or tensors).  Columns
+        Mc..M-1 of S are new snapshots (default Mc = C's column count)."""
+        torch = _torch()
+        _check2d(S, torch.complex128, "S")
+        M, N = S.shape
+        dev = S.device
+        as_t = lambda x, dt: torch.as_tensor(x, dtype=dt).to(dev)
+        Q0 = as_t(checkpoint["Q"], torch.complex128)
+        k0 = int(Q0.shape[0])
+        piv0 = as_t(checkpoint["pivots"], torch.int64)[:k0]
+        C0 = as_t(checkpoint["C"], torch.complex128)[:k0]
+        ec0 = as_t(checkpoint["err_curve"], torch.float64)[:k0]
+        rd0 = as_t(checkpoint["rdiag"], torch.float64)[:k0]
+        Mc = int(C0.shape[1]) if Mc is None else int(Mc)
+        if k0 > kmax or Q0.shape[1] != N or C0.shape[1] < Mc or Mc > M or piv0.numel() != k0:
+            raise ValueError("checkpoint does not match S / kmax")
+        with torch.cuda.stream(self.stream):
+            r, bufs = self._alloc_result(N, M, kmax, dev, True, want_final_err)
+            if k0:
+                bufs["Q"][:k0] = Q0
+                bufs["pivots"][:k0] = piv0
+                bufs["C"][:k0, :Mc] = C0[:, :Mc]
+                bufs["err_curve"][:k0] = ec0
+                bufs["rdiag"][:k0] = rd0
+        st = self._check(self.lib.rb_greedy_resume(self._h, S.data_ptr(), N, M, _ld(S), float(tol), int(kmax), k0, Mc,
+                                                   ctypes.byref(r)))
         return self._pack(st, r, bufs)
 
     def greedy_split(self, hi, lo, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True):
