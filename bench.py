@@ -424,6 +424,40 @@ def run_eim_once(args):
         "median_err_eim_over_proj": float((ee / ep.clamp_min(1e-300)).median())}), flush=True)
 
 
+def run_resume_once(args):
+    """Resume and enrichment at N x M chirps (seed 1, tol 1e-12): (a) one
+    uninterrupted FP64-form call; (b) a call stopped at k0 = 16 plus
+    rb_greedy_resume to the end; (c) enrichment: a basis built on the first
+    M/2 columns, then resumed on all M columns (the new half projected onto it
+    first).  Device time of each call from the library's CUDA events (ms_total;
+    the projection in (c) is timed from the host around the synchronous call)."""
+    import torch
+    from paper_1805_06124_gb300 import rb, synth
+    c = rb.RB(device=0)
+    S = c.generate(*synth.chirp_params(args.M, 1), args.N)
+    c.greedy(S, 1e-12, 800)                                   # warm-up
+    full = c.greedy(S, 1e-12, 800)
+    part = c.greedy(S, 1e-12, 16)
+    res = c.greedy_resume(S, 1e-12, 800, part)
+    half = args.M // 2
+    g1 = c.greedy(S[:half], 1e-12, 800)
+    c.greedy_resume(S, 1e-12, 800, g1, Mc=half)               # warm-up: workspace and slice planes allocated
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    enr = c.greedy_resume(S, 1e-12, 800, g1, Mc=half)
+    torch.cuda.synchronize()
+    t_enr = 1e3 * (time.perf_counter() - t0)
+    same = bool(torch.equal(res["pivots"], full["pivots"]))
+    print(json.dumps({
+        "workload": f"greedy resume / enrichment, chirps N={args.N} x M={args.M} seed 1, tol 1e-12",
+        "uninterrupted": {"k": full["k"], "ms": round(full["ms_total"], 3)},
+        "stop_at_16_then_resume": {"k": res["k"], "ms_part": round(part["ms_total"], 3),
+                                   "ms_resume": round(res["ms_total"], 3), "same_pivots": same},
+        "enrichment": {"k_half": g1["k"], "ms_half": round(g1["ms_total"], 3), "k_all": enr["k"],
+                       "ms_resume_device": round(enr["ms_total"], 3), "ms_resume_with_projection": round(t_enr, 3)}}),
+          flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_1805_06124_gb300 import rb, synth
@@ -562,7 +596,7 @@ def main():
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate", "split", "project", "batched",
-                                                                "recon", "eim"])
+                                                                "recon", "eim", "resume"])
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--k", type=int, default=53)
     ap.add_argument("--project-fp64", action="store_true")
@@ -577,6 +611,8 @@ def main():
         run_recon_once(args)
     elif args.workload == "eim":
         run_eim_once(args)
+    elif args.workload == "resume":
+        run_resume_once(args)
     elif args.workload == "batched":
         import torch
         from paper_1805_06124_gb300 import rb, synth
