@@ -31,6 +31,18 @@ constexpr int OZ_KS = 16;        // K per shared-memory stage (double-buffered)
 constexpr int OZ_DRAIN = 512;    // K per exact TMEM chunk
 constexpr int OZ_TCOLS = 512;    // TMEM columns allocated (7 levels x 64 used)
 
+// Slice planes are stored tile by tile in the K-major shared-memory layout the
+// MMAs read (8-row x 16-byte core matrices, see kmajor_off), so that the A
+// tile of one K stage (7 planes x 128 rows x OZ_KS) and the B tile of one
+// column tile (7 planes x 64 rows x OZ_KS) are each one contiguous block that
+// a single bulk copy moves:  block (tile t, stage st, plane s) starts at
+// ((t * nst + st) * OZ_S + s) * R * OZ_KS elements, R = OZ_M or OZ_N.
+__device__ __forceinline__ long long oz_tile_off(long long r, long long kpos, int R, long long nst) {
+    const long long t = r / R, st = kpos / OZ_KS;
+    const int rr = (int)(r % R), kk = (int)(kpos % OZ_KS);
+    return ((t * nst + st) * OZ_S) * (long long)(R * OZ_KS) + (kmajor_off(rr, kk, OZ_KS) >> 1);
+}
+
 __device__ __forceinline__ int scale_exp(double mx) {
     if (!(mx > 0.0)) return 0;
     int e;
@@ -111,77 +123,87 @@ __global__ void k_oz_slice_A(const double2 *__restrict__ Q, long long N, int k, 
     __syncthreads();
     const int E = scale_exp(sm[0]);
     if (threadIdx.x == 0) Ea[l] = E;
-    const long long sstride = Rp * Kp;
+    const long long nst = Kp / OZ_KS;
+    constexpr long long pstride2 = OZ_M * OZ_KS / 2;  // plane stride in BF16 pairs
     for (long long i = threadIdx.x; i < N; i += blockDim.x) {
         double2 v = q[i];
-        __nv_bfloat162 *re = (__nv_bfloat162 *)(As + (long long)(2 * l) * Kp + 2 * i);
-        __nv_bfloat162 *im = (__nv_bfloat162 *)(As + (long long)(2 * l + 1) * Kp + 2 * i);
-        slice7_pair(v.x, v.y, E, re, sstride / 2);
-        slice7_pair(-v.y, v.x, E, im, sstride / 2);
+        __nv_bfloat162 *re = (__nv_bfloat162 *)(As + oz_tile_off(2 * l, 2 * i, OZ_M, nst));
+        __nv_bfloat162 *im = (__nv_bfloat162 *)(As + oz_tile_off(2 * l + 1, 2 * i, OZ_M, nst));
+        slice7_pair(v.x, v.y, E, re, pstride2);
+        slice7_pair(-v.y, v.x, E, im, pstride2);
     }
 }
 
-// B: one block per column j of this batch.  The scale comes from the largest
-// biased exponent (integer max over the IEEE bits, no FP64 work): max|x| <
-// 2^(e_max - 1022), so E = e_max - 1021, as frexp of the maximum would give.
-// K positions past 2N (padding to Kp) are written as zero slices here.
-__global__ void k_oz_slice_B(const double2 *__restrict__ X, long long N, long long Mb, long long ldX, long long Kp,
-                             long long Cp, __nv_bfloat16 *__restrict__ Bs, int *__restrict__ Eb) {
-    const long long j = blockIdx.x;
-    if (j >= Mb) return;
-    const double2 *x = X + j * ldX;
-    unsigned int em = 0;
-    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-        const double2 v = x[i];
-        const unsigned int a = ((unsigned int)(__double_as_longlong(v.x) >> 52)) & 0x7FFu;
-        const unsigned int b = ((unsigned int)(__double_as_longlong(v.y) >> 52)) & 0x7FFu;
-        em = max(em, max(a, b));
-    }
-    __shared__ unsigned int se[32];
-    for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
-    if ((threadIdx.x & 31) == 0) se[threadIdx.x >> 5] = em;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int m = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = max(m, se[w]);
-        se[0] = m;
-    }
-    __syncthreads();
-    const int E = se[0] ? (int)se[0] - 1021 : 0;
-    if (threadIdx.x == 0) Eb[j] = E;
-    const long long sstride = Cp * Kp;
-    const __nv_bfloat162 z2 = __floats2bfloat162_rn(0.f, 0.f);
-    for (long long i = threadIdx.x; i < Kp / 2; i += blockDim.x) {
-        __nv_bfloat162 *o = (__nv_bfloat162 *)(Bs + j * Kp + 2 * i);
-        if (i < N) {
+// B, pass 1: one warp per column j of this batch.  The scale comes from the
+// largest biased exponent (integer max over the IEEE bits, no FP64 work):
+// max|x| < 2^(e_max - 1022), so E = e_max - 1021, as frexp of the maximum
+// would give.
+__global__ void k_oz_exp_B(const double2 *__restrict__ X, long long N, long long Mb, long long ldX, int *__restrict__ Eb) {
+    const int lane = threadIdx.x & 31;
+    for (long long j = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; j < Mb;
+         j += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const double2 *x = X + j * ldX;
+        unsigned int em = 0;
+        for (long long i = lane; i < N; i += 32) {
             const double2 v = x[i];
-            slice7_pair(v.x, v.y, E, o, sstride / 2);
-        } else {
-#pragma unroll
-            for (int sl = 0; sl < OZ_S; sl++) o[sl * (sstride / 2)] = z2;
+            const unsigned int a = ((unsigned int)(__double_as_longlong(v.x) >> 52)) & 0x7FFu;
+            const unsigned int b = ((unsigned int)(__double_as_longlong(v.y) >> 52)) & 0x7FFu;
+            em = max(em, max(a, b));
         }
+        for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+        if (lane == 0) Eb[j] = em ? (int)em - 1021 : 0;
     }
 }
 
-// Asynchronous copy of rows [r0, r0+R) x K [k0, k0+OZ_KS) of the 7 slice
-// planes (row-major, K contiguous) into K-major shared tiles, 16 bytes (one
-// core-matrix row) per cp.async.  The 8 threads of each quarter warp fill the
-// 8 rows of one core matrix (128 contiguous bytes, no bank conflicts).
-__device__ __forceinline__ void oz_stage_async(uint8_t *dst, const __nv_bfloat16 *src, long long plane, long long Kp,
-                                               int R, long long r0, long long k0) {
-    constexpr int per_row = OZ_KS / 8;
-    for (int t = threadIdx.x; t < OZ_S * R * per_row; t += blockDim.x) {
-        int s = t / (R * per_row), rem = t % (R * per_row);
-        int r = (rem & 7) + 8 * (rem / (8 * per_row)), kk = ((rem >> 3) % per_row) * 8;
-        const void *g = src + s * plane + (r0 + r) * Kp + k0 + kk;
-        uint32_t d = smem_u32(dst + s * (R * OZ_KS * 2) + kmajor_off(r, kk, OZ_KS));
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g));
+// B, pass 2: block (column tile ct, range of OZ_SLICE_ST stages).  Thread t
+// slices complex elements 2(t & 3) and 2(t & 3) + 1 of each stage of column
+// 64 ct + (t >> 2): the four threads of a column read 128 contiguous bytes and
+// each warp writes whole 256-byte groups (8 columns x 16 K) of every plane.
+// K positions past 2N and columns Mb..Cp-1 are written as zero slices.
+constexpr int OZ_SLICE_ST = 32;
+
+__global__ void __launch_bounds__(256) k_oz_slice_B(const double2 *__restrict__ X, long long N, long long Mb,
+                                                    long long ldX, long long Kp, const int *__restrict__ Eb,
+                                                    __nv_bfloat16 *__restrict__ Bs) {
+    const long long ct = blockIdx.x, nst = Kp / OZ_KS;
+    const int jj = threadIdx.x >> 2, p0 = (threadIdx.x & 3) * 2;
+    const long long j = ct * OZ_N + jj;
+    const bool live = j < Mb;
+    const int E = live ? Eb[j] : 0;
+    const double2 *x = X + (live ? j : 0) * ldX;
+    constexpr long long pstride2 = OZ_N * OZ_KS / 2;
+    const uint32_t off0 = kmajor_off(jj, 2 * p0, OZ_KS) >> 1, off1 = kmajor_off(jj, 2 * p0 + 2, OZ_KS) >> 1;
+    const __nv_bfloat162 z2 = __floats2bfloat162_rn(0.f, 0.f);
+    const long long s0 = (long long)blockIdx.y * OZ_SLICE_ST, s1 = s0 + OZ_SLICE_ST < nst ? s0 + OZ_SLICE_ST : nst;
+    for (long long st = s0; st < s1; st++) {
+        __nv_bfloat16 *blk = Bs + (ct * nst + st) * (long long)(OZ_S * OZ_N * OZ_KS);
+        const long long i0 = st * (OZ_KS / 2) + p0;
+        double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
+        if (live && i0 < N) v0 = x[i0];
+        if (live && i0 + 1 < N) v1 = x[i0 + 1];
+        __nv_bfloat162 *o0 = (__nv_bfloat162 *)(blk + off0), *o1 = (__nv_bfloat162 *)(blk + off1);
+        if (live && i0 < N) slice7_pair(v0.x, v0.y, E, o0, pstride2);
+        else
+#pragma unroll
+            for (int sl = 0; sl < OZ_S; sl++) o0[sl * pstride2] = z2;
+        if (live && i0 + 1 < N) slice7_pair(v1.x, v1.y, E, o1, pstride2);
+        else
+#pragma unroll
+            for (int sl = 0; sl < OZ_S; sl++) o1[sl * pstride2] = z2;
     }
-    asm volatile("cp.async.commit_group;");
 }
 
 // (hi, lo) += x, both double-float
 __device__ __forceinline__ void dfs_add(float &ah, float &al, float bh, float bl) { df_add(ah, al, bh, bl); }
+
+// Ring of OZ_NBUF stage buffers filled by bulk copies: one thread issues the
+// copies of stage st + 2 (the A and the B block, 28 KB + 14 KB) as soon as the
+// MMAs of stage st - 1, the last user of that buffer, have completed, waits
+// for the bytes of stage st, and issues its 28 MMAs.  "full" barriers count
+// the copied bytes; "done" barriers receive the MMA commits; the n-th phase of
+// buffer b's barriers belongs to stage b + OZ_NBUF n.  At the end of each
+// exact chunk (OZ_DRAIN K values) all threads drain the TMEM levels.
+constexpr int OZ_NBUF = 3;
 
 __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__restrict__ Bs,
                                                  const int *__restrict__ Ea, const int *__restrict__ Eb, int k, long long Mb,
@@ -189,94 +211,105 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict
                                                  long long ldC, long long col_off, int *err) {
     extern __shared__ __align__(1024) uint8_t dsm[];
     constexpr int SA = OZ_S * OZ_M * OZ_KS * 2, SB = OZ_S * OZ_N * OZ_KS * 2;  // 28 KB, 14 KB per buffer
-    uint8_t *sAb[2] = {dsm, dsm + SA};
-    uint8_t *sBb[2] = {dsm + 2 * SA, dsm + 2 * SA + SB};
-    float *acc_h = (float *)(dsm + 2 * (SA + SB));  // 128 x 64 double-float running sums
+    float *acc_h = (float *)(dsm + OZ_NBUF * (SA + SB));  // 128 x 64 double-float running sums
     float *acc_l = acc_h + OZ_M * OZ_N;
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t full[OZ_NBUF], done[OZ_NBUF], cdone;
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5;
-    const long long j0 = (long long)blockIdx.x * OZ_N;
-    const long long r0 = (long long)blockIdx.y * OZ_M;
+    const long long ct = blockIdx.x, rt = blockIdx.y;
+    const long long j0 = ct * OZ_N, r0 = rt * OZ_M;
     for (int t = threadIdx.x; t < OZ_M * OZ_N; t += blockDim.x) acc_h[t] = acc_l[t] = 0.f;
     if (warp == 0) tmem_alloc(&tslot, OZ_TCOLS);
-    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    if (threadIdx.x == 0)
+    {
+        for (int b = 0; b < OZ_NBUF; b++) {
+            mbar_init(&full[b], 1);
+            mbar_init(&done[b], 1);
+        }
+        mbar_init(&cdone, 1);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
     constexpr uint32_t idesc = idesc_bf16_f32(OZ_M, OZ_N);
-    uint32_t phase = 0;
     bool ok = true;
     const long long nst = Kp / OZ_KS;
     constexpr int per_drain = OZ_DRAIN / OZ_KS;
-    const long long planeA = Rp * Kp, planeB = Cp * Kp;
-    oz_stage_async(sAb[0], As, planeA, Kp, OZ_M, r0, 0);
-    oz_stage_async(sBb[0], Bs, planeB, Kp, OZ_N, j0, 0);
-    for (long long st = 0; st < nst; st++) {
-        const int cur = (int)(st & 1);
-        uint8_t *sA = sAb[cur], *sB = sBb[cur];
-        if (st + 1 < nst) {  // prefetch the next stage into the other buffer
-            oz_stage_async(sAb[cur ^ 1], As, planeA, Kp, OZ_M, r0, (st + 1) * OZ_KS);
-            oz_stage_async(sBb[cur ^ 1], Bs, planeB, Kp, OZ_N, j0, (st + 1) * OZ_KS);
-            asm volatile("cp.async.wait_group 2;");
-        } else {
-            asm volatile("cp.async.wait_group 0;");
-        }
-        fence_async_smem();
-        __syncthreads();
-        const bool fresh = (st % per_drain) == 0;
+    auto bufA = [&](long long st) { return dsm + (int)(st % OZ_NBUF) * (SA + SB); };
+    auto bufB = [&](long long st) { return dsm + (int)(st % OZ_NBUF) * (SA + SB) + SA; };
+    auto par = [&](long long st) { return (uint32_t)((st / OZ_NBUF) & 1); };
+    auto load = [&](long long st) {  // thread 0 only
+        uint64_t *fb = &full[st % OZ_NBUF];
+        mbar_expect_tx(fb, SA + SB);
+        bulk_g2s(bufA(st), As + (rt * nst + st) * (long long)(OZ_S * OZ_M * OZ_KS), SA, fb);
+        bulk_g2s(bufB(st), Bs + (ct * nst + st) * (long long)(OZ_S * OZ_N * OZ_KS), SB, fb);
+    };
+    if (threadIdx.x == 0)
+        for (long long st = 0; st < 2 && st < nst; st++) load(st);
+    for (long long cs = 0; cs < nst; cs += per_drain) {
+        const long long ce = cs + per_drain < nst ? cs + per_drain : nst;
         if (threadIdx.x == 0) {
-            tc_fence_after();
-            bool started[OZ_LV];
+            for (long long st = cs; st < ce; st++) {
+                ok = mbar_wait(&full[st % OZ_NBUF], par(st)) && ok;
+                tc_fence_after();
+                // one descriptor per operand and stage; slices and K steps are
+                // constant offsets of its 16-byte address field
+                const uint64_t ad0 = smem_desc(smem_u32(bufA(st)), 128, (OZ_KS / 8) * 128);
+                const uint64_t bd0 = smem_desc(smem_u32(bufB(st)), 128, (OZ_KS / 8) * 128);
+                const uint32_t acc0 = st == cs ? 0u : 1u;  // a chunk's first stage overwrites the levels
 #pragma unroll
-            for (int L = 0; L < OZ_LV; L++) started[L] = !fresh;
+                for (int sa = 0; sa < OZ_S; sa++)
 #pragma unroll
-            for (int sa = 0; sa < OZ_S; sa++)
+                    for (int sb = 0; sb < OZ_S; sb++) {
+                        const int L = sa + sb;  // level - 2
+                        if (L >= OZ_LV) continue;
 #pragma unroll
-                for (int sb = 0; sb < OZ_S; sb++) {
-                    const int L = sa + sb;  // level - 2
-                    if (L >= OZ_LV) continue;
-#pragma unroll
-                    for (int kk = 0; kk < OZ_KS / 16; kk++) {
-                        uint64_t ad = smem_desc(smem_u32(sA) + sa * (OZ_M * OZ_KS * 2) + kk * 256, 128, (OZ_KS / 8) * 128);
-                        uint64_t bd = smem_desc(smem_u32(sB) + sb * (OZ_N * OZ_KS * 2) + kk * 256, 128, (OZ_KS / 8) * 128);
-                        tc_mma_bf16(tmem + (uint32_t)(L * OZ_N), ad, bd, idesc, started[L] ? 1u : 0u);
-                        started[L] = true;
+                        for (int kk = 0; kk < OZ_KS / 16; kk++) {
+                            const uint64_t ad = ad0 + (uint64_t)((sa * (OZ_M * OZ_KS * 2) + kk * 256) >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)((sb * (OZ_N * OZ_KS * 2) + kk * 256) >> 4);
+                            // level L is first reached at sa = 0 (sb = L <= 6)
+                            const uint32_t a = (sa == 0 && kk == 0) ? acc0 : 1u;
+                            tc_mma_bf16(tmem + (uint32_t)(L * OZ_N), ad, bd, idesc, a);
+                        }
                     }
-                }
-            tc_commit(&mbar);
-        }
-        ok = mbar_wait(&mbar, phase) && ok;
-        phase ^= 1;
-        tc_fence_after();
-        __syncthreads();
-        if ((st % per_drain) == per_drain - 1 || st == nst - 1) {
-            // drain: row = TMEM lane; levels combined smallest first, in double-float
-            const int r = threadIdx.x;
-            const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-            for (int c0 = 0; c0 < OZ_N; c0 += 16) {
-                float v[OZ_LV][16];
-#pragma unroll
-                for (int L = 0; L < OZ_LV; L++) tmem_ld16(tmem + lane_off + (uint32_t)(L * OZ_N + c0), v[L]);
-#pragma unroll
-                for (int e = 0; e < 16; e++) {
-                    float th = 0.f, tl = 0.f;
-#pragma unroll
-                    for (int L = OZ_LV - 1; L >= 0; L--) {
-                        // level L+2 carries 2^(-7 (L+2)): an exact power-of-two factor
-                        float x = v[L][e] * __int_as_float((127 - OZ_BITS * (L + 2)) << 23);
-                        dfs_add(th, tl, x, 0.f);
-                    }
-                    float &h = acc_h[r * OZ_N + c0 + e];
-                    float &lo = acc_l[r * OZ_N + c0 + e];
-                    dfs_add(h, lo, th, tl);
+                tc_commit(&done[st % OZ_NBUF]);
+                if (st + 2 < nst) {
+                    if (st >= 1) ok = mbar_wait(&done[(st - 1) % OZ_NBUF], par(st - 1)) && ok;
+                    load(st + 2);
                 }
             }
-            tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
+            tc_commit(&cdone);
         }
+        // drain: every thread waits for the chunk's MMAs (cdone completes once
+        // per chunk; the other threads run at most one chunk behind thread 0,
+        // so the parity of the chunk index is unambiguous), then reads its
+        // TMEM lane; levels combined smallest first, in double-float
+        ok = mbar_wait(&cdone, (uint32_t)((cs / per_drain) & 1)) && ok;
+        tc_fence_after();
+        const int r = threadIdx.x;
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        for (int c0 = 0; c0 < OZ_N; c0 += 16) {
+            float v[OZ_LV][16];
+#pragma unroll
+            for (int L = 0; L < OZ_LV; L++) tmem_ld16(tmem + lane_off + (uint32_t)(L * OZ_N + c0), v[L]);
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                float th = 0.f, tl = 0.f;
+#pragma unroll
+                for (int L = OZ_LV - 1; L >= 0; L--) {
+                    // level L+2 carries 2^(-7 (L+2)): an exact power-of-two factor
+                    float x = v[L][e] * __int_as_float((127 - OZ_BITS * (L + 2)) << 23);
+                    dfs_add(th, tl, x, 0.f);
+                }
+                float &h = acc_h[r * OZ_N + c0 + e];
+                float &lo = acc_l[r * OZ_N + c0 + e];
+                dfs_add(h, lo, th, tl);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
     }
     if (!ok && err) atomicExch(err, 1);
     // write: row r of the tile -> basis vector (r0 + r) / 2, Re or Im part
@@ -337,18 +370,17 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
     __nv_bfloat16 *Bs = As + (size_t)OZ_S * Rp * Kp;
     int *Ea = (int *)(Bs + (size_t)OZ_S * Cp * Kp);
     int *Eb = Ea + k;
-    // zero fill: the A planes (small) and the padded B rows Mb..Cp-1 of each
-    // plane; k_oz_slice_B writes every other B entry, K padding included
+    // zero fill of the A planes (small: rows 2k..Rp-1 and the K padding);
+    // k_oz_slice_B writes every B entry, K padding and padded columns included
     cudaError_t e = cudaMemsetAsync(As, 0, (size_t)OZ_S * Rp * Kp * 2, s);
     if (e != cudaSuccess) return e;
-    if (Cp > Mb)
-        for (int sl = 0; sl < OZ_S; sl++) {
-            e = cudaMemsetAsync(Bs + (size_t)sl * Cp * Kp + (size_t)Mb * Kp, 0, (size_t)(Cp - Mb) * Kp * 2, s);
-            if (e != cudaSuccess) return e;
-        }
     k_oz_slice_A<<<k, 256, 0, s>>>(Q, N, k, ldQ, Kp, Rp, As, Ea);
-    k_oz_slice_B<<<(unsigned)Mb, 256, 0, s>>>(X, N, Mb, ldX, Kp, Cp, Bs, Eb);
-    const size_t dsm = (size_t)2 * OZ_S * (OZ_M + OZ_N) * OZ_KS * 2 + (size_t)2 * OZ_M * OZ_N * 4;
+    const long long ge = (Mb * 32 + 255) / 256;
+    k_oz_exp_B<<<(unsigned)(ge < 4096 ? ge : 4096), 256, 0, s>>>(X, N, Mb, ldX, Eb);
+    const long long nst = Kp / OZ_KS;
+    k_oz_slice_B<<<dim3((unsigned)(Cp / OZ_N), (unsigned)((nst + OZ_SLICE_ST - 1) / OZ_SLICE_ST)), 256, 0, s>>>(
+        X, N, Mb, ldX, Kp, Eb, Bs);
+    const size_t dsm = (size_t)OZ_NBUF * OZ_S * (OZ_M + OZ_N) * OZ_KS * 2 + (size_t)2 * OZ_M * OZ_N * 4;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);

@@ -80,6 +80,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long b
     return done != 0;
 }
 
+// mbarrier arrive that also announces `bytes` of asynchronous transfers
+// which must land before the phase completes.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Bulk (non-tensor) copy of `bytes` contiguous bytes from global to shared
+// memory; both addresses 16-byte aligned, bytes a multiple of 16.  Counts its
+// bytes on the mbarrier when they have landed.
+__device__ __forceinline__ void bulk_g2s(void *sdst, const void *gsrc, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(sdst)),
+                 "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     uint32_t r[16];
