@@ -336,9 +336,10 @@ def run_recon_once(args):
       transform  B = V1^H C in double-float: 48 FP32 operations per complex
                  multiply-add, j^2 M of them, against 152 SMs x 128 FP32
                  lanes x the sampled SM clock;
-      pass-2 Jacobi (one block): 42 j FP64 operations per rotation applied
-                 (rows and columns of G, columns of V), against one SM's FP64
-                 rate (2 per clock)."""
+      pass-2 Jacobi (one block): 16 j FP64 operations per rotation applied
+                 (each rotation enters j/2 - 1 Hermitian 2 x 2 pair blocks of G
+                 on one side, 32 operations each; V is formed by another
+                 kernel), against one SM's FP64 rate (2 per clock)."""
     import statistics
     import torch
     from paper_1805_06124_gb300 import rb, synth
@@ -365,7 +366,7 @@ def run_recon_once(args):
     fp32_peak = 152 * 128 * mhz * 1e6 / 1e12            # T instructions/s
     fp64_sm_peak = 2 * mhz * 1e6 / 1e9                   # G FP64 ops/s on one SM
     t_ops = 48.0 * j * j * args.M
-    jac_ops = 42.0 * j * st["rotations"][1]
+    jac_ops = 16.0 * j * st["rotations"][1]
     print(json.dumps({
         "workload": f"reconstruction after the greedy, chirps N={args.N} x M={args.M} seed 1, tol 1e-12",
         "j": j, "k": out["k"], "greedy_ms": round(g["ms_total"], 3),

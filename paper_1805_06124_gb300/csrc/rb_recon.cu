@@ -42,6 +42,7 @@ constexpr int RJ_PAIRS = 64;      // index pairs per step (j <= 128)
 constexpr int RT_THREADS = 256;   // transform block
 constexpr int RT_ROWS = 14;       // output rows per warp: ceil(112 / 8)
 constexpr int kMaxJ = 112;
+constexpr int kJacobiMaxSweeps = 60;
 
 // Largest biased exponent over C (integer max on the IEEE bits).
 __global__ void k_max_exp(const double2 *__restrict__ A, long long ldA, int j, long long M, int *__restrict__ emax) {
@@ -186,36 +187,52 @@ template <typename T> __device__ __forceinline__ T cmulc_t(T a, T b) {  // a con
     return r;
 }
 
-// Hermitian Jacobi on G (j x j, FP64 input, row-major) in precision R.
-// V starts as the identity (Vinit == nullptr) or as Vinit and ends in Vg
-// (FP64).  VS: V in shared memory (else in Vg, global; R = double only).
-// The eigenvalues (diag of the rotated G) go to lam; stats (optional) gets
-// the sweeps and the rotations applied.  Dynamic shared memory: G (j^2
-// complex R) followed by V when VS.
-template <typename R, bool VS>
-__global__ void __launch_bounds__(RJ_THREADS) k_jacobi(const double2 *__restrict__ Gin, const double2 *__restrict__ Vinit,
-                                                       double2 *__restrict__ Vg, int j, double eps, int max_sweeps,
-                                                       double *__restrict__ lam, int *__restrict__ stats) {
+// Hermitian Jacobi on G (j x j, FP64 input, row-major) in precision R, G in
+// shared memory, one block.  A step rotates the npad/2 disjoint pairs of the
+// round-robin ordering at once; G <- J^H G J is formed block by block over the
+// upper triangle of 2 x 2 pair blocks (rows of pair i, columns of pair i2,
+// i <= i2: the left rotation of i, then the right rotation of i2, the mirror
+// entries by Hermitian symmetry), the diagonal blocks in closed form (G_pp -=
+// t|g|, G_qq += t|g|, G_pq = 0).  Every entry belongs to one block, so a step
+// needs one barrier after the rotation parameters and one after the update.
+// The rotations are recorded (c, s, phase) in rec, step by step, for
+// k_apply_rot; V is not formed here.  The eigenvalues (diag of the rotated G)
+// go to lam; stats gets the sweeps that rotated and the rotations applied.
+constexpr int RJ_BLK = 4;  // pair blocks per thread: ceil(56 * 57 / 2 / 512)
+
+struct __align__(32) Rot {  // one recorded rotation: c, s, e^{i phi}
+    double c, s, px, py;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(RJ_THREADS) k_jacobi(const double2 *__restrict__ Gin, int j, double eps, int max_sweeps,
+                                                       double *__restrict__ lam, int *__restrict__ stats,
+                                                       Rot *__restrict__ rec) {
     using T = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char jsm[];
     T *G = reinterpret_cast<T *>(jsm);
-    T *Vs = G + j * j;
     __shared__ int sp[RJ_PAIRS], sq[RJ_PAIRS];
-    __shared__ R sc[RJ_PAIRS], ss[RJ_PAIRS];
+    __shared__ R sc[RJ_PAIRS], ss[RJ_PAIRS], stg[RJ_PAIRS];  // c, s, t |g|
     __shared__ T sph[RJ_PAIRS];
     __shared__ int s_rot;
-    const int npad = j + (j & 1), np2 = npad / 2;
+    const int npad = j + (j & 1), np2 = npad / 2, nblk = np2 * (np2 + 1) / 2;
     for (int u = threadIdx.x; u < j * j; u += blockDim.x) {
         const double2 g = Gin[u];
         G[u] = cx<T>(g.x, g.y);
-        const bool d = (u / j) == (u % j);
-        const double2 v = Vinit ? Vinit[u] : make_double2(d ? 1.0 : 0.0, 0.0);
-        if (VS) Vs[u] = cx<T>(v.x, v.y);
-        else Vg[u] = v;
+    }
+    int blk[RJ_BLK];  // (i, i2) with i <= i2, packed i | i2 << 8
+#pragma unroll
+    for (int b = 0; b < RJ_BLK; b++) {
+        int u = threadIdx.x + b * RJ_THREADS, i = 0;
+        while (i < np2 && u >= np2 - i) {
+            u -= np2 - i;
+            i++;
+        }
+        blk[b] = i < np2 ? (i | (i + u) << 8) : 0;
     }
     __syncthreads();
-    T *V = VS ? Vs : reinterpret_cast<T *>(Vg);
     const R e = (R)eps;
+    const T zero = cx<T>(0.0, 0.0);
     int sw = 0, nrot = 0;
     for (; sw < max_sweeps; sw++) {
         if (threadIdx.x == 0) s_rot = 0;
@@ -231,21 +248,25 @@ __global__ void __launch_bounds__(RJ_THREADS) k_jacobi(const double2 *__restrict
                     p = q;
                     q = t;
                 }
-                R c = 1, s = 0;
+                R c = 1, s = 0, tg = 0;
                 T ph = cx<T>(1.0, 0.0);
                 if (q < j) {
+                    // few square roots and divisions: they are long sequences
+                    // on this GPU's FP64 pipe
                     const T g = G[p * j + q];
-                    const R ag = sqrt(g.x * g.x + g.y * g.y);
+                    const R g2 = g.x * g.x + g.y * g.y;
                     const R a = G[p * j + p].x, b = G[q * j + q].x;
-                    if (ag > (R)0 && ag > e * sqrt(fabs(a * b))) {
-                        const R tau = (b - a) / (2 * ag);
+                    if (g2 > (R)0 && g2 > e * e * fabs(a * b)) {
+                        const R rg = rsqrt(g2), ag = g2 * rg;  // 1/|g|, |g|
+                        const R tau = (b - a) * (R)0.5 * rg;
                         const R at_ = fabs(tau);
                         R t = at_ > (R)1e15 ? (R)0.5 / at_ : (R)1 / (at_ + sqrt((R)1 + tau * tau));
                         if (tau < (R)0) t = -t;
-                        c = (R)1 / sqrt((R)1 + t * t);
+                        c = rsqrt((R)1 + t * t);
                         s = t * c;
-                        ph.x = g.x / ag;
-                        ph.y = g.y / ag;
+                        tg = t * ag;
+                        ph.x = g.x * rg;
+                        ph.y = g.y * rg;
                         if (s != (R)0) atomicAdd(&s_rot, 1);
                     }
                 }
@@ -253,49 +274,70 @@ __global__ void __launch_bounds__(RJ_THREADS) k_jacobi(const double2 *__restrict
                 sq[i] = q;
                 sc[i] = c;
                 ss[i] = s;
+                stg[i] = tg;
                 sph[i] = ph;
+                if (sw < max_sweeps)
+                    rec[((long long)sw * (npad - 1) + step) * RJ_PAIRS + i] =
+                        Rot{(double)c, (double)s, (double)ph.x, (double)ph.y};
             }
             __syncthreads();
-            // left: rows p, q of G <- J^H (rows)
-            for (int u = threadIdx.x; u < np2 * j; u += blockDim.x) {
-                const int i = u / j, r = u % j;
-                const R s = ss[i];
-                if (s == (R)0) continue;
+#pragma unroll
+            for (int bb = 0; bb < RJ_BLK; bb++) {
+                if ((int)threadIdx.x + bb * RJ_THREADS >= nblk) break;
+                const int i = blk[bb] & 0xFF, i2 = blk[bb] >> 8;
+                const R s1 = ss[i], s2 = ss[i2];
+                if (s1 == (R)0 && s2 == (R)0) continue;
                 const int p = sp[i], q = sq[i];
-                const R c = sc[i];
-                const T ph = sph[i];
-                const T gp = G[p * j + r], gq = G[q * j + r];
-                const T e1 = cmul_t(ph, gq);   // e^{i phi} G_qr
-                const T e2 = cmulc_t(gp, ph);  // e^{-i phi} G_pr
-                T np, nq;
-                np.x = c * gp.x - s * e1.x;
-                np.y = c * gp.y - s * e1.y;
-                nq.x = s * e2.x + c * gq.x;
-                nq.y = s * e2.y + c * gq.y;
-                G[p * j + r] = np;
-                G[q * j + r] = nq;
-            }
-            __syncthreads();
-            // right: columns p, q of G and V <- (.) J
-            for (int u = threadIdx.x; u < 2 * np2 * j; u += blockDim.x) {
-                const int w = u / (np2 * j), uu = u % (np2 * j);
-                const int i = uu / j, r = uu % j;
-                const R s = ss[i];
-                if (s == (R)0) continue;
-                const int p = sp[i], q = sq[i];
-                const R c = sc[i];
-                const T ph = sph[i];
-                T *Mx = w ? V : G;
-                const T xp = Mx[r * j + p], xq = Mx[r * j + q];
-                const T f1 = cmulc_t(xq, ph);  // e^{-i phi} x_q
-                const T f2 = cmul_t(ph, xp);   // e^{i phi} x_p
-                T np, nq;
-                np.x = c * xp.x - s * f1.x;
-                np.y = c * xp.y - s * f1.y;
-                nq.x = s * f2.x + c * xq.x;
-                nq.y = s * f2.y + c * xq.y;
-                Mx[r * j + p] = np;
-                Mx[r * j + q] = nq;
+                if (i == i2) {  // rotated pair: closed form
+                    const R tg = stg[i];
+                    T gp = G[p * j + p], gq = G[q * j + q];
+                    gp.x -= tg;
+                    gp.y = 0;
+                    gq.x += tg;
+                    gq.y = 0;
+                    G[p * j + p] = gp;
+                    G[q * j + q] = gq;
+                    G[p * j + q] = zero;
+                    G[q * j + p] = zero;
+                    continue;
+                }
+                const int p2 = sp[i2], q2 = sq[i2];
+                const bool vq = q < j, vq2 = q2 < j;
+                T x00 = G[p * j + p2], x01 = vq2 ? G[p * j + q2] : zero, x10 = vq ? G[q * j + p2] : zero,
+                  x11 = (vq && vq2) ? G[q * j + q2] : zero;
+                if (s1 != (R)0) {  // rows (p, q) <- J_i^H
+                    const R c = sc[i];
+                    const T ph = sph[i];
+                    const T a0 = cmul_t(ph, x10), a1 = cmul_t(ph, x11);      // e^{i phi} x_q.
+                    const T b0 = cmulc_t(x00, ph), b1 = cmulc_t(x01, ph);    // e^{-i phi} x_p.
+                    T n00, n01, n10, n11;
+                    n00.x = c * x00.x - s1 * a0.x; n00.y = c * x00.y - s1 * a0.y;
+                    n01.x = c * x01.x - s1 * a1.x; n01.y = c * x01.y - s1 * a1.y;
+                    n10.x = s1 * b0.x + c * x10.x; n10.y = s1 * b0.y + c * x10.y;
+                    n11.x = s1 * b1.x + c * x11.x; n11.y = s1 * b1.y + c * x11.y;
+                    x00 = n00; x01 = n01; x10 = n10; x11 = n11;
+                }
+                if (s2 != (R)0) {  // columns (p2, q2) <- (.) J_i2
+                    const R c = sc[i2];
+                    const T ph = sph[i2];
+                    const T f0 = cmulc_t(x01, ph), f1 = cmulc_t(x11, ph);    // e^{-i phi} x_.q
+                    const T h0 = cmul_t(ph, x00), h1 = cmul_t(ph, x10);      // e^{i phi} x_.p
+                    T n00, n01, n10, n11;
+                    n00.x = c * x00.x - s2 * f0.x; n00.y = c * x00.y - s2 * f0.y;
+                    n10.x = c * x10.x - s2 * f1.x; n10.y = c * x10.y - s2 * f1.y;
+                    n01.x = s2 * h0.x + c * x01.x; n01.y = s2 * h0.y + c * x01.y;
+                    n11.x = s2 * h1.x + c * x11.x; n11.y = s2 * h1.y + c * x11.y;
+                    x00 = n00; x01 = n01; x10 = n10; x11 = n11;
+                }
+                auto put = [&](int r, int cc, T v) {
+                    G[r * j + cc] = v;
+                    v.y = -v.y;
+                    G[cc * j + r] = v;
+                };
+                put(p, p2, x00);
+                if (vq2) put(p, q2, x01);
+                if (vq) put(q, p2, x10);
+                if (vq && vq2) put(q, q2, x11);
             }
             __syncthreads();
         }
@@ -304,13 +346,62 @@ __global__ void __launch_bounds__(RJ_THREADS) k_jacobi(const double2 *__restrict
         __syncthreads();
         if (!any) break;
     }
-    if (VS)
-        for (int u = threadIdx.x; u < j * j; u += blockDim.x) Vg[u] = make_double2((double)Vs[u].x, (double)Vs[u].y);
     for (int a = threadIdx.x; a < j; a += blockDim.x) lam[a] = (double)G[a * j + a].x;
     if (threadIdx.x == 0 && stats) {
-        stats[0] = sw;    // sweeps with at least one rotation
+        stats[0] = sw;    // sweeps with at least one rotation (all recorded)
         stats[1] = nrot;  // rotations applied
     }
+}
+
+// V <- Vinit (identity when null) times the recorded rotations of the first
+// stats[0] sweeps, in order.  Rows of V are independent under V <- V J: block
+// r keeps row r in shared memory and thread i applies pair i of each step
+// (the same round-robin pairs), one barrier per step; the records come in
+// batches of RA_BATCH steps, copied to shared memory with coalesced loads.
+// FP64 arithmetic on the recorded values (FP32 rotations of pass 1 are unitary
+// only to FP32 precision; the Newton-Schulz steps that follow fix that).
+constexpr int RA_BATCH = 16;
+
+__global__ void __launch_bounds__(128) k_apply_rot(const Rot *__restrict__ rec, const int *__restrict__ stats, int j,
+                                                   const double2 *__restrict__ Vinit, double2 *__restrict__ Vout) {
+    __shared__ double2 row[128];
+    __shared__ Rot srec[RA_BATCH * RJ_PAIRS];
+    const int r = blockIdx.x;
+    const int npad = j + (j & 1), np2 = npad / 2;
+    for (int c = threadIdx.x; c < j; c += blockDim.x)
+        row[c] = Vinit ? Vinit[r * j + c] : make_double2(c == r ? 1.0 : 0.0, 0.0);
+    const long long nsteps = (long long)stats[0] * (npad - 1);
+    for (long long t0 = 0; t0 < nsteps; t0 += RA_BATCH) {
+        const int nb = nsteps - t0 < RA_BATCH ? (int)(nsteps - t0) : RA_BATCH;
+        __syncthreads();
+        for (int u = threadIdx.x; u < nb * RJ_PAIRS; u += blockDim.x) srec[u] = rec[t0 * RJ_PAIRS + u];
+        __syncthreads();
+        for (int b = 0; b < nb; b++) {
+            const long long t = t0 + b;
+            const int step = (int)(t % (npad - 1)), i = threadIdx.x;
+            if (i < np2) {
+                auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (npad - 1); };
+                int p = at(i), q = at(npad - 1 - i);
+                if (p > q) {
+                    const int tt = p;
+                    p = q;
+                    q = tt;
+                }
+                const Rot g = srec[b * RJ_PAIRS + i];
+                if (q < j && g.s != 0.0) {
+                    const double c = g.c, s = g.s;
+                    const double2 ph = make_double2(g.px, g.py);
+                    const double2 xp = row[p], xq = row[q];
+                    const double2 f1 = cmulc_t(xq, ph), f2 = cmul_t(ph, xp);
+                    row[p] = make_double2(c * xp.x - s * f1.x, c * xp.y - s * f1.y);
+                    row[q] = make_double2(s * f2.x + c * xq.x, s * f2.y + c * xq.y);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < j; c += blockDim.x) Vout[r * j + c] = row[c];
 }
 
 // ----------------------------------------------------- Newton-Schulz step
@@ -471,6 +562,7 @@ struct ReconWs {
     int *emax, *stats;
     double2 *part, *B, *G1, *G2, *Va, *Vb, *E;
     float4 *Vsp;
+    Rot *rec;
     double *lam;
     int *perm;
     size_t total;
@@ -499,21 +591,19 @@ ReconWs carve(void *base, int j, long long M, int nsm) {
     w.Vsp = (float4 *)take(jj * 16);
     w.lam = (double *)take((size_t)j * 8);
     w.perm = (int *)take((size_t)j * 4);
+    w.rec = (Rot *)take((size_t)kJacobiMaxSweeps * (j + 1) * RJ_PAIRS * 32);
     w.total = off;
     return w;
 }
 
-template <typename R, bool VS> size_t jacobi_smem(int j) {
-    return (size_t)j * j * sizeof(typename Cx<R>::T) * (VS ? 2 : 1);
-}
+template <typename R> size_t jacobi_smem(int j) { return (size_t)j * j * sizeof(typename Cx<R>::T); }
 
-template <typename R, bool VS>
-cudaError_t launch_jacobi(const double2 *G, const double2 *Vinit, double2 *Vg, int j, double eps, double *lam, int *sw,
-                          cudaStream_t s) {
-    const size_t sm = jacobi_smem<R, VS>(j);
-    cudaError_t e = cudaFuncSetAttribute(k_jacobi<R, VS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <typename R>
+cudaError_t launch_jacobi(const double2 *G, int j, double eps, double *lam, int *stats, Rot *rec, cudaStream_t s) {
+    const size_t sm = jacobi_smem<R>(j);
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_jacobi<R, VS><<<1, RJ_THREADS, sm, s>>>(G, Vinit, Vg, j, eps, 60, lam, sw);
+    k_jacobi<R><<<1, RJ_THREADS, sm, s>>>(G, j, eps, kJacobiMaxSweeps, lam, stats, rec);
     return cudaGetLastError();
 }
 }  // namespace
@@ -550,10 +640,11 @@ cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M
     k_gram_tri<false><<<nchunk, RG_THREADS, gsm, s>>>(C, ldC, j, M, chunk, w.emax, w.part);
     k_gram_reduce<<<gr, 256, 0, s>>>(w.part, j, nchunk, w.G1);
     if ((e = mark(1)) != cudaSuccess) return e;
-    if ((e = launch_jacobi<float, true>(w.G1, nullptr, w.Va, j, 0x1p-22, w.lam, w.stats, s)) != cudaSuccess) return e;
+    if ((e = launch_jacobi<float>(w.G1, j, 0x1p-22, w.lam, w.stats, w.rec, s)) != cudaSuccess) return e;
+    k_apply_rot<<<j, 128, 0, s>>>(w.rec, w.stats, j, nullptr, w.Va);
     if ((e = mark(2)) != cudaSuccess) return e;
     // V1 unitary to FP64 precision: three Newton-Schulz steps (the FP32
-    // Jacobi leaves ||V^H V - I|| near 1e-5; each step squares it)
+    // rotations leave ||V^H V - I|| near 1e-5; each step squares it)
     double2 *cur = w.Va, *nxt = w.Vb;
     const int nt = (j + 31) / 32 * 32;
     for (int it = 0; it < 3; it++) {
@@ -575,14 +666,8 @@ cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M
     k_gram_tri<true><<<nchunk, RG_THREADS, gsm, s>>>(w.B, M, j, M, chunk, nullptr, w.part);
     k_gram_reduce<<<gr, 256, 0, s>>>(w.part, j, nchunk, w.G2);
     if ((e = mark(5)) != cudaSuccess) return e;
-    int dev = 0, maxsm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
-        return e;
-    const bool vs = jacobi_smem<double, true>(j) + 8192 <= (size_t)maxsm;
-    e = vs ? launch_jacobi<double, true>(w.G2, cur, nxt, j, 0x1p-52, w.lam, w.stats + 2, s)
-           : launch_jacobi<double, false>(w.G2, cur, nxt, j, 0x1p-52, w.lam, w.stats + 2, s);
-    if (e != cudaSuccess) return e;
+    if ((e = launch_jacobi<double>(w.G2, j, 0x1p-52, w.lam, w.stats + 2, w.rec, s)) != cudaSuccess) return e;
+    k_apply_rot<<<j, 128, 0, s>>>(w.rec, w.stats + 2, j, cur, nxt);
     k_recon_finish<<<1, 256, 0, s>>>(w.lam, nxt, j, w.emax, V, sigma, w.perm);
     if (stats && (e = cudaMemcpyAsync(stats, w.stats, 4 * sizeof(int), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return e;
