@@ -511,6 +511,40 @@ def run_ours(args):
     tpb = _sweep_traffic_per_byte()
     launches = sum(r["n_launches"] for r in results)
     clocks = clk.summary()
+
+    # the rows after the greedy, on the timed run's basis: reconstruction
+    # (Alg. 4), EI nodes, out-of-sample validation (16,384 chirps of seed 7)
+    extra_next = None
+    if rank == 0 and world == 1 and not args.no_next:
+        import statistics
+        Qd, Cd = results[-1]["Q"], results[-1]["C"]
+
+        def timed(fn, reps=3):
+            fn()
+            ts = []
+            for _ in range(reps):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                r_ = fn()
+                torch.cuda.synchronize(dev)
+                ts.append(1e3 * (time.perf_counter() - t0))
+            return r_, round(statistics.median(ts), 3)
+
+        with torch.cuda.stream(stream):
+            rec, t_rec = timed(lambda: ctx.reconstruct(Qd, Cd, 0.0))
+            rst = ctx.reconstruct_stats()
+            ei, t_eim = timed(lambda: ctx.eim(Qd))
+            T = ctx.generate(*synth.chirp_params(16384, 7), N)
+            va, t_val = timed(lambda: ctx.validate(Qd, T, ei["nodes"], ei["Vinv"]))
+        extra_next = {
+            "reconstruction": {"j": int(Qd.shape[0]), "ms": t_rec,
+                               "phase_ms": {kk: round(vv, 4) for kk, vv in rst["ms"].items()},
+                               "jacobi_sweeps": rst["sweeps"],
+                               "sigma_ratio": float(rec["sigma"][-1] / rec["sigma"][0])},
+            "eim": {"k": int(Qd.shape[0]), "ms": t_eim},
+            "validation": {"snapshots": 16384, "ms": t_val,
+                           "max_err_proj": float(va["err_proj"].max()), "max_err_eim": float(va["err_eim"].max())}}
+        del T, rec, ei, va
     del results
 
     # end to end through the host-buffer entry point
@@ -575,7 +609,7 @@ def run_ours(args):
                              "traffic": (round(tpb * per_launch) if tpb else None),
                              "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": round(sweep_ms, 4)},
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
-                "split_vs_fp64": extra_split, "batched": extra_batched}
+                "split_vs_fp64": extra_split, "batched": extra_batched, "after_greedy": extra_next}
         print(json.dumps(line), flush=True)
     if not (rank == 0 and world == 1):
         ctx.close()
@@ -596,6 +630,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-next", action="store_true")
     ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate", "split", "project", "batched",
                                                                 "recon", "eim", "resume"])
     ap.add_argument("--epochs", type=int, default=200)
