@@ -109,7 +109,7 @@ struct BProb {
     const float2 *ql;
     DevState *st;
     int kmax;
-    int pad;
+    int cw;  // columns per sweep chunk
     long long minNM;
     double tol;
     const float2 *hi;  // pre-split copy (null: split in registers)
