@@ -607,30 +607,42 @@ constexpr int PT = 128;  // tile rows (A) and columns (B)
 constexpr int PKC = 32;  // K per stage
 constexpr int PSL = 3;   // BF16 pieces per FP32 value
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16 *o) {
-    __nv_bfloat16 x1 = __float2bfloat16_rn(x);
-    float r = x - __bfloat162float(x1);
-    __nv_bfloat16 x2 = __float2bfloat16_rn(r);
-    r -= __bfloat162float(x2);
-    o[0] = x1;
-    o[1] = x2;
-    o[2] = __float2bfloat16_rn(r);
+// x rounded to BF16 (nearest, ties to even), as the FP32 bit pattern with the
+// low 16 bits cleared: BF16 is the top half of an FP32, so the rounding is an
+// integer add and mask (finite x; conversion instructions run at a low rate on
+// this GPU).
+__device__ __forceinline__ uint32_t bf16_round_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+}
+
+// Exact split x = x1 + x2 + x3 into BF16 pieces (each difference is exact in
+// FP32); o[s] = the FP32 bit pattern of piece s (its BF16 value in the top half).
+__device__ __forceinline__ void split3_bits(float x, uint32_t o[PSL]) {
+    o[0] = bf16_round_bits(x);
+    const float r = x - __uint_as_float(o[0]);
+    o[1] = bf16_round_bits(r);
+    o[2] = bf16_round_bits(r - __uint_as_float(o[1]));
 }
 
 // Stage 8 consecutive K entries (4 complex elements) of one tile row into the
 // three piece tiles: one 16-byte core-matrix row per piece.
 __device__ __forceinline__ void stage_row8(uint8_t *base, int r, int kk, const float v[8]) {
-    __nv_bfloat16 pc[PSL][8];
+    uint32_t pc[PSL][8];
 #pragma unroll
     for (int e = 0; e < 8; e++) {
-        __nv_bfloat16 o[PSL];
-        split3(v[e], o);
+        uint32_t o[PSL];
+        split3_bits(v[e], o);
 #pragma unroll
         for (int s = 0; s < PSL; s++) pc[s][e] = o[s];
     }
 #pragma unroll
-    for (int s = 0; s < PSL; s++)
-        *(uint4 *)(base + s * (PT * PKC * 2) + kmajor_off(r, kk, PKC)) = *(const uint4 *)pc[s];
+    for (int s = 0; s < PSL; s++) {
+        // pairs of BF16 values: element 2i in the low half of word i
+        const uint4 w = make_uint4(__byte_perm(pc[s][0], pc[s][1], 0x7632), __byte_perm(pc[s][2], pc[s][3], 0x7632),
+                                   __byte_perm(pc[s][4], pc[s][5], 0x7632), __byte_perm(pc[s][6], pc[s][7], 0x7632));
+        *(uint4 *)(base + s * (PT * PKC * 2) + kmajor_off(r, kk, PKC)) = w;
+    }
 }
 
 // A operand pieces, built once when the loop ends: for row tile rt and K
@@ -716,22 +728,27 @@ __device__ __forceinline__ void proj_store_b(uint8_t *sB, const float4 bx[PBU], 
     }
 }
 
-// The prepared 48 KB of A pieces of one stage, copied asynchronously.
-__device__ __forceinline__ void proj_copy_a(uint8_t *sA, const uint8_t *ga) {
-#pragma unroll
-    for (int u = 0; u < PTILE / 16 / kThreads; u++) {
-        const int t = threadIdx.x + u * kThreads;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sA + 16 * t)), "l"(ga + 16 * t));
-    }
-    asm volatile("cp.async.commit_group;");
-}
+// d = Qh^H lo on the tensor cores, C += d.  One block per SM (persistent over
+// tiles), warp-specialised around a ring of LP_NBUF stage buffers (A pieces,
+// then B pieces):
+//   warps 0-7 (producers) convert the lo values of stage s (loaded into
+//     registers LP_AHEAD stages earlier) into the B pieces of buffer s % LP_NBUF
+//     once the MMAs of stage s - LP_NBUF are done, then arrive on bfull;
+//   warp 8, lane 0 waits for the A bytes (afull) and the B pieces (bfull) of
+//     stage s, issues its MMAs, commits them to done, and bulk-copies the A
+//     pieces of stage s + LP_NBUF - 1 into the buffer of stage s - 1 once the
+//     MMAs of stage s - 1 are done;
+//   warps 0-3 (TMEM lanes 0-127) run the epilogue of each tile.
+// Barrier phases follow a running stage count g over all tiles of the block:
+// buffer g % LP_NBUF, phase (g / LP_NBUF) & 1.  No role can run a full ring
+// ahead of another (each refill waits for the MMAs that emptied the buffer),
+// so no wait can be two phases behind.
+constexpr int LP_NBUF = 4;
+constexpr int LP_AHEAD = 4;                    // stages of lo loaded ahead into registers
+constexpr int LP_PRODUCERS = kThreads;         // 256 converting threads
+constexpr int LP_THREADS = kThreads + 32;      // + the MMA warp
 
-// d = Qh^H lo on the tensor cores, C += d.  One block per SM, 256 threads,
-// two stage buffers: while the MMAs of stage s run, the block converts the
-// lo values of stage s+1 (loaded into registers during stage s) and copies
-// the A pieces of stage s+1; thread 0 issues the MMAs; warps 0-3 (TMEM lanes
-// 0-127) run the epilogue.
-__global__ void __launch_bounds__(kThreads) k_lo_project_tc(Prob p, int *err) {
+__global__ void __launch_bounds__(LP_THREADS) k_lo_project_tc(Prob p, int *err) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop) || !ld_volatile(&st->switch_pending)) return;
     const int k1 = st->k;
@@ -740,14 +757,20 @@ __global__ void __launch_bounds__(kThreads) k_lo_project_tc(Prob p, int *err) {
     const long long ntiles = (long long)nrt * nct;
     if (k1 <= 0 || (long long)blockIdx.x >= ntiles) return;
     extern __shared__ __align__(1024) uint8_t dsm[];
-    // buffer b: A pieces at dsm + 2 b PTILE, B pieces right after
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t afull[LP_NBUF], bfull[LP_NBUF], done[LP_NBUF];
     __shared__ uint32_t tslot;
+    __shared__ int s_bad;
     const int warp = threadIdx.x >> 5;
+    const bool producer = threadIdx.x < LP_PRODUCERS;
+    const bool issuer = threadIdx.x == LP_PRODUCERS;  // lane 0 of warp 8
     if (warp == 0) tmem_alloc(&tslot, PT);
     if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        s_bad = 0;
+        for (int b = 0; b < LP_NBUF; b++) {
+            mbar_init(&afull[b], 1);
+            mbar_init(&bfull[b], LP_PRODUCERS);  // one arrive per producer thread
+            mbar_init(&done[b], 1);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -755,62 +778,80 @@ __global__ void __launch_bounds__(kThreads) k_lo_project_tc(Prob p, int *err) {
     const uint32_t tmem = tslot;
     constexpr uint32_t idesc = idesc_bf16_f32(PT, PT);
     const long long nstg = (2 * p.N + PKC - 1) / PKC;
-    uint32_t phbits = 0u;  // bit b: the next completion parity of mbar[b]
     bool ok = true;
-    // lo values of two stages ahead live in registers: set 0 for even
-    // stages, set 1 for odd ones
-    float4 bx0[PBU], by0[PBU], bx1[PBU], by1[PBU];
-    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    long long gs = 0;  // stages run by this block so far (all tiles)
+    auto bufA = [&](long long g) { return dsm + (int)(g % LP_NBUF) * 2 * PTILE; };
+    auto par = [&](long long g) { return (uint32_t)((g / LP_NBUF) & 1); };
+    float4 bx0[PBU], by0[PBU], bx1[PBU], by1[PBU], bx2[PBU], by2[PBU], bx3[PBU], by3[PBU];
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int rt = (int)(tile % nrt);
         const long long j0 = (tile / nrt) * PT;
         const uint8_t *ga = p.apieces + (long long)rt * nstg * PTILE;
-        proj_load_b(p, j0, 0, bx0, by0);
-        if (nstg > 1) proj_load_b(p, j0, 1, bx1, by1);
-        proj_copy_a(dsm, ga);
-        // one stage: B(stg) from registers into buffer b, registers refilled with
-        // B(stg + 2), MMAs on buffer b, then buffer b^1 is refilled with A(stg + 1)
-        // once the MMAs of stage stg - 1 are done
-#define RB_PROJ_STAGE(b, BX, BY)                                                                                    \
-    do {                                                                                                            \
-        uint8_t *sAb = dsm + 2 * (b) * PTILE, *sBb = sAb + PTILE;                                                   \
-        proj_store_b(sBb, BX, BY);                                                                                  \
-        if (stg + 2 < nstg) proj_load_b(p, j0, stg + 2, BX, BY);                                                    \
-        asm volatile("cp.async.wait_all;");                                                                         \
-        fence_async_smem();                                                                                         \
-        __syncthreads();                                                                                            \
-        if (threadIdx.x == 0) {                                                                                     \
-            tc_fence_after();                                                                                       \
-            int first = 1;                                                                                          \
-            _Pragma("unroll") for (int sa = 0; sa < PSL; sa++)                                                      \
-            _Pragma("unroll") for (int sb = 0; sb < PSL; sb++) {                                                    \
-                if (sa + sb > 2) continue; /* pieces s + t <= 4 (0-based sa + sb <= 2) */                          \
-                _Pragma("unroll") for (int kk = 0; kk < PKC / 16; kk++) {                                           \
-                    uint64_t ad = smem_desc(smem_u32(sAb) + sa * (PT * PKC * 2) + kk * 256, 128, (PKC / 8) * 128);  \
-                    uint64_t bd = smem_desc(smem_u32(sBb) + sb * (PT * PKC * 2) + kk * 256, 128, (PKC / 8) * 128);  \
-                    tc_mma_bf16(tmem, ad, bd, idesc, (stg > 0 || !first) ? 1u : 0u);                                \
-                    first = 0;                                                                                      \
-                }                                                                                                   \
-            }                                                                                                       \
-            tc_commit(&mbar[b]);                                                                                    \
-        }                                                                                                           \
-        if (stg >= 1) {                                                                                             \
-            ok = mbar_wait(&mbar[(b) ^ 1], (phbits >> ((b) ^ 1)) & 1u) && ok;                                       \
-            phbits ^= 1u << ((b) ^ 1);                                                                              \
-        }                                                                                                           \
-        if (stg + 1 < nstg) proj_copy_a(dsm + 2 * ((b) ^ 1) * PTILE, ga + (stg + 1) * PTILE);                     \
-    } while (0)
-        for (long long stg = 0; stg < nstg; stg++) {
-            RB_PROJ_STAGE(0, bx0, by0);
-            if (++stg >= nstg) break;
-            RB_PROJ_STAGE(1, bx1, by1);
+        const long long g0 = gs;
+        if (producer) {
+            // register sets: stage s uses set s % 4
+            proj_load_b(p, j0, 0, bx0, by0);
+            if (nstg > 1) proj_load_b(p, j0, 1, bx1, by1);
+            if (nstg > 2) proj_load_b(p, j0, 2, bx2, by2);
+            if (nstg > 3) proj_load_b(p, j0, 3, bx3, by3);
+            auto produce = [&](long long s, float4 (&BX)[PBU], float4 (&BY)[PBU]) {
+                const long long g = g0 + s;
+                if (g >= LP_NBUF) ok = mbar_wait(&done[g % LP_NBUF], par(g - LP_NBUF)) && ok;
+                proj_store_b(bufA(g) + PTILE, BX, BY);
+                if (s + LP_AHEAD < nstg) proj_load_b(p, j0, s + LP_AHEAD, BX, BY);
+                // each thread makes its own stores visible to the tensor core
+                // (async proxy), then arrives
+                fence_async_smem();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[g % LP_NBUF])) : "memory");
+            };
+            for (long long s = 0; s < nstg; s += 4) {
+                produce(s, bx0, by0);
+                if (s + 1 < nstg) produce(s + 1, bx1, by1);
+                if (s + 2 < nstg) produce(s + 2, bx2, by2);
+                if (s + 3 < nstg) produce(s + 3, bx3, by3);
+            }
+        } else if (issuer) {
+            auto load_a = [&](long long s) {
+                uint64_t *fb = &afull[(g0 + s) % LP_NBUF];
+                mbar_expect_tx(fb, PTILE);
+                bulk_g2s(bufA(g0 + s), ga + s * PTILE, PTILE, fb);
+            };
+            // the first LP_NBUF - 1 stages: their buffers' MMAs (previous tile)
+            // are complete
+            for (long long s = 0; s < LP_NBUF - 1 && s < nstg; s++) load_a(s);
+            for (long long s = 0; s < nstg; s++) {
+                const long long g = g0 + s;
+                const int b = (int)(g % LP_NBUF);
+                ok = mbar_wait(&afull[b], par(g)) && ok;
+                ok = mbar_wait(&bfull[b], par(g)) && ok;
+                tc_fence_after();
+                const uint64_t ad0 = smem_desc(smem_u32(bufA(g)), 128, (PKC / 8) * 128);
+                const uint64_t bd0 = smem_desc(smem_u32(bufA(g) + PTILE), 128, (PKC / 8) * 128);
+                bool first = true;
+#pragma unroll
+                for (int sa = 0; sa < PSL; sa++)
+#pragma unroll
+                    for (int sb = 0; sb < PSL; sb++) {
+                        if (sa + sb > 2) continue;  // pieces s + t <= 4 (0-based sa + sb <= 2)
+#pragma unroll
+                        for (int kk = 0; kk < PKC / 16; kk++) {
+                            const uint64_t ad = ad0 + (uint64_t)((sa * (PT * PKC * 2) + kk * 256) >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)((sb * (PT * PKC * 2) + kk * 256) >> 4);
+                            tc_mma_bf16(tmem, ad, bd, idesc, (s > 0 || !first) ? 1u : 0u);
+                            first = false;
+                        }
+                    }
+                tc_commit(&done[b]);
+                // A of stage s + LP_NBUF - 1 into the buffer of stage s - 1
+                if (s + LP_NBUF - 1 < nstg) {
+                    if (s >= 1) ok = mbar_wait(&done[(g - 1) % LP_NBUF], par(g - 1)) && ok;
+                    load_a(s + LP_NBUF - 1);
+                }
+            }
         }
-#undef RB_PROJ_STAGE
-        // the last stage's MMAs
-        {
-            const int b = (int)((nstg - 1) & 1);
-            ok = mbar_wait(b ? &mbar[1] : &mbar[0], (phbits >> b) & 1u) && ok;
-            phbits ^= 1u << b;
-        }
+        gs = g0 + nstg;
+        // every thread: the tile's last MMAs (the latest phase of that barrier)
+        ok = mbar_wait(&done[(gs - 1) % LP_NBUF], par(gs - 1)) && ok;
         tc_fence_after();
         // epilogue: thread = A row (TMEM lane); row 2l adds to Re C[l, j], row 2l+1 to Im
         if (warp < 4) {
@@ -828,10 +869,13 @@ __global__ void __launch_bounds__(kThreads) k_lo_project_tc(Prob p, int *err) {
                 }
             }
         }
+        if (!ok) s_bad = 1;
         tc_fence_before();
         __syncthreads();
+        tc_fence_after();
+        if (s_bad) break;
     }
-    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    if (s_bad && threadIdx.x == 0) atomicExch(err, 1);
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, PT);
 }
@@ -925,19 +969,19 @@ size_t lo_pieces_bytes(long long N, int kcap) {
 }
 
 cudaError_t launch_split_finish(const Prob &p, int grid, cudaStream_t s, int *nlaunch) {
-    const size_t dsmem = 4 * PTILE;
+    const size_t dsmem = (size_t)LP_NBUF * 2 * PTILE;  // 192 KB
     static int g_proj = 0;
     if (!g_proj) {
         cudaFuncSetAttribute(k_lo_project_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
         cudaFuncSetAttribute(k_lo_project_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        // two blocks per SM (96 KB of buffers each) interleave their stages
+        // one block per SM (144 KB ring)
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g_proj = 2 * sms;
+        g_proj = sms;
     }
     k_qpieces<<<grid, kThreads, 0, s>>>(p);
-    k_lo_project_tc<<<g_proj, kThreads, dsmem, s>>>(p, p.tc_err);
+    k_lo_project_tc<<<g_proj, LP_THREADS, dsmem, s>>>(p, p.tc_err);
     long long rf = (p.M + kThreads - 1) / kThreads;
     if (rf > grid) rf = grid;
     k_rebase_finish<<<(int)rf, kThreads, 0, s>>>(p);
