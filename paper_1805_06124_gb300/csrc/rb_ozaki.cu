@@ -197,31 +197,36 @@ __global__ void __launch_bounds__(256) k_oz_slice_B(const double2 *__restrict__ 
 __device__ __forceinline__ void dfs_add(float &ah, float &al, float bh, float bl) { df_add(ah, al, bh, bl); }
 
 // Ring of OZ_NBUF stage buffers filled by bulk copies: one thread issues the
-// copies of stage st + 2 (the A and the B block, 28 KB + 14 KB) as soon as the
-// MMAs of stage st - 1, the last user of that buffer, have completed, waits
-// for the bytes of stage st, and issues its 28 MMAs.  "full" barriers count
-// the copied bytes; "done" barriers receive the MMA commits; the n-th phase of
-// buffer b's barriers belongs to stage b + OZ_NBUF n.  At the end of each
-// exact chunk (OZ_DRAIN K values) all threads drain the TMEM levels.
-constexpr int OZ_NBUF = 3;
+// copies of stage st + OZ_NBUF - 1 (the A and the B block, 28 KB + 14 KB) as
+// soon as the MMAs of stage st - 1, the last user of that buffer, have
+// completed, waits for the bytes of stage st, and issues its 28 MMAs.  "full"
+// barriers count the copied bytes; "done" barriers receive the MMA commits;
+// the n-th phase of buffer b's barriers belongs to stage b + OZ_NBUF n.  At
+// the end of each exact chunk (OZ_DRAIN K values) all 256 threads drain the
+// TMEM levels into double-float running sums held in registers: thread
+// (warp w, lane l) owns row 32 (w % 4) + l and columns 32 (w / 4) .. + 31.
+constexpr int OZ_NBUF = 5;
+constexpr int OZ_THREADS = 256;
 
-__global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__restrict__ Bs,
-                                                 const int *__restrict__ Ea, const int *__restrict__ Eb, int k, long long Mb,
-                                                 long long Kp, long long Rp, long long Cp, double2 *__restrict__ C,
-                                                 long long ldC, long long col_off, int *err) {
+__global__ void __launch_bounds__(OZ_THREADS) k_oz_gemm(const __nv_bfloat16 *__restrict__ As,
+                                                        const __nv_bfloat16 *__restrict__ Bs,
+                                                        const int *__restrict__ Ea, const int *__restrict__ Eb, int k,
+                                                        long long Mb, long long Kp, long long Rp, long long Cp,
+                                                        double2 *__restrict__ C, long long ldC, long long col_off,
+                                                        int *err) {
     extern __shared__ __align__(1024) uint8_t dsm[];
     constexpr int SA = OZ_S * OZ_M * OZ_KS * 2, SB = OZ_S * OZ_N * OZ_KS * 2;  // 28 KB, 14 KB per buffer
-    float *acc_h = (float *)(dsm + OZ_NBUF * (SA + SB));  // 128 x 64 double-float running sums
-    float *acc_l = acc_h + OZ_M * OZ_N;
     __shared__ __align__(8) uint64_t full[OZ_NBUF], done[OZ_NBUF], cdone;
     __shared__ uint32_t tslot;
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = 32 * (warp & 3) + lane, cbase = 32 * (warp >> 2);
     const long long ct = blockIdx.x, rt = blockIdx.y;
     const long long j0 = ct * OZ_N, r0 = rt * OZ_M;
-    for (int t = threadIdx.x; t < OZ_M * OZ_N; t += blockDim.x) acc_h[t] = acc_l[t] = 0.f;
+    float acc_h[32], acc_l[32];
+#pragma unroll
+    for (int c = 0; c < 32; c++) acc_h[c] = acc_l[c] = 0.f;
     if (warp == 0) tmem_alloc(&tslot, OZ_TCOLS);
-    if (threadIdx.x == 0)
-    {
+    if (threadIdx.x == 0) {
         for (int b = 0; b < OZ_NBUF; b++) {
             mbar_init(&full[b], 1);
             mbar_init(&done[b], 1);
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict
         bulk_g2s(bufB(st), Bs + (ct * nst + st) * (long long)(OZ_S * OZ_N * OZ_KS), SB, fb);
     };
     if (threadIdx.x == 0)
-        for (long long st = 0; st < 2 && st < nst; st++) load(st);
+        for (long long st = 0; st < OZ_NBUF - 1 && st < nst; st++) load(st);
     for (long long cs = 0; cs < nst; cs += per_drain) {
         const long long ce = cs + per_drain < nst ? cs + per_drain : nst;
         if (threadIdx.x == 0) {
@@ -274,9 +279,9 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict
                         }
                     }
                 tc_commit(&done[st % OZ_NBUF]);
-                if (st + 2 < nst) {
+                if (st + OZ_NBUF - 1 < nst) {
                     if (st >= 1) ok = mbar_wait(&done[(st - 1) % OZ_NBUF], par(st - 1)) && ok;
-                    load(st + 2);
+                    load(st + OZ_NBUF - 1);
                 }
             }
             tc_commit(&cdone);
@@ -287,12 +292,12 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict
         // TMEM lane; levels combined smallest first, in double-float
         ok = mbar_wait(&cdone, (uint32_t)((cs / per_drain) & 1)) && ok;
         tc_fence_after();
-        const int r = threadIdx.x;
-        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-        for (int c0 = 0; c0 < OZ_N; c0 += 16) {
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
             float v[OZ_LV][16];
 #pragma unroll
-            for (int L = 0; L < OZ_LV; L++) tmem_ld16(tmem + lane_off + (uint32_t)(L * OZ_N + c0), v[L]);
+            for (int L = 0; L < OZ_LV; L++) tmem_ld16(tmem + lane_off + (uint32_t)(L * OZ_N + cbase + 16 * h), v[L]);
 #pragma unroll
             for (int e = 0; e < 16; e++) {
                 float th = 0.f, tl = 0.f;
@@ -302,9 +307,7 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict
                     float x = v[L][e] * __int_as_float((127 - OZ_BITS * (L + 2)) << 23);
                     dfs_add(th, tl, x, 0.f);
                 }
-                float &h = acc_h[r * OZ_N + c0 + e];
-                float &lo = acc_l[r * OZ_N + c0 + e];
-                dfs_add(h, lo, th, tl);
+                dfs_add(acc_h[16 * h + e], acc_l[16 * h + e], th, tl);
             }
         }
         tc_fence_before();
@@ -312,17 +315,16 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __nv_bfloat16 *__restrict
         tc_fence_after();
     }
     if (!ok && err) atomicExch(err, 1);
-    // write: row r of the tile -> basis vector (r0 + r) / 2, Re or Im part
-    const long long R = r0 + threadIdx.x;
+    // write: row of the tile -> basis vector (r0 + row) / 2, Re or Im part
+    const long long R = r0 + row;
     if (R < 2LL * k) {
         const int l = (int)(R >> 1);
         const int Ex = Ea[l];
         double *crow = (double *)(C + (long long)l * ldC) + (R & 1);
-        for (int c = 0; c < OZ_N; c++) {
-            long long j = j0 + c;
-            if (j >= Mb) break;
-            double t = (double)acc_h[threadIdx.x * OZ_N + c] + (double)acc_l[threadIdx.x * OZ_N + c];
-            crow[2 * (col_off + j)] = ldexp(t, Ex + Eb[j]);
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+            const long long j = j0 + cbase + c;
+            if (j < Mb) crow[2 * (col_off + j)] = ldexp((double)acc_h[c] + (double)acc_l[c], Ex + Eb[j]);
         }
     }
     tc_fence_before();
@@ -380,14 +382,14 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
     const long long nst = Kp / OZ_KS;
     k_oz_slice_B<<<dim3((unsigned)(Cp / OZ_N), (unsigned)((nst + OZ_SLICE_ST - 1) / OZ_SLICE_ST)), 256, 0, s>>>(
         X, N, Mb, ldX, Kp, Eb, Bs);
-    const size_t dsm = (size_t)OZ_NBUF * OZ_S * (OZ_M + OZ_N) * OZ_KS * 2 + (size_t)2 * OZ_M * OZ_N * 4;
+    const size_t dsm = (size_t)OZ_NBUF * OZ_S * (OZ_M + OZ_N) * OZ_KS * 2;  // 210 KB ring
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
         attr = true;
     }
     dim3 grid((unsigned)(Cp / OZ_N), (unsigned)(Rp / OZ_M));
-    k_oz_gemm<<<grid, 128, dsm, s>>>(As, Bs, Ea, Eb, k, Mb, Kp, Rp, Cp, C, ldC, col_off, err);
+    k_oz_gemm<<<grid, OZ_THREADS, dsm, s>>>(As, Bs, Ea, Eb, k, Mb, Kp, Rp, Cp, C, ldC, col_off, err);
     return cudaGetLastError();
 }
 
