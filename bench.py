@@ -123,20 +123,24 @@ def reduce_across_ranks(dist, ms, nbytes):
     return float(m[0].item()), float(t[1].item())
 
 
-def cpu_oracle_run(m_sample: int, steps: int = 1):
-    """Times the FP64 C oracle on an N x m_sample column sample (seed 1)."""
+def cpu_oracle_run(m_sample: int, steps: int = 1, omp: bool = False, want_result: bool = False):
+    """Times the FP64 C oracle on an N x m_sample column sample (seed 1);
+    omp: the -fopenmp build (column loops on all host cores)."""
     from oracle import oracle
     from paper_1805_06124_gb300 import synth
-    oracle.build()
+    oracle.build(omp=omp)
     S = synth.chirps(N_DEF, m_sample, SEED)
     t_tot, by = 0.0, 0.0
     k = 0
+    r = None
     for _ in range(steps):
         t0 = time.perf_counter()
-        r = oracle.rb_greedy(S, TOL, KMAX)
+        r = oracle.rb_greedy(S, TOL, KMAX, omp=omp)
         t_tot += time.perf_counter() - t0
         k = r["k"]
         by += k * (16.0 * N_DEF * m_sample + 16.0 * N_DEF + 41.0 * m_sample)
+    if want_result:
+        return by / t_tot / 1e9, t_tot / steps, k, r
     return by / t_tot / 1e9, t_tot / steps, k
 
 
@@ -573,13 +577,25 @@ def run_ours(args):
         ctx_h.close()
         del Sh, outb, rh
 
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = 1
-        gbs, t_cpu, k_cpu = cpu_oracle_run(CPU_SAMPLE_M, 1)
+        gbs, t_cpu, k_cpu, r1 = cpu_oracle_run(CPU_SAMPLE_M, 1, want_result=True)
         cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"one full greedy on {CPU_SAMPLE_M} of {M} columns (N={N}, seed {SEED}, tol {TOL}), "
                          f"k={k_cpu}, {t_cpu:.1f} s"}
+        # the paper's shared-memory scheme: the same oracle with its column
+        # loops on all host cores (identical results)
+        try:
+            gbs_o, t_o, k_o, r2 = cpu_oracle_run(CPU_SAMPLE_M, 1, omp=True, want_result=True)
+            import numpy as np
+            cpu_omp = {"value": round(gbs_o, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle, OpenMP",
+                       "sample": f"the same {CPU_SAMPLE_M}-column sample, {t_o:.1f} s",
+                       "identical_to_single_thread": bool(k_o == k_cpu and
+                                                          np.array_equal(r1["pivots"], r2["pivots"]) and
+                                                          np.array_equal(r1["err_curve"], r2["err_curve"]))}
+        except Exception as e:  # no OpenMP runtime on this host
+            cpu_omp = {"unavailable": str(e)[:200]}
 
     extra_split = extra_batched = None
     if rank == 0 and world == 1:
@@ -609,6 +625,7 @@ def run_ours(args):
                              "traffic": (round(tpb * per_launch) if tpb else None),
                              "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": round(sweep_ms, 4)},
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
+                "cpu_baseline_openmp": cpu_omp,
                 "split_vs_fp64": extra_split, "batched": extra_batched, "after_greedy": extra_next}
         print(json.dumps(line), flush=True)
     if not (rank == 0 and world == 1):

@@ -44,15 +44,19 @@ _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_float_p = ctypes.POINTER(ctypes.c_float)
 
 
-def lib_path(plant: int = 0) -> str:
+def lib_path(plant: int = 0, omp: bool = False) -> str:
     name = "liborc.so" if plant == 0 else f"liborc_plant{plant}.so"
+    if omp:
+        name = "liborc_omp.so"
     return os.path.join(_BUILD, name)
 
 
-def build(plant: int = 0, force: bool = False) -> str:
+def build(plant: int = 0, force: bool = False, omp: bool = False) -> str:
     """Compile the oracle (or a planted-mistake variant used by the oracle's
-    own mutation tests) with gcc into ``oracle/_build``."""
-    out = lib_path(plant)
+    own mutation tests) with gcc into ``oracle/_build``.  ``omp``: the same
+    source with -fopenmp (column loops over all host cores; identical
+    results), used only to time the paper's shared-memory scheme."""
+    out = lib_path(plant, omp)
     with _LOCK:
         if (not force and os.path.exists(out)
                 and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
@@ -60,15 +64,16 @@ def build(plant: int = 0, force: bool = False) -> str:
         os.makedirs(_BUILD, exist_ok=True)
         tmp = out + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               f"-DORC_PLANT={plant}", _SRC, "-o", tmp, "-lm"]
+               f"-DORC_PLANT={plant}"] + (["-fopenmp"] if omp else []) + [_SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, out)
     return out
 
 
-def _lib(plant: int = 0) -> ctypes.CDLL:
-    if plant not in _LIBS:
-        lib = ctypes.CDLL(build(plant))
+def _lib(plant: int = 0, omp: bool = False) -> ctypes.CDLL:
+    key = "omp" if omp else plant
+    if key not in _LIBS:
+        lib = ctypes.CDLL(build(plant, omp=omp))
         lib.orc_rb_greedy.restype = ctypes.c_int
         lib.orc_rb_greedy.argtypes = [
             _c_double_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
@@ -92,8 +97,8 @@ def _lib(plant: int = 0) -> ctypes.CDLL:
         lib.orc_split.argtypes = [
             _c_double_p, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
             _c_float_p, _c_float_p, ctypes.c_longlong]
-        _LIBS[plant] = lib
-    return _LIBS[plant]
+        _LIBS[key] = lib
+    return _LIBS[key]
 
 
 def _dp(a: np.ndarray):
@@ -116,12 +121,13 @@ def _snapshots(S: np.ndarray) -> tuple[np.ndarray, int, int, int]:
 
 
 def rb_greedy(S, tol: float, kmax: int, kappa: float = 2.0, max_passes: int = 4,
-              forced=None, plant: int = 0) -> dict:
+              forced=None, plant: int = 0, omp: bool = False) -> dict:
     """RB-greedy (Alg. 3) in FP64.  See the module docstring for layouts.
 
     ``forced``: optional sequence of pivots to replay (forced-replay mode);
     the result then also carries, per replayed step, the oracle's own argmax,
     its max error, the forced column's error and the runner-up error.
+    ``omp``: run the column loops on all host cores (identical results).
     """
     S, N, M, ld = _snapshots(S)
     kcap = max(int(kmax), 0)
@@ -144,7 +150,7 @@ def rb_greedy(S, tol: float, kmax: int, kappa: float = 2.0, max_passes: int = 4,
     f_err = np.zeros(ndiag)
     second = np.zeros(ndiag)
     k = ctypes.c_int(0)
-    st = _lib(plant).orc_rb_greedy(
+    st = _lib(plant, omp).orc_rb_greedy(
         _dp(S.view(np.float64)), N, M, ld, float(tol), kcap, float(kappa), int(max_passes),
         fptr, nf,
         _dp(Q.view(np.float64)), piv.ctypes.data_as(_c_i64_p), _dp(errc), _dp(C.view(np.float64)),

@@ -177,14 +177,20 @@ int orc_rb_greedy(const double *S, i64 N, i64 M, i64 ldS, double tol, int kmax,
         free(norm2); free(acc); free(err); free(picked); free(v);
         return ORC_ENOMEM;
     }
-    int status = ORC_OK;
-    /* Alg. 3 steps "Define sigma_0(s_i) = ||s_i||" and "j(0) = arg sup". */
+    int status = ORC_OK, bad = 0;
+    /* Alg. 3 steps "Define sigma_0(s_i) = ||s_i||" and "j(0) = arg sup".
+     * Columns are independent; built with -fopenmp (the paper's shared-memory
+     * scheme, Sec. 6.2) they are split over threads, each column still summed
+     * sequentially, so the results do not depend on the thread count. */
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (i64 j = 0; j < M; j++) {
         norm2[j] = cnorm2(S + 2 * j * ldS, N);
         if (!isfinite(norm2[j]))
-            status = ORC_ENONFINITE;
+            bad |= 1;
         err[j] = norm2[j];
     }
+    if (bad)
+        status = ORC_ENONFINITE;
     if (status != ORC_OK)
         goto done;
     i64 minNM = N < M ? N : M;
@@ -239,6 +245,7 @@ int orc_rb_greedy(const double *S, i64 N, i64 M, i64 ldS, double tol, int kmax,
         if (passes) passes[k] = np;
         picked[J] = 1;
         /* Pivot search of the next step: c_j = q^H s_j, Eq. (Residual). */
+#pragma omp parallel for schedule(static)
         for (i64 j = 0; j < M; j++) {
             double cr, ci;
             cdot_conj(q, S + 2 * j * ldS, N, &cr, &ci);

@@ -286,3 +286,20 @@ def test_split_definition(orc):
     rem = S - hi.astype(np.complex128)
     np.testing.assert_array_equal(lo, rem.astype(np.complex64))
     assert np.max(np.abs(S - hi - lo.astype(np.complex128)) / np.abs(S)) <= 2.0 ** -47
+
+
+def test_openmp_build_gives_identical_results(orc):
+    """The -fopenmp build of the oracle (column loops over all host cores)
+    returns bit-identical results: each column is still summed sequentially."""
+    from paper_1805_06124_gb300 import synth
+    S = synth.chirps(256, 700, seed=8)
+    a = orc.rb_greedy(S, 1e-10, 200)
+    try:
+        b = orc.rb_greedy(S, 1e-10, 200, omp=True)
+    except Exception as e:  # no OpenMP runtime on this host
+        pytest.skip(f"no -fopenmp build: {e}")
+    assert a["k"] == b["k"]
+    np.testing.assert_array_equal(a["pivots"], b["pivots"])
+    np.testing.assert_array_equal(a["err_curve"], b["err_curve"])
+    np.testing.assert_array_equal(a["Q"], b["Q"])
+    np.testing.assert_array_equal(a["C"], b["C"])
