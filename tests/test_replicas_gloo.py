@@ -25,7 +25,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_reduction():
     port = 29500 + os.getpid() % 1000
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a multi-threaded test process
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     assert out[0] == out[1] == (15.0, 3e9)
