@@ -790,25 +790,15 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
     RB_CK(cudaMemcpyAsync(dP, bp.data(), nprob * sizeof(rbk::BProb), cudaMemcpyHostToDevice, sm), "copy problems");
     RB_CK(cudaMemcpyAsync(dPP, pp.data(), nprob * sizeof(rbk::Prob), cudaMemcpyHostToDevice, sm), "copy problems");
     RB_CK(cudaMemcpyAsync(dcol, col0.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm), "copy prefix");
-    // chunk widths: mode 0 / 1 = 32 / 128 columns for every problem; mode 2 =
-    // 32 x (8192 / N) rounded down to a power of two (at most 512): chunks of
-    // about the same bytes for short and long columns
-    auto cw_of = [&](int b, int mode) -> int {
-        if (mode < 2) return CWs[mode];
-        int cw = 32;
-        while (cw < 512 && (long long)cw * 2 * probs[b].N <= 32LL * 8192) cw *= 2;
-        return cw;
-    };
-    // chunk prefix sums and the per-problem widths on the device
-    auto upload_chunks = [&](int mode) -> cudaError_t {
+    auto chunk_prefix = [&](int CW) {
         std::vector<long long> c(nprob + 1, 0);
-        for (int b = 0; b < nprob; b++) {
-            bp[b].cw = cw_of(b, mode);
-            c[b + 1] = c[b] + (probs[b].M + bp[b].cw - 1) / bp[b].cw;
-        }
+        for (int b = 0; b < nprob; b++) c[b + 1] = c[b] + (probs[b].M + CW - 1) / CW;
+        return c;
+    };
+    // chunk prefix sums on the device
+    auto upload_chunks = [&](int CW) -> cudaError_t {
+        std::vector<long long> c = chunk_prefix(CW);
         cudaError_t e1 = cudaMemcpyAsync(dch, c.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice, sm);
-        if (e1 != cudaSuccess) return e1;
-        e1 = cudaMemcpyAsync(dP, bp.data(), nprob * sizeof(rbk::BProb), cudaMemcpyHostToDevice, sm);
         if (e1 != cudaSuccess) return e1;
         return cudaStreamSynchronize(sm);
     };
@@ -820,33 +810,32 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
             RB_CK(rbk::launch_split(pp[b].S, probs[b].N, probs[b].M, probs[b].ldS, (float2 *)bp[b].hi,
                                     (float2 *)bp[b].lo, ldHs[b], pp[b].norm2, sm),
                   "split");
-    int best_v = v0 + 3, best_cw = 0;  // best_cw: chunk-width mode
+    int best_v = v0 + 3, best_cw = 32;
     auto it_t = ctx->tune.find(key);
     if (it_t != ctx->tune.end()) {
         best_v = it_t->second.first;
         best_cw = it_t->second.second;
     } else {
         float best_ms = 1e30f;
-        for (int ci = 0; ci < 3; ci++) {
-            RB_CK(upload_chunks(ci), "copy chunks");
+        for (int ci = 0; ci < 2; ci++) {
+            RB_CK(upload_chunks(CWs[ci]), "copy chunks");
             for (int v = v0; v < v0 + 6; v++) {
                 int g = rbk::bsweep_grid(v, ctx->device);
                 float ms = 0.f;
                 for (int rep = 0; rep < 2; rep++) {
                     RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
-                    RB_CK(rbk::launch_bsweep(v, g, dP, nprob, dch, cw_of(0, ci), dpe, dpi, 1, sm), "dry sweep");
+                    RB_CK(rbk::launch_bsweep(v, g, dP, nprob, dch, CWs[ci], dpe, dpi, 1, sm), "dry sweep");
                     RB_CK(cudaEventRecord(ctx->ev1, sm), "cudaEventRecord");
                     RB_CK(cudaEventSynchronize(ctx->ev1), "cudaEventSynchronize");
                     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
                 }
                 if (rb_log_level() > 0)
-                    fprintf(stderr, "rb autotune: %s U=%d threads=%d chunks=%s  %.3f ms\n",
-                            presplit ? "hi/lo" : "complex128", 2 << (v % 3), rbk::bsweep_threads(v),
-                            ci == 0 ? "32" : (ci == 1 ? "128" : "32x8192/N"), ms);
+                    fprintf(stderr, "rb autotune: %s U=%d threads=%d CW=%d  %.3f ms\n",
+                            presplit ? "hi/lo" : "complex128", 2 << (v % 3), rbk::bsweep_threads(v), CWs[ci], ms);
                 if (ms < best_ms) {
                     best_ms = ms;
                     best_v = v;
-                    best_cw = ci;
+                    best_cw = CWs[ci];
                 }
             }
         }

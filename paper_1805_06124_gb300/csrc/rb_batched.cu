@@ -1,7 +1,7 @@
 // rb_batched.cu -- many independent greedy problems of uneven N and M.
 //
 // The sweep of every active problem runs in ONE persistent launch: the
-// column ranges of all problems are cut into chunks (cw columns, per problem), the chunks
+// column ranges of all problems are cut into chunks of CW columns, the chunks
 // are numbered across problems (prefix sums), and each block takes chunks in
 // a grid-stride loop, finds their problem by binary search, and streams the
 // columns warp by warp.  When a hi/lo copy of the batch fits in free device
@@ -12,11 +12,9 @@
 // problem by a second small kernel, which also applies each problem's own
 // stopping rule; stopped problems' chunks return at once.
 //
-// The tunables -- loads in flight per lane (U), threads per block and the
-// chunk widths (32 or 128 columns for every problem, or 32 x 8192 / N so that
-// chunks of short columns carry as many bytes as those of long ones) -- are
-// picked by timing every variant on a dry sweep of the batch itself (see
-// rb_api.cu).
+// The tunables -- loads in flight per lane (U), threads per block and
+// columns per chunk (CW) -- are picked by timing every variant on a dry sweep
+// of the batch itself (see rb_api.cu).
 #include "rb_internal.cuh"
 
 namespace rbk {
@@ -147,8 +145,8 @@ __global__ void __launch_bounds__(THREADS) k_bsweep(const BProb *__restrict__ P,
         if (!s_skip) {
             const BProb &pr = P[b];
             const int k = s_k;
-            const long long j0 = (ch - chunk0[b]) * pr.cw;
-            const long long j1 = j0 + pr.cw < pr.M ? j0 + pr.cw : pr.M;
+            const long long j0 = (ch - chunk0[b]) * CW;
+            const long long j1 = j0 + CW < pr.M ? j0 + CW : pr.M;
             double be = -INFINITY;
             long long bi = kNoIdx;
             for (long long j = j0 + warp; j < j1; j += NW) {

@@ -109,7 +109,7 @@ struct BProb {
     const float2 *ql;
     DevState *st;
     int kmax;
-    int cw;  // columns per sweep chunk
+    int pad;
     long long minNM;
     double tol;
     const float2 *hi;  // pre-split copy (null: split in registers)
