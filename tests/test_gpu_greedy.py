@@ -195,6 +195,20 @@ def test_project_parity(orc, rbm, path):
     c.close()
 
 
+@pytest.mark.parametrize("k", [64, 65, 130])
+def test_project_tc_row_tiles(orc, rbm, k):
+    """k = 64, 65, 130: one, two (the second almost empty) and three 128-row
+    tiles of the tensor-core projection; odd N (K padding), ragged columns."""
+    c = rbm.RB(device=0)
+    rng = np.random.default_rng(k)
+    Q = rng.standard_normal((k, 777)) + 1j * rng.standard_normal((k, 777))
+    X = rng.standard_normal((301, 777)) + 1j * rng.standard_normal((301, 777))
+    Cg = c.project(upload(Q), upload(X)).cpu().numpy()
+    Cr = orc.project(Q, X)
+    assert np.max(np.abs(Cg - Cr)) < _tc_bound(Q, X), (np.max(np.abs(Cg - Cr)), _tc_bound(Q, X))
+    c.close()
+
+
 def test_project_tc_chirps_ragged(orc, rbm):
     """Basis of a chirp greedy projected onto held-out chirps: odd N, k not a
     multiple of the tile, Mx not a multiple of 64; within 1e-12 of the oracle."""

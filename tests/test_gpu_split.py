@@ -156,3 +156,17 @@ def test_split_matches_fp64_form_on_gpu_split(orc, rbm):
         rep = parity.replay_and_check(orc, S, g, 1e-10, 300)
         parity.compare(g, rep, S, c_rel=cr)
     c.close()
+
+
+@pytest.mark.parametrize("kmax", [64, 65, 130])
+def test_split_several_row_tiles(orc, rbm, kmax):
+    """Bases of 64, 65 and 130 vectors: the projection onto lo runs over one,
+    two (the second holding two rows) and three 128-row tiles of the basis."""
+    S = synth.random_complex(520, 333, seed=kmax, scales=np.exp(-np.linspace(0.0, 8.0, 520)))
+    c = rbm.RB(device=0)
+    H, L = split_upload(orc, S)
+    g = npy(c.greedy_split(H, L, 0.0, kmax))
+    assert g["k"] == kmax and g["status"] == rbm.KMAX_REACHED
+    rep = parity.replay_and_check(orc, S, g, 0.0, kmax)
+    parity.compare(g, rep, S, err_atol=1e-12 * rep["err_curve"][0], c_rel=c_rel(S.shape[1]))
+    c.close()
