@@ -209,6 +209,28 @@ def test_project_tc_row_tiles(orc, rbm, k):
     c.close()
 
 
+def test_project_tc_column_batches(orc, rbm):
+    """N = 8192 and 20,000 columns: the slice planes would exceed the 4 GB
+    batch limit, so the columns go in two batches of 10,000 (the batch width is
+    halved until it fits); checked against the oracle on columns at both ends,
+    around the batch boundary and inside the second batch."""
+    c = rbm.RB(device=0)
+    N, M = 8192, 20000
+    rng = np.random.default_rng(11)
+    Q = rng.standard_normal((53, N)) + 1j * rng.standard_normal((53, N))
+    Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    X = c.generate(*synth.chirp_params(M, seed=12), N)
+    Cg = c.project(upload(Q), X)
+    cols = np.r_[0:40, 9900:10100, 18550:18650, M - 40:M]
+    Xs = X[torch.from_numpy(cols).cuda()].cpu().numpy()
+    Cr = orc.project(Q, Xs)
+    Cs = Cg[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+    assert np.max(np.abs(Cs - Cr)) < _tc_bound(Q, Xs), np.max(np.abs(Cs - Cr))
+    c.close()
+    del X, Cg
+    torch.cuda.empty_cache()
+
+
 def test_project_tc_chirps_ragged(orc, rbm):
     """Basis of a chirp greedy projected onto held-out chirps: odd N, k not a
     multiple of the tile, Mx not a multiple of 64; within 1e-12 of the oracle."""
