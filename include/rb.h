@@ -277,6 +277,16 @@ rb_status rb_eim(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ, 
 rb_status rb_validate(rb_ctx *ctx, const void *Q, long long N, int k, long long ldQ, const long long *nodes,
                       const void *Vinv, const void *T, long long Mt, long long ldT, double *err_proj, double *err_eim);
 
+/* Per-iteration trace of the last rb_greedy / rb_greedy_host / rb_greedy_resume
+ * on ctx (FP64 form; host arrays of capacity cap, any may be NULL):
+ *   imgs_passes[i]  IMGS passes of the i-th vector built by the call (the
+ *                   paper reports fewer than three, Sec. 6.1.2);
+ *   sweep_ms[i], imgs_ms[i]  CUDA-event times of that iteration's sweep and
+ *                   IMGS steps (zeros unless the context has RB_FLAG_TIMING).
+ * *n receives the number of iterations (entries beyond cap are not written).
+ * Errors: RB_EINVAL. */
+rb_status rb_trace(const rb_ctx *ctx, int *imgs_passes, double *sweep_ms, double *imgs_ms, int cap, int *n);
+
 /* Same as rb_greedy, but S, every output array of *out, and the result are in
  * HOST memory (pinned or pageable).  The call copies S to the device and the
  * outputs back inside the call; device workspace is owned by the context. */

@@ -36,6 +36,9 @@ struct rb_ctx {
     rbk::DevState *st_host = nullptr;  // pinned copy of the device state
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> sweep_ev;
+    std::vector<cudaEvent_t> imgs_ev;   // IMGS events per iteration of the FP64 form (RB_FLAG_TIMING)
+    std::vector<int> trace_passes;      // last FP64-form call: IMGS passes per iteration
+    std::vector<double> trace_sweep_ms, trace_imgs_ms;  // and phase times (RB_FLAG_TIMING)
     std::vector<cudaEvent_t> recon_ev;  // phase events of rb_reconstruct (RB_FLAG_TIMING)
     double recon_ms[7] = {0};           // phase times of the last rb_reconstruct
     int recon_counts[4] = {0};          // Jacobi sweeps / rotations, pass 1 and pass 2
@@ -169,6 +172,7 @@ void rb_destroy(rb_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t ev : ctx->sweep_ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : ctx->recon_ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : ctx->imgs_ev) cudaEventDestroy(ev);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ws) cudaFree(ctx->ws);
@@ -342,6 +346,18 @@ rb_status rb_validate(rb_ctx *ctx, const void *Q, long long N, int k, long long 
     return RB_OK;
 }
 
+rb_status rb_trace(const rb_ctx *ctx, int *imgs_passes, double *sweep_ms, double *imgs_ms, int cap, int *n) {
+    if (!ctx || cap < 0 || !n) return RB_EINVAL;
+    const int np = (int)ctx->trace_passes.size();
+    *n = np;
+    for (int i = 0; i < np && i < cap; i++) {
+        if (imgs_passes) imgs_passes[i] = ctx->trace_passes[i];
+        if (sweep_ms) sweep_ms[i] = i < (int)ctx->trace_sweep_ms.size() ? ctx->trace_sweep_ms[i] : 0.0;
+        if (imgs_ms) imgs_ms[i] = i < (int)ctx->trace_imgs_ms.size() ? ctx->trace_imgs_ms[i] : 0.0;
+    }
+    return RB_OK;
+}
+
 rb_status rb_reconstruct_stats(const rb_ctx *ctx, double *ms, int *counts) {
     if (!ctx) return RB_EINVAL;
     if (ms)
@@ -378,6 +394,7 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     size_t np = (size_t)(G > gN ? G : gN);
     size_t o_np = L.add(np * 8), o_be = L.add((size_t)G * 8), o_bi = L.add((size_t)G * 8);
     size_t o_st = L.add(sizeof(rbk::DevState));
+    size_t o_pass = L.add((size_t)kcap * sizeof(int));
     // the periodic recompute reads the stored coefficients: keep them in the
     // workspace when the caller does not ask for C
     const bool ws_C = !out->C && o.recompute_period > 0;
@@ -419,6 +436,7 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     p.bpart_err = (double *)(w + o_be);
     p.bpart_idx = (long long *)(w + o_bi);
     p.st = (rbk::DevState *)(w + o_st);
+    p.passes_out = (int *)(w + o_pass);
 
     cudaStream_t sm = ctx->stream;
     const bool timing = (o.flags & RB_FLAG_TIMING) != 0;
@@ -429,6 +447,16 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
             ctx->sweep_ev.push_back(ev);
         }
     }
+    if (timing && (int)ctx->imgs_ev.size() < 2 * kcap) {
+        while ((int)ctx->imgs_ev.size() < 2 * kcap) {
+            cudaEvent_t ev;
+            RB_CK(cudaEventCreate(&ev), "cudaEventCreate");
+            ctx->imgs_ev.push_back(ev);
+        }
+    }
+    ctx->trace_passes.clear();
+    ctx->trace_sweep_ms.clear();
+    ctx->trace_imgs_ms.clear();
     int nlaunch = 0;
     RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
     RB_CK(cudaMemsetAsync(p.st, 0, sizeof(rbk::DevState), sm), "memset state");
@@ -448,7 +476,9 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     bool stopped = false;
     while (!stopped) {
         for (int t = 0; t < o.iters_per_sync && it < kcap; t++, it++) {
+            if (timing) RB_CK(cudaEventRecord(ctx->imgs_ev[2 * it], sm), "cudaEventRecord");
             RB_CK(rbk::launch_imgs(p, G, false, sm, &nlaunch), "imgs");
+            if (timing) RB_CK(cudaEventRecord(ctx->imgs_ev[2 * it + 1], sm), "cudaEventRecord");
             if (o.recompute_period > 0) {
                 RB_CK(rbk::launch_recompute(p, o.recompute_period, G, sm), "recompute");
                 nlaunch += 1;
@@ -482,10 +512,19 @@ static rb_status greedy_device(rb_ctx *ctx, const void *S, long long N, long lon
     out->ms_sweep = 0.0;
     if (timing) {
         for (int i = k0; i < k0 + hs.n_sweeps && i < it; i++) {
-            float t = 0.f;
+            float t = 0.f, ti = 0.f;
             cudaEventElapsedTime(&t, ctx->sweep_ev[2 * i], ctx->sweep_ev[2 * i + 1]);
+            cudaEventElapsedTime(&ti, ctx->imgs_ev[2 * i], ctx->imgs_ev[2 * i + 1]);
             out->ms_sweep += t;
+            ctx->trace_sweep_ms.push_back(t);
+            ctx->trace_imgs_ms.push_back(ti);
         }
+    }
+    if (hs.k > k0) {
+        ctx->trace_passes.resize((size_t)(hs.k - k0));
+        RB_CK(cudaMemcpy(ctx->trace_passes.data(), p.passes_out + k0, (size_t)(hs.k - k0) * sizeof(int),
+                         cudaMemcpyDeviceToHost),
+              "passes copy");
     }
     // algorithmic bytes of one sweep: S (16 N M: complex128, or hi+lo complex64),
     // q (16 N), norm2 + acc reads (16 M), picked (M), C row + acc writes (24 M)

@@ -167,6 +167,7 @@ __device__ __forceinline__ void imgs_finalize(const Prob &p) {
         long long J = st->J;
         p.pivots[k] = J;
         if (p.rdiag) p.rdiag[k] = nv;
+        if (p.passes_out) p.passes_out[k] = st->passes;
         p.picked[J] = 1;
     }
 }

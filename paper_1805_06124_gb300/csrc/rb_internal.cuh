@@ -93,6 +93,7 @@ struct Prob {
     int *tc_err;       // set when a tensor-core wait ran out
     double *dacc;      // D_j = sum_l (|c_lj|^2 - |c~_lj|^2) over the rows re-checked so far
     int *dcnt;         // rows covered by D_j
+    int *passes_out;   // IMGS passes of iteration k at [k] (may be null)
 };
 
 // One problem of a batch (rb_greedy_batched): what the persistent sweep and

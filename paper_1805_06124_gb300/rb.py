@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.rb_reconstruct.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_double, c_void_p,
                                    c_ll, c_void_p, c_void_p, ctypes.POINTER(c_int)]
     lib.rb_reconstruct_stats.argtypes = [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]
+    lib.rb_trace.argtypes = [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                             c_int, ctypes.POINTER(c_int)]
     lib.rb_greedy_resume.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int, c_int, c_ll,
                                      ctypes.POINTER(Result)]
     lib.rb_eim.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_void_p, c_void_p, c_ll, c_void_p]
@@ -97,7 +99,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                       ctypes.POINTER(Result)]
     lib.rb_greedy_batched.restype = c_int
     for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_greedy_split", "rb_project",
-              "rb_reconstruct", "rb_reconstruct_stats", "rb_eim", "rb_validate", "rb_greedy_resume"):
+              "rb_reconstruct", "rb_reconstruct_stats", "rb_eim", "rb_validate", "rb_greedy_resume", "rb_trace"):
         getattr(lib, f).restype = c_int
     _LIB = lib
     return lib
@@ -449,6 +451,16 @@ class RB:
         if want_eim:
             out["err_eim"] = ee[:Mt]
         return out
+
+    def trace(self):
+        """Per-iteration trace of the last FP64-form greedy call: IMGS passes,
+        and sweep / IMGS times in ms (with timing=True)."""
+        n = c_int(0)
+        self._check(self.lib.rb_trace(self._h, None, None, None, 0, ctypes.byref(n)))
+        cap = n.value
+        ps, sw, im = (c_int * max(cap, 1))(), (c_double * max(cap, 1))(), (c_double * max(cap, 1))()
+        self._check(self.lib.rb_trace(self._h, ps, sw, im, cap, ctypes.byref(n)))
+        return dict(imgs_passes=list(ps[:cap]), sweep_ms=list(sw[:cap]), imgs_ms=list(im[:cap]))
 
     RECON_PHASES = ("gram1_fp32", "jacobi1_fp32", "newton_schulz", "transform_df32", "gram2_df32",
                     "jacobi2_fp64", "basis")

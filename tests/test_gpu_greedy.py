@@ -195,6 +195,29 @@ def test_project_parity(orc, rbm, path):
     c.close()
 
 
+def test_trace_per_iteration(orc, rbm):
+    """rb_trace: one entry per vector built; the pass counts add up to the
+    call's total and stay below the cap (the paper reports fewer than three
+    passes, Sec. 6.1.2); with timing, the sweep times add up to ms_sweep."""
+    c = rbm.RB(device=0, timing=True)
+    S = synth.chirps(1024, 2048, seed=0)
+    g = c.greedy(upload(S), 1e-10, 300)
+    t = c.trace()
+    k = g["k"]
+    assert len(t["imgs_passes"]) == k
+    assert sum(t["imgs_passes"]) == g["imgs_passes"]
+    # the first vector has no basis to be orthogonalised against
+    ps = t["imgs_passes"]
+    assert ps[0] in (0, 1) and all(1 <= p_ <= 4 for p_ in ps[1:]) and np.mean(ps[1:]) < 3, ps
+    assert all(x > 0 for x in t["sweep_ms"]) and all(x > 0 for x in t["imgs_ms"])
+    assert abs(sum(t["sweep_ms"]) - g["ms_sweep"]) < 1e-3 * max(g["ms_sweep"], 1.0)
+    # a resumed call traces only the vectors it built
+    part = c.greedy(upload(S), 1e-10, 10)
+    r = c.greedy_resume(upload(S), 1e-10, 300, part)
+    assert len(c.trace()["imgs_passes"]) == r["k"] - 10
+    c.close()
+
+
 @pytest.mark.parametrize("k", [64, 65, 130])
 def test_project_tc_row_tiles(orc, rbm, k):
     """k = 64, 65, 130: one, two (the second almost empty) and three 128-row
