@@ -124,8 +124,10 @@ __global__ void __launch_bounds__(kThreads) k_bnorms(const BProb *__restrict__ P
     }
 }
 
+// The pre-split variants are held to 64 registers (32 warps per SM, as the
+// single-problem sweep) so that enough loads are in flight per SM.
 template <int U, int THREADS, bool SPLIT>
-__global__ void __launch_bounds__(THREADS) k_bsweep(const BProb *__restrict__ P, int nprob,
+__global__ void __launch_bounds__(THREADS, SPLIT ? 1024 / THREADS : 1) k_bsweep(const BProb *__restrict__ P, int nprob,
                                                     const long long *__restrict__ chunk0, int CW,
                                                     double *__restrict__ part_err, long long *__restrict__ part_idx,
                                                     int dry) {
