@@ -37,10 +37,12 @@ namespace rbk {
 constexpr int RG_T = 32;          // columns per staged tile
 constexpr int RG_THREADS = 512;   // Gram block (triangle of entries)
 constexpr int RG_MAXE = 13;       // entries per thread: ceil(112 * 113 / 2 / 512)
+constexpr int RG_MAXE_S = 4;      // the same for j <= 63 (2016 entries)
 constexpr int RJ_THREADS = 512;   // Jacobi block
 constexpr int RJ_PAIRS = 64;      // index pairs per step (j <= 128)
 constexpr int RT_THREADS = 256;   // transform block
 constexpr int RT_ROWS = 14;       // output rows per warp: ceil(112 / 8)
+constexpr int RT_ROWS_S = 7;      // the same for j <= 56
 constexpr int kMaxJ = 112;
 constexpr int kJacobiMaxSweeps = 60;
 
@@ -75,17 +77,17 @@ __device__ __forceinline__ float4 split_c(double2 v) {
 // The block stages RG_T columns of all j rows in shared memory; thread t
 // owns the upper-triangle entries e = t + RG_THREADS i (row-major order).
 // DF: double-float products and sums; otherwise FP32.
-template <bool DF>
-__global__ void __launch_bounds__(RG_THREADS) k_gram_tri(const double2 *__restrict__ A, long long ldA, int j,
+template <bool DF, int MAXE>
+__global__ void __launch_bounds__(RG_THREADS, MAXE <= RG_MAXE_S ? 2 : 1) k_gram_tri(const double2 *__restrict__ A, long long ldA, int j,
                                                           long long M, long long chunk, const int *__restrict__ emax,
                                                           double2 *__restrict__ part) {
     extern __shared__ float4 st[];  // j x (RG_T + 1)
     const int ne = j * (j + 1) / 2;
     const double sc = emax ? c_scale(emax) : 1.0;
-    int eab[RG_MAXE];  // row offsets of a (low 16 bits) and b (high 16 bits) in the tile
-    float acc[RG_MAXE][4];
+    int eab[MAXE];  // row offsets of a (low 16 bits) and b (high 16 bits) in the tile
+    float acc[MAXE][4];
 #pragma unroll
-    for (int i = 0; i < RG_MAXE; i++) {
+    for (int i = 0; i < MAXE; i++) {
         int e = threadIdx.x + RG_THREADS * i, a = 0;
         while (a < j && e >= j - a) {
             e -= j - a;
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(RG_THREADS) k_gram_tri(const double2 *__restri
         const int nc = m1 - mt < RG_T ? (int)(m1 - mt) : RG_T;
         for (int c = 0; c < nc; c++) {
 #pragma unroll
-            for (int i = 0; i < RG_MAXE; i++) {
+            for (int i = 0; i < MAXE; i++) {
                 if (RG_THREADS * i >= ne) break;
                 if ((int)threadIdx.x + RG_THREADS * i < ne) {
                     const float4 x = st[(eab[i] & 0xFFFF) + c], y = st[(eab[i] >> 16) + c];
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(RG_THREADS) k_gram_tri(const double2 *__restri
         }
     }
 #pragma unroll
-    for (int i = 0; i < RG_MAXE; i++) {
+    for (int i = 0; i < MAXE; i++) {
         if ((int)threadIdx.x + RG_THREADS * i < ne)
             part[((long long)blockIdx.x * j + (eab[i] & 0xFFFF) / (RG_T + 1)) * j + (eab[i] >> 16) / (RG_T + 1)] =
                 make_double2((double)acc[i][0] + (double)acc[i][1], (double)acc[i][2] + (double)acc[i][3]);
@@ -441,7 +443,8 @@ __global__ void k_ns_update(const double2 *__restrict__ V, const double2 *__rest
 // Lane = column within a tile of 32, warp w = rows a = w + 8 i.  The C tile
 // (j x 32, split) sits in shared memory; V (split) is read with warp-wide
 // broadcast loads.
-__global__ void __launch_bounds__(RT_THREADS) k_transform_df(const float4 *__restrict__ Vsp, const double2 *__restrict__ C,
+template <int ROWS>
+__global__ void __launch_bounds__(RT_THREADS, ROWS <= RT_ROWS_S ? 3 : 1) k_transform_df(const float4 *__restrict__ Vsp, const double2 *__restrict__ C,
                                                              long long ldC, int j, long long M,
                                                              const int *__restrict__ emax, double2 *__restrict__ B,
                                                              long long ldB) {
@@ -459,13 +462,13 @@ __global__ void __launch_bounds__(RT_THREADS) k_transform_df(const float4 *__res
             tsm[u] = split_c(v);
         }
         __syncthreads();
-        float acc[RT_ROWS][4];
+        float acc[ROWS][4];
 #pragma unroll
-        for (int i = 0; i < RT_ROWS; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+        for (int i = 0; i < ROWS; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
         for (int l = 0; l < j; l++) {
             const float4 x = tsm[l * 32 + lane];
 #pragma unroll
-            for (int i = 0; i < RT_ROWS; i++) {
+            for (int i = 0; i < ROWS; i++) {
                 const int a = w + 8 * i;
                 if (a < j) {
                     const float4 v = __ldg(Vsp + l * j + a);
@@ -476,7 +479,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_transform_df(const float4 *__res
         const long long m = mt + lane;
         if (m < M) {
 #pragma unroll
-            for (int i = 0; i < RT_ROWS; i++) {
+            for (int i = 0; i < ROWS; i++) {
                 const int a = w + 8 * i;
                 if (a < j)
                     B[(long long)a * ldB + m] =
@@ -625,10 +628,14 @@ cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M
     const int gr = (j * (j + 1) / 2 + 7) / 8;  // one warp per entry, 8 warps per block
     const size_t gsm = (size_t)j * (RG_T + 1) * 16;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_gram_tri<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)) !=
-            cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_gram_tri<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)) !=
-            cudaSuccess)
+    // register arrays sized for the largest j, or for j <= 63 / 56 (more
+    // warps per SM on the common sizes)
+    const bool small = j <= 56;
+    auto gram32 = small ? k_gram_tri<false, RG_MAXE_S> : k_gram_tri<false, RG_MAXE>;
+    auto gramdf = small ? k_gram_tri<true, RG_MAXE_S> : k_gram_tri<true, RG_MAXE>;
+    auto transf = small ? k_transform_df<RT_ROWS_S> : k_transform_df<RT_ROWS>;
+    if ((e = cudaFuncSetAttribute(gram32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(gramdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)) != cudaSuccess)
         return e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
@@ -637,7 +644,7 @@ cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M
     if (gx > 2LL * nsm) gx = 2LL * nsm;
     k_max_exp<<<dim3((unsigned)gx, (unsigned)(j < 8 ? j : 8)), 256, 0, s>>>(C, ldC, j, M, w.emax);
     // pass 1: FP32 Gram and Jacobi
-    k_gram_tri<false><<<nchunk, RG_THREADS, gsm, s>>>(C, ldC, j, M, chunk, w.emax, w.part);
+    gram32<<<nchunk, RG_THREADS, gsm, s>>>(C, ldC, j, M, chunk, w.emax, w.part);
     k_gram_reduce<<<gr, 256, 0, s>>>(w.part, j, nchunk, w.G1);
     if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_jacobi<float>(w.G1, j, 0x1p-22, w.lam, w.stats, w.rec, s)) != cudaSuccess) return e;
@@ -657,13 +664,13 @@ cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M
     if ((e = mark(3)) != cudaSuccess) return e;
     // pass 2: B = V1^H C, G2 = B B^H in double-float, Jacobi in FP64 from V1
     const size_t tsm = (size_t)j * 32 * 16;
-    if ((e = cudaFuncSetAttribute(k_transform_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(transf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) != cudaSuccess)
         return e;
     long long gt = (M + 31) / 32;
-    if (gt > 4LL * nsm) gt = 4LL * nsm;
-    k_transform_df<<<(unsigned)gt, RT_THREADS, tsm, s>>>(w.Vsp, C, ldC, j, M, w.emax, w.B, M);
+    if (gt > 6LL * nsm) gt = 6LL * nsm;
+    transf<<<(unsigned)gt, RT_THREADS, tsm, s>>>(w.Vsp, C, ldC, j, M, w.emax, w.B, M);
     if ((e = mark(4)) != cudaSuccess) return e;
-    k_gram_tri<true><<<nchunk, RG_THREADS, gsm, s>>>(w.B, M, j, M, chunk, nullptr, w.part);
+    gramdf<<<nchunk, RG_THREADS, gsm, s>>>(w.B, M, j, M, chunk, nullptr, w.part);
     k_gram_reduce<<<gr, 256, 0, s>>>(w.part, j, nchunk, w.G2);
     if ((e = mark(5)) != cudaSuccess) return e;
     if ((e = launch_jacobi<double>(w.G2, j, 0x1p-52, w.lam, w.stats + 2, w.rec, s)) != cudaSuccess) return e;
