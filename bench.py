@@ -463,6 +463,44 @@ def run_resume_once(args):
           flush=True)
 
 
+def run_streamed_once(args):
+    """The greedy on snapshots held in pinned host memory (rb_greedy_streamed)
+    at N x M chirps (seed 1, tol 1e-12): all columns resident (one pass over
+    host memory builds the device split copy), half resident, and a quarter
+    resident, each against the in-core call on the same matrix.  Device time
+    from the library's CUDA events (ms_total); host GB/s = bytes read from
+    host memory / ms_total; chunk-read fraction = chunk reads / (chunks x
+    iterations)."""
+    import torch
+    from paper_1805_06124_gb300 import rb, synth
+    c = rb.RB(device=0)
+    N, M = args.N, args.M
+    Sd = c.generate(*synth.chirp_params(M, 1), N)
+    c.greedy(Sd, 1e-12, 800)                                   # warm-up
+    ref = c.greedy(Sd, 1e-12, 800)
+    piv, k, ms_ref = ref["pivots"].cpu(), ref["k"], ref["ms_total"]
+    Sh = torch.empty((M, N), dtype=torch.complex128).pin_memory()
+    Sh.copy_(Sd)
+    del Sd, ref
+    torch.cuda.empty_cache()
+    runs = {}
+    with Clocks(0) as clk:
+        for label, res, cols in (("all_resident", M, 64), ("half_resident", M // 2, 64),
+                                 ("quarter_resident", M // 4, 64), ("quarter_resident_cols32", M // 4, 32)):
+            c.greedy_streamed(Sh, 1e-12, 800, resident=res, chunk_cols=cols)   # warm-up (workspace)
+            g = c.greedy_streamed(Sh, 1e-12, 800, resident=res, chunk_cols=cols)
+            st = c.streamed_stats()
+            runs[label] = {"resident": st["resident"], "chunk_cols": st["chunk_cols"], "chunks": st["chunks"],
+                           "ms": round(g["ms_total"], 3), "k": g["k"],
+                           "same_pivots": bool(torch.equal(g["pivots"].cpu(), piv)),
+                           "host_GB": round(st["host_bytes"] / 1e9, 2),
+                           "host_GBps": round(st["host_bytes"] / (g["ms_total"] * 1e-3) / 1e9, 1),
+                           "chunk_read_fraction": round(st["chunk_reads"] / max(1, st["chunks"] * g["k"]), 3)}
+    print(json.dumps({"workload": f"greedy on pinned host snapshots, chirps N={N} x M={M} seed 1, tol 1e-12 "
+                                  f"({16 * N * M / 1e9:.1f} GB in host memory)",
+                      "in_core_ms": round(ms_ref, 3), "k": k, "runs": runs, "clocks": clk.summary()}), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_1805_06124_gb300 import rb, synth
@@ -649,7 +687,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-next", action="store_true")
     ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate", "split", "project", "batched",
-                                                                "recon", "eim", "resume"])
+                                                                "recon", "eim", "resume", "streamed"])
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--k", type=int, default=53)
     ap.add_argument("--project-fp64", action="store_true")
@@ -666,6 +704,8 @@ def main():
         run_eim_once(args)
     elif args.workload == "resume":
         run_resume_once(args)
+    elif args.workload == "streamed":
+        run_streamed_once(args)
     elif args.workload == "batched":
         import torch
         from paper_1805_06124_gb300 import rb, synth

@@ -288,10 +288,43 @@ rb_status rb_validate(rb_ctx *ctx, const void *Q, long long N, int k, long long 
 rb_status rb_trace(const rb_ctx *ctx, int *imgs_passes, double *sweep_ms, double *imgs_ms, int cap, int *n);
 
 /* Same as rb_greedy, but S, every output array of *out, and the result are in
- * HOST memory (pinned or pageable).  The call copies S to the device and the
- * outputs back inside the call; device workspace is owned by the context. */
+ * HOST memory (pinned or pageable).  Pinned S under RB_SWEEP_DF32 is read in
+ * place over the host link (rb_greedy_streamed with resident = -1: no device
+ * copy of S; identical results); otherwise the call copies S to the device.
+ * The outputs are copied back inside the call; device workspace is owned by
+ * the context. */
 rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS,
                          double tol, int kmax, rb_result *out);
+
+/* The FP64-form greedy (Alg. 3, Eq. (Residual) bookkeeping, the same
+ * double-float sweep and IMGS as rb_greedy) on a snapshot matrix S that stays
+ * in HOST memory: the paper's largest runs hold S of about half a terabyte
+ * (Sec. 1, Sec. 6), beyond one GPU's memory.
+ *   S: host complex128 N x M column-major (ldS >= N), 16-byte aligned; pinned
+ *      memory is used in place, pageable memory is registered (mapped) for
+ *      the duration of the call.  Device memory is rejected (RB_EINVAL).
+ *   resident: columns 0..resident-1 keep a hi/lo split copy (16 ldH bytes per
+ *      column, ldH = N rounded up to 64) on the device; < 0 = as many as the
+ *      free device memory holds (after 4 GB of headroom).  The other columns
+ *      are read from host memory in chunks of chunk_cols (0 = 64) columns.
+ *   out: as for rb_greedy (DEVICE arrays).
+ * A chunk is read only when its errors, as of its last read plus a bound on
+ * their rounding drift, may reach the best error of the iteration; it then
+ * applies every basis vector it has not seen, in order and with the
+ * arithmetic of the in-core sweep.  Pivots, Q, C, err_curve, rdiag and
+ * final_err equal those of rb_greedy bit for bit.  Needs RB_SWEEP_DF32.
+ * Errors: as rb_greedy; RB_EINVAL for device S or chunk_cols outside
+ * [0, 2^20]; RB_ECUDA when the host memory cannot be mapped. */
+rb_status rb_greedy_streamed(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol,
+                             int kmax, long long resident, long long chunk_cols, rb_result *out);
+
+/* Statistics of the last rb_greedy_streamed on ctx: counts[0..3] = resident
+ * columns, chunks, columns per chunk, chunk reads (each applies one or more
+ * basis vectors); *host_bytes = bytes read from host memory (the first pass
+ * over all of S, the IMGS pivot columns and every chunk read); *ms_init = the
+ * CUDA-event time of the first pass (RB_FLAG_TIMING only, else 0).  Any
+ * pointer may be NULL.  Errors: RB_EINVAL. */
+rb_status rb_streamed_stats(const rb_ctx *ctx, long long *counts, double *host_bytes, double *ms_init);
 
 /* Projection onto a basis: C[l*ldC + j] = q_l^H x_j for l < k, j < Mx
  * (Sec. 2: a column is represented by its orthogonal projection onto the

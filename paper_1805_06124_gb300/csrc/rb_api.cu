@@ -43,6 +43,11 @@ struct rb_ctx {
     double recon_ms[7] = {0};           // phase times of the last rb_reconstruct
     int recon_counts[4] = {0};          // Jacobi sweeps / rotations, pass 1 and pass 2
     int grid_cache[2] = {0, 0};
+    // last rb_greedy_streamed: resident columns, chunks, columns per chunk,
+    // chunk updates, bytes read from host memory
+    long long str_stats[4] = {0, 0, 0, 0};
+    double str_host_bytes = 0.0;
+    double str_ms_init = 0.0;
     std::map<std::tuple<int, long long, long long>, std::pair<int, int>> tune;  // batch shape -> (variant, CW)
 };
 
@@ -1020,6 +1025,290 @@ rb_status rb_greedy_resume(rb_ctx *ctx, const void *S, long long N, long long M,
     return greedy_device(ctx, S, N, M, ldS, tol, kmax, out, k0);
 }
 
+// Host pointer of S as the device sees it; registers pageable memory for the
+// call (*registered = true) and rejects device memory.
+static rb_status host_view(rb_ctx *ctx, const void *S, size_t bytes, const double2 **dptr, bool *registered) {
+    *registered = false;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, S);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+        return fail(ctx, RB_EINVAL, "rb_greedy_streamed: S must be host memory (device arrays go to rb_greedy)");
+    if (at.type == cudaMemoryTypeUnregistered) {
+        RB_CK(cudaHostRegister(const_cast<void *>(S), bytes, cudaHostRegisterMapped), "cudaHostRegister of S");
+        *registered = true;
+    }
+    // pinned memory under unified addressing: the attributes carry the device
+    // view; otherwise ask for the mapping
+    void *d = nullptr;
+    if (cudaPointerGetAttributes(&at, S) == cudaSuccess && at.type == cudaMemoryTypeHost) d = at.devicePointer;
+    cudaGetLastError();
+    if (!d) {
+        e = cudaHostGetDevicePointer(&d, const_cast<void *>(S), 0);
+        if (e != cudaSuccess) cudaGetLastError();
+    }
+    if (!d) {
+        if (*registered) cudaHostUnregister(const_cast<void *>(S));
+        *registered = false;
+        return fail(ctx, RB_ECUDA, "rb_greedy_streamed: S has no device mapping (host memory not mapped)");
+    }
+    *dptr = (const double2 *)d;
+    return RB_OK;
+}
+
+static rb_status greedy_streamed_device(rb_ctx *ctx, const double2 *Sd, long long N, long long M, long long ldS,
+                                       double tol, int kmax, long long Mr, long long cols, rb_result *out) {
+    const rb_options &o = ctx->opt;
+    const int G = grid_for_variant(ctx, RB_SWEEP_DF32);
+    const long long ldH = (long long)align_up((size_t)N, 64);
+    const int chunk = 2048;
+    const int nchunk = (int)((N + chunk - 1) / chunk);
+    const int gN = (int)((N + rbk::kThreads - 1) / rbk::kThreads);
+    const int kcap = kmax > 0 ? kmax : 1;
+    const int nch = (int)((M - Mr + cols - 1) / cols);
+    const int Gs = rbk::stream_sweep_grid(ctx->device);
+    const int nwarps = Gs * (rbk::kThreads / 32);
+
+    Layout L;
+    size_t o_hi = L.add((size_t)Mr * ldH * sizeof(float2)), o_lo = L.add((size_t)Mr * ldH * sizeof(float2));
+    size_t o_norm = L.add((size_t)M * 8), o_acc = L.add((size_t)M * 8), o_pick = L.add((size_t)M);
+    size_t o_qh = L.add((size_t)kcap * ldH * sizeof(float2)), o_ql = L.add((size_t)kcap * ldH * sizeof(float2));
+    size_t o_v = L.add((size_t)N * sizeof(double2));
+    size_t o_hp = L.add((size_t)kcap * nchunk * sizeof(double2));
+    size_t np = (size_t)std::max(std::max(G, gN), Gs);
+    size_t o_np = L.add(np * 8), o_be = L.add(np * 8), o_bi = L.add(np * 8);
+    size_t o_st = L.add(sizeof(rbk::DevState));
+    size_t o_pass = L.add((size_t)kcap * sizeof(int));
+    const bool ws_C = !out->C && o.recompute_period > 0;
+    size_t o_C = ws_C ? L.add((size_t)kcap * M * sizeof(double2)) : 0;
+    size_t o_last = L.add((size_t)nch * 4), o_bound = L.add((size_t)nch * 8), o_nmax = L.add((size_t)nch * 8);
+    size_t o_list = L.add((size_t)nch * 4), o_cnt = L.add(16), o_upd = L.add(8);
+    size_t o_stage = nch ? L.add((size_t)nwarps * 2 * ldH * sizeof(float2)) : 0;
+    rb_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.off);
+    if (s != RB_OK) return s;
+    char *w = (char *)ctx->ws;
+
+    rbk::Prob p{};
+    p.N = N;
+    p.M = M;
+    p.ldS = ldS;
+    p.ldH = ldH;
+    p.ldQ = out->ldQ;
+    p.ldC = ws_C ? M : out->ldC;
+    p.minNM = N < M ? N : M;
+    p.kmax = kmax;
+    p.max_passes = o.imgs_max_passes;
+    p.nchunk = nchunk;
+    p.chunk = chunk;
+    p.tol = tol;
+    p.kappa2 = o.imgs_kappa * o.imgs_kappa;
+    p.S = Sd;  // the IMGS steps read the pivot column from host memory
+    p.hi = (const float2 *)(w + o_hi);
+    p.lo = (const float2 *)(w + o_lo);
+    p.Q = (double2 *)out->Q;
+    p.pivots = out->pivots;
+    p.err_curve = out->err_curve;
+    p.C = ws_C ? (double2 *)(w + o_C) : (double2 *)out->C;
+    p.rdiag = out->rdiag;
+    p.norm2 = (double *)(w + o_norm);
+    p.acc = (double *)(w + o_acc);
+    p.picked = (unsigned char *)(w + o_pick);
+    p.qh = (float2 *)(w + o_qh);
+    p.ql = (float2 *)(w + o_ql);
+    p.qs_stride = ldH;  // one FP32 slot per basis vector: lazy chunks apply old vectors
+    p.v = (double2 *)(w + o_v);
+    p.hpart = (double2 *)(w + o_hp);
+    p.npart = (double *)(w + o_np);
+    p.bpart_err = (double *)(w + o_be);
+    p.bpart_idx = (long long *)(w + o_bi);
+    p.st = (rbk::DevState *)(w + o_st);
+    p.passes_out = (int *)(w + o_pass);
+
+    rbk::StreamPart sp{};
+    sp.Sd = Sd;
+    sp.Mr = Mr;
+    sp.cols = cols;
+    sp.nch = nch;
+    sp.period = o.recompute_period;
+    sp.gamma = 0.5;
+    sp.last = (int *)(w + o_last);
+    sp.bound = (double *)(w + o_bound);
+    sp.nmax = (double *)(w + o_nmax);
+    sp.list = (int *)(w + o_list);
+    sp.cnt = (int *)(w + o_cnt);
+    sp.updates = (unsigned long long *)(w + o_upd);
+    sp.stage = nch ? (float2 *)(w + o_stage) : nullptr;
+    sp.stage_ld = ldH;
+
+    cudaStream_t sm = ctx->stream;
+    const bool timing = (o.flags & RB_FLAG_TIMING) != 0;
+    if (timing) {
+        while ((int)ctx->sweep_ev.size() < 2 * kcap) {
+            cudaEvent_t ev;
+            RB_CK(cudaEventCreate(&ev), "cudaEventCreate");
+            ctx->sweep_ev.push_back(ev);
+        }
+        while ((int)ctx->imgs_ev.size() < 2 * kcap) {
+            cudaEvent_t ev;
+            RB_CK(cudaEventCreate(&ev), "cudaEventCreate");
+            ctx->imgs_ev.push_back(ev);
+        }
+    }
+    ctx->trace_passes.clear();
+    ctx->trace_sweep_ms.clear();
+    ctx->trace_imgs_ms.clear();
+    int nlaunch = 0;
+    cudaEvent_t ev_init = timing ? ctx->sweep_ev[0] : nullptr;
+    RB_CK(cudaEventRecord(ctx->ev0, sm), "cudaEventRecord");
+    RB_CK(cudaMemsetAsync(p.st, 0, sizeof(rbk::DevState), sm), "memset state");
+    RB_CK(cudaMemsetAsync(sp.updates, 0, 8, sm), "memset counters");
+    // one read of S from host memory: the resident split and every norm
+    if (Mr > 0) RB_CK(rbk::launch_split(Sd, N, Mr, ldS, (float2 *)p.hi, (float2 *)p.lo, ldH, p.norm2, sm), "split");
+    if (M > Mr)
+        RB_CK(rbk::launch_split(Sd + Mr * ldS, N, M - Mr, ldS, nullptr, nullptr, ldH, p.norm2 + Mr, sm), "norms");
+    RB_CK(rbk::launch_init(p, G, sm), "init");
+    RB_CK(rbk::launch_stream_init(p, sp, sm), "stream init");
+    nlaunch += 2 + (Mr > 0) + (M > Mr);
+    float ms_init = 0.f;
+    if (timing) {
+        RB_CK(cudaEventRecord(ev_init, sm), "cudaEventRecord");
+        RB_CK(cudaEventSynchronize(ev_init), "cudaEventSynchronize");
+        cudaEventElapsedTime(&ms_init, ctx->ev0, ev_init);
+    }
+    rbk::Prob pres = p;  // the recompute of the resident columns
+    pres.M = Mr;
+    const int per_iter = 1 + 4 * (nch > 0) + 1;
+
+    int it = 0;
+    bool stopped = false;
+    while (!stopped) {
+        for (int t = 0; t < o.iters_per_sync && it < kcap; t++, it++) {
+            if (timing) RB_CK(cudaEventRecord(ctx->imgs_ev[2 * it], sm), "cudaEventRecord");
+            RB_CK(rbk::launch_imgs(p, G, false, sm, &nlaunch), "imgs");
+            if (timing) RB_CK(cudaEventRecord(ctx->imgs_ev[2 * it + 1], sm), "cudaEventRecord");
+            if (o.recompute_period > 0 && Mr > 0) {
+                RB_CK(rbk::launch_recompute(pres, o.recompute_period, G, sm), "recompute");
+                nlaunch += 1;
+            }
+            if (timing) RB_CK(cudaEventRecord(ctx->sweep_ev[2 * it], sm), "cudaEventRecord");
+            RB_CK(rbk::launch_stream_iteration(p, sp, G, Gs, sm), "streamed sweep");
+            if (timing) RB_CK(cudaEventRecord(ctx->sweep_ev[2 * it + 1], sm), "cudaEventRecord");
+            nlaunch += per_iter;
+        }
+        RB_CK(cudaMemcpyAsync(ctx->st_host, p.st, sizeof(rbk::DevState), cudaMemcpyDeviceToHost, sm), "state copy");
+        RB_CK(cudaStreamSynchronize(sm), "stream sync");
+        stopped = ctx->st_host->stop != 0;
+        if (!stopped && it >= kcap) return fail(ctx, RB_ESTATE, "greedy loop did not stop after kmax iterations");
+    }
+    RB_CK(rbk::launch_stream_flush(p, sp, Gs, sm), "flush");
+    nlaunch += nch > 0 ? 2 : 0;
+    if (out->final_err) {
+        RB_CK(rbk::launch_final_err(p, out->final_err, sm), "final_err");
+        nlaunch += 1;
+    }
+    RB_CK(cudaEventRecord(ctx->ev1, sm), "cudaEventRecord");
+    RB_CK(cudaEventSynchronize(ctx->ev1), "cudaEventSynchronize");
+    unsigned long long updates = 0;
+    RB_CK(cudaMemcpy(&updates, sp.updates, 8, cudaMemcpyDeviceToHost), "counter copy");
+    const rbk::DevState &hs = *ctx->st_host;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    out->k = hs.k;
+    out->status = hs.status;
+    out->imgs_passes = hs.total_passes;
+    out->switch_iter = -1;
+    out->n_launches = nlaunch;
+    out->n_sweeps = hs.n_sweeps;
+    out->ms_total = ms;
+    out->ms_sweep = 0.0;
+    if (timing) {
+        for (int i = 0; i < hs.n_sweeps && i < it; i++) {
+            float t = 0.f, ti = 0.f;
+            cudaEventElapsedTime(&t, ctx->sweep_ev[2 * i], ctx->sweep_ev[2 * i + 1]);
+            cudaEventElapsedTime(&ti, ctx->imgs_ev[2 * i], ctx->imgs_ev[2 * i + 1]);
+            out->ms_sweep += t;
+            ctx->trace_sweep_ms.push_back(t);
+            ctx->trace_imgs_ms.push_back(ti);
+        }
+    }
+    if (hs.k > 0) {
+        ctx->trace_passes.resize((size_t)hs.k);
+        RB_CK(cudaMemcpy(ctx->trace_passes.data(), p.passes_out, (size_t)hs.k * sizeof(int), cudaMemcpyDeviceToHost),
+              "passes copy");
+    }
+    // device bytes of the resident sweeps (hi + lo, q, bookkeeping)
+    out->sweep_bytes = (double)hs.n_sweeps * (16.0 * N * Mr + 16.0 * N + 41.0 * Mr);
+    ctx->str_stats[0] = Mr;
+    ctx->str_stats[1] = nch;
+    ctx->str_stats[2] = cols;
+    ctx->str_stats[3] = (long long)updates;
+    // host bytes: the initial pass over all of S, one column per IMGS step, and
+    // the non-resident columns of every chunk update
+    double host = 16.0 * (double)N * (double)M + 16.0 * (double)N * hs.k;
+    if (nch > 0) host += 16.0 * (double)N * (double)(M - Mr) / nch * (double)updates;
+    ctx->str_host_bytes = host;
+    ctx->str_ms_init = ms_init;
+    if (hs.status < 0) {
+        const char *why = hs.status == RB_ENONFINITE ? "NaN or Inf in S"
+                          : hs.status == RB_EORTHO   ? "IMGS did not pass the kappa test within imgs_max_passes"
+                                                     : "device error";
+        return fail(ctx, (rb_status)hs.status, "rb_greedy_streamed: %s", why);
+    }
+    return (rb_status)hs.status;
+}
+
+rb_status rb_greedy_streamed(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, double tol,
+                             int kmax, long long resident, long long chunk_cols, rb_result *out) {
+    rb_status s = check_greedy_args(ctx, S, N, M, ldS, tol, kmax, out);
+    if (s != RB_OK) return s;
+    if (!aligned(S, 16) || !aligned(out->Q, 16) || (out->C && !aligned(out->C, 16)))
+        return fail(ctx, RB_EINVAL, "complex128 arrays must be 16-byte aligned");
+    if (ctx->opt.sweep != RB_SWEEP_DF32)
+        return fail(ctx, RB_EINVAL, "rb_greedy_streamed: needs the double-float sweep (RB_SWEEP_DF32)");
+    if (chunk_cols < 0 || chunk_cols > (1LL << 20))
+        return fail(ctx, RB_EINVAL, "rb_greedy_streamed: chunk_cols must be in [0, 2^20]");
+    if (chunk_cols == 0) chunk_cols = 64;
+    if ((M + chunk_cols - 1) / chunk_cols > (1LL << 30))
+        return fail(ctx, RB_EINVAL, "rb_greedy_streamed: too many chunks");
+    RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const long long ldH = (long long)align_up((size_t)N, 64);
+    long long Mr = resident;
+    if (Mr < 0) {
+        // as many resident columns as the free device memory holds after the
+        // per-column state, C, the basis slots and 4 GB of headroom
+        size_t fr = 0, tot = 0;
+        RB_CK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+        const int kcap = kmax > 0 ? kmax : 1;
+        double other = 17.0 * M + (out->C ? 0.0 : 16.0 * kcap * M) + 16.0 * kcap * ldH + 4e9 + (double)ctx->ws_cap;
+        double room = (double)fr + (double)ctx->ws_cap - other;
+        Mr = room > 0 ? (long long)(room / (16.0 * ldH)) : 0;
+    }
+    if (Mr > M) Mr = M;
+    const size_t bytes = ((size_t)(M - 1) * (size_t)ldS + (size_t)N) * 16;
+    const double2 *Sd = nullptr;
+    bool reg = false;
+    s = host_view(ctx, S, bytes, &Sd, &reg);
+    if (s != RB_OK) return s;
+    s = greedy_streamed_device(ctx, Sd, N, M, ldS, tol, kmax, Mr, chunk_cols, out);
+    if (reg) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaHostUnregister(const_cast<void *>(S));
+    }
+    return s;
+}
+
+rb_status rb_streamed_stats(const rb_ctx *ctx, long long *counts, double *host_bytes, double *ms_init) {
+    if (!ctx) return RB_EINVAL;
+    if (counts)
+        for (int i = 0; i < 4; i++) counts[i] = ctx->str_stats[i];
+    if (host_bytes) *host_bytes = ctx->str_host_bytes;
+    if (ms_init) *ms_init = ctx->str_ms_init;
+    return RB_OK;
+}
+
 rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long N, long long M, long long ld,
                           double tol, int kmax, rb_result *out) {
     rb_status s = check_greedy_args(ctx, hi, N, M, ld, tol, kmax, out);
@@ -1053,9 +1342,20 @@ rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, l
     rb_status s = check_greedy_args(ctx, S, N, M, ldS, tol, kmax, out);
     if (s != RB_OK) return s;
     RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    // pinned S under the double-float sweep: the kernels read it in place over
+    // the host link (rb_greedy_streamed; no device copy of S, identical
+    // results); otherwise one copy of S to the device
+    bool in_place = false;
+    if (ctx->opt.sweep == RB_SWEEP_DF32 && aligned(S, 16)) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, S) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer)
+            in_place = true;
+        cudaGetLastError();
+    }
     const int kcap = kmax > 0 ? kmax : 1;
     Layout L;
-    size_t o_S = L.add((size_t)M * N * 16), o_Q = L.add((size_t)kcap * N * 16), o_p = L.add((size_t)kcap * 8);
+    size_t o_S = in_place ? 0 : L.add((size_t)M * N * 16);
+    size_t o_Q = L.add((size_t)kcap * N * 16), o_p = L.add((size_t)kcap * 8);
     size_t o_e = L.add((size_t)(kcap + 1) * 8);
     size_t o_C = out->C ? L.add((size_t)kcap * M * 16) : 0;
     size_t o_f = out->final_err ? L.add((size_t)M * 8) : 0;
@@ -1064,14 +1364,16 @@ rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, l
     if (s != RB_OK) return s;
     char *w = (char *)ctx->stage;
     cudaStream_t sm = ctx->stream;
-    // a contiguous S goes in one linear copy (the 2D copy engine path is about
-    // 2.5x slower for a 34 GB transfer from pinned memory)
-    if (ldS == N)
-        RB_CK(cudaMemcpyAsync(w + o_S, S, (size_t)M * N * 16, cudaMemcpyHostToDevice, sm), "copy S to device");
-    else
-        RB_CK(cudaMemcpy2DAsync(w + o_S, (size_t)N * 16, S, (size_t)ldS * 16, (size_t)N * 16, (size_t)M,
-                                cudaMemcpyHostToDevice, sm),
-              "copy S to device");
+    if (!in_place) {
+        // a contiguous S goes in one linear copy (the 2D copy engine path is
+        // about 2.5x slower for a 34 GB transfer from pinned memory)
+        if (ldS == N)
+            RB_CK(cudaMemcpyAsync(w + o_S, S, (size_t)M * N * 16, cudaMemcpyHostToDevice, sm), "copy S to device");
+        else
+            RB_CK(cudaMemcpy2DAsync(w + o_S, (size_t)N * 16, S, (size_t)ldS * 16, (size_t)N * 16, (size_t)M,
+                                    cudaMemcpyHostToDevice, sm),
+                  "copy S to device");
+    }
     rb_result d = *out;
     d.Q = w + o_Q;
     d.ldQ = N;
@@ -1081,7 +1383,8 @@ rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, l
     d.ldC = M;
     d.final_err = out->final_err ? (double *)(w + o_f) : nullptr;
     d.rdiag = out->rdiag ? (double *)(w + o_r) : nullptr;
-    rb_status st = greedy_device(ctx, w + o_S, N, M, N, tol, kmax, &d);
+    rb_status st = in_place ? rb_greedy_streamed(ctx, S, N, M, ldS, tol, kmax, -1, 0, &d)
+                            : greedy_device(ctx, w + o_S, N, M, N, tol, kmax, &d);
     if (st < 0) return st;
     const int k = d.k;
     if (k > 0) {

@@ -81,8 +81,10 @@ __global__ void __launch_bounds__(kThreads) k_split(const double2 *__restrict__ 
                     lr = __double2float_rn(x[u].x - (double)hr);
                     lm = __double2float_rn(x[u].y - (double)hm);
                 }
-                h[i + 32 * u] = make_float2(hr, hm);
-                l[i + 32 * u] = make_float2(lr, lm);
+                if (hi) {  // null: norms only (columns that stay in host memory)
+                    h[i + 32 * u] = make_float2(hr, hm);
+                    l[i + 32 * u] = make_float2(lr, lm);
+                }
                 df_sq(nh, nl, hr, lr);
                 df_sq(nh, nl, hm, lm);
             }

@@ -42,6 +42,10 @@ struct DevState {
     unsigned int ticket_imgs;
     unsigned int ticket_init;
     unsigned int ticket_aux;
+    unsigned int ticket_host;   // streamed form: last-block counter of the chunk sweeps
+    int pad1;
+    double hbest_err;           // streamed form: best (err, idx) of the current sweep so far
+    long long hbest_idx;
 };
 
 // Problem description passed by value to every kernel of a greedy call.
@@ -94,6 +98,25 @@ struct Prob {
     double *dacc;      // D_j = sum_l (|c_lj|^2 - |c~_lj|^2) over the rows re-checked so far
     int *dcnt;         // rows covered by D_j
     int *passes_out;   // IMGS passes of iteration k at [k] (may be null)
+};
+
+// Streamed part of a problem: chunk bookkeeping and the per-warp staging of
+// one column's hi/lo split (reused by the second and later pending vectors).
+struct StreamPart {
+    const double2 *Sd;    // device-visible pointer to S (host memory)
+    long long Mr;         // resident columns 0..Mr-1
+    long long cols;       // columns per chunk
+    int nch;              // chunks over columns Mr..M-1
+    int period;           // recompute period (0: none)
+    double gamma;         // round-A threshold factor
+    int *last;            // [nch] first basis vector not yet applied
+    double *bound;        // [nch] largest unpicked error when last updated (-inf: none)
+    double *nmax;         // [nch] largest ||s_j||^2 of the chunk
+    int *list;            // [nch] chunks selected for the current launch
+    int *cnt;             // [0] = length of list
+    unsigned long long *updates;  // chunk updates so far
+    float2 *stage;        // per warp: hi then lo, stage_ld each
+    long long stage_ld;
 };
 
 // One problem of a batch (rb_greedy_batched): what the persistent sweep and
@@ -354,6 +377,69 @@ __device__ __forceinline__ void split_rn(double x, float &h, float &l) {
     }
 }
 
+// hi/lo split of one complex128 element, exactly as the split kernel stores
+// it: the integer fast path for both parts, else the conversions for both.
+__device__ __forceinline__ void split_c(double2 x, float2 &h, float2 &l) {
+    float hr, lr, hm, lm;
+    bool ok = split_rn_fast(x.x, hr, lr);
+    ok = split_rn_fast(x.y, hm, lm) && ok;
+    if (!ok) {
+        hr = __double2float_rn(x.x);
+        hm = __double2float_rn(x.y);
+        lr = __double2float_rn(x.x - (double)hr);
+        lm = __double2float_rn(x.y - (double)hm);
+    }
+    h = make_float2(hr, hm);
+    l = make_float2(lr, lm);
+}
+
+// Eq. (Residual) running update acc_j += |c_kj|^2 (one expression, shared by
+// every sweep of the FP64 form so that all of them round it alike).
+__device__ __forceinline__ double acc_add(double a, double2 c) { return a + (c.x * c.x + c.y * c.y); }
+
+// acc_j = sum_{l<k} |C[l, j]|^2 from the stored coefficients, with
+// error-free squares (FMA) and a compensated (TwoSum) running sum: the
+// periodic exact recompute of the Eq. (Residual) bookkeeping.
+__device__ __forceinline__ double acc_recompute(const double2 *C, long long ldC, long long j, int k) {
+    double s = 0.0, e = 0.0;
+    for (int l = 0; l < k; l++) {
+        const double2 c = C[(long long)l * ldC + j];
+        const double x = c.x * c.x, ex = fma(c.x, c.x, -x);
+        const double y = c.y * c.y, ey = fma(c.y, c.y, -y);
+        double t = s + x, b = t - s;
+        e += ((s - (t - b)) + (x - b)) + ex;
+        s = t;
+        t = s + y;
+        b = t - s;
+        e += ((s - (t - b)) + (y - b)) + ey;
+        s = t;
+    }
+    return s + e;
+}
+
+// End of a sweep of the FP64 form: append err_curve[k+1], publish the next
+// pivot (bi, be) and apply the stopping rule (Alg. 3 while-test on the
+// squared error, Cor. 5.4).  One thread.
+__device__ __forceinline__ void sweep_publish(const Prob &p, DevState *st, int k, double be, long long bi) {
+    const int k1 = k + 1;
+    st->k = k1;
+    st->n_sweeps += 1;
+    const double emax = bi == kNoIdx ? 0.0 : be;
+    p.err_curve[k1] = emax;
+    st->J = bi;
+    st->errJ = emax;
+    if (bi == kNoIdx || emax < p.tol) {
+        st->status = RB_OK;
+        st->stop = 1;
+    } else if (k1 >= p.kmax) {
+        st->status = RB_KMAX_REACHED;
+        st->stop = 1;
+    } else if (k1 >= p.minNM) {
+        st->status = RB_OK;
+        st->stop = 1;
+    }
+}
+
 }  // namespace rbk
 
 // ------------------------------------------------------------- host launchers
@@ -370,6 +456,10 @@ cudaError_t launch_resume(const Prob &p, int k0, int grid, cudaStream_t s);
 cudaError_t launch_sweep(const Prob &p, int variant, int grid, cudaStream_t s);
 cudaError_t launch_recompute(const Prob &p, int period, int grid, cudaStream_t s);
 cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s, int *nlaunch);
+int stream_sweep_grid(int device);
+cudaError_t launch_stream_init(const Prob &p, const StreamPart &sp, cudaStream_t s);
+cudaError_t launch_stream_iteration(const Prob &p, const StreamPart &sp, int res_grid, int str_grid, cudaStream_t s);
+cudaError_t launch_stream_flush(const Prob &p, const StreamPart &sp, int str_grid, cudaStream_t s);
 cudaError_t launch_imgs_batched(const Prob *pp_dev, int nprob, long long maxN, int max_passes, int grid,
                                 cudaStream_t s, int *nlaunch);
 cudaError_t launch_final_err(const Prob &p, double *final_err, cudaStream_t s);

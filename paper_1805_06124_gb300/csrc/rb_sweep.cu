@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(Prob p) {
             c = col_dot_fp64(p.S + j * p.ldS, qk, p.N, lane);
         if (lane == 0) {
             if (p.C) p.C[(long long)k * p.ldC + j] = c;
-            double a = p.acc[j] + (c.x * c.x + c.y * c.y);
+            double a = acc_add(p.acc[j], c);
             p.acc[j] = a;
             double e = p.norm2[j] - a;
             if (!p.picked[j] && better(e, j, be, bi)) { be = e; bi = j; }
@@ -85,24 +85,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(Prob p) {
     block_best(be, bi);
     if (threadIdx.x == 0) {
         st->ticket_sweep = 0;
-        int k1 = k + 1;
-        st->k = k1;
-        st->n_sweeps += 1;
-        double emax = bi == kNoIdx ? 0.0 : be;
-        p.err_curve[k1] = emax;
-        st->J = bi;
-        st->errJ = emax;
-        // Stopping rule (Alg. 3 while-test on the squared error, Cor. 5.4).
-        if (bi == kNoIdx || emax < p.tol) {
-            st->status = RB_OK;
-            st->stop = 1;
-        } else if (k1 >= p.kmax) {
-            st->status = RB_KMAX_REACHED;
-            st->stop = 1;
-        } else if (k1 >= p.minNM) {
-            st->status = RB_OK;
-            st->stop = 1;
-        }
+        sweep_publish(p, st, k, be, bi);
     }
 }
 
@@ -129,22 +112,8 @@ __global__ void __launch_bounds__(kThreads) k_recompute(Prob p, int period) {
     const int k = st->k;
     if (k == 0 || k % period != 0) return;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < p.M;
-         j += (long long)gridDim.x * blockDim.x) {
-        double s = 0.0, e = 0.0;
-        for (int l = 0; l < k; l++) {
-            const double2 c = p.C[(long long)l * p.ldC + j];
-            const double x = c.x * c.x, ex = fma(c.x, c.x, -x);
-            const double y = c.y * c.y, ey = fma(c.y, c.y, -y);
-            double t = s + x, b = t - s;
-            e += ((s - (t - b)) + (x - b)) + ex;
-            s = t;
-            t = s + y;
-            b = t - s;
-            e += ((s - (t - b)) + (y - b)) + ey;
-            s = t;
-        }
-        p.acc[j] = s + e;
-    }
+         j += (long long)gridDim.x * blockDim.x)
+        p.acc[j] = acc_recompute(p.C, p.ldC, j, k);
 }
 
 cudaError_t launch_recompute(const Prob &p, int period, int grid, cudaStream_t s) {

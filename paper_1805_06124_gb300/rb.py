@@ -82,6 +82,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.rb_split.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_void_p, c_void_p, c_ll]
     lib.rb_greedy.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int, ctypes.POINTER(Result)]
     lib.rb_greedy_host.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int, ctypes.POINTER(Result)]
+    lib.rb_greedy_streamed.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int, c_ll, c_ll,
+                                       ctypes.POINTER(Result)]
+    lib.rb_streamed_stats.argtypes = [c_void_p, ctypes.POINTER(c_ll), ctypes.POINTER(c_double),
+                                      ctypes.POINTER(c_double)]
     lib.rb_greedy_split.argtypes = [c_void_p, c_void_p, c_void_p, c_ll, c_ll, c_ll, c_double, c_int,
                                     ctypes.POINTER(Result)]
     lib.rb_project.argtypes = [c_void_p, c_void_p, c_ll, c_int, c_ll, c_void_p, c_ll, c_ll, c_void_p, c_ll]
@@ -326,6 +330,34 @@ class RB:
         if want_final_err:
             bufs["final_err"] = torch.empty((M,), dtype=torch.float64, pin_memory=pin)
         return bufs
+
+    def greedy_streamed(self, S, tol: float, kmax: int, resident: int = -1, chunk_cols: int = 0,
+                        want_C: bool = True, want_final_err: bool = True):
+        """RB-greedy on snapshots S (M, N) complex128 that stay in HOST memory
+        (a CPU tensor; pinned memory is used in place, pageable memory is
+        mapped for the call).  Columns 0..resident-1 keep a split copy on the
+        device (-1: as many as fit); the rest are read in chunks of
+        ``chunk_cols`` (0: 64).  Outputs are device tensors, bit-identical to
+        ``greedy``'s."""
+        torch = _torch()
+        if (not isinstance(S, torch.Tensor) or S.dim() != 2 or S.dtype != torch.complex128 or S.is_cuda
+                or S.stride(1) != 1):
+            raise TypeError("S must be a 2-D complex128 CPU tensor with unit column stride")
+        M, N = S.shape
+        dev = torch.device("cuda", self.device)
+        with torch.cuda.stream(self.stream):
+            r, bufs = self._alloc_result(N, M, kmax, dev, want_C, want_final_err)
+        st = self._check(self.lib.rb_greedy_streamed(self._h, S.data_ptr(), N, M, _ld(S), float(tol), int(kmax),
+                                                     int(resident), int(chunk_cols), ctypes.byref(r)))
+        return self._pack(st, r, bufs)
+
+    def streamed_stats(self) -> dict:
+        """Counters of the last greedy_streamed call."""
+        cnt = (c_ll * 4)()
+        hb, mi = c_double(), c_double()
+        self._check(self.lib.rb_streamed_stats(self._h, cnt, ctypes.byref(hb), ctypes.byref(mi)))
+        return dict(resident=cnt[0], chunks=cnt[1], chunk_cols=cnt[2], chunk_reads=cnt[3],
+                    host_bytes=hb.value, ms_init=mi.value)
 
     def greedy_host(self, S, tol: float, kmax: int, want_C: bool = True, want_final_err: bool = True, out=None):
         """Same as greedy, with S and all outputs in host memory (CPU tensors;

@@ -73,3 +73,5 @@ def test_bad_options_rejected_before_any_device_call(lib):
     assert L.rb_greedy_resume(None, None, 1, 1, 1, 0.0, 1, 0, 0, None) == rb.EINVAL
     assert L.rb_trace(None, None, None, None, 0, None) == rb.EINVAL
     assert L.rb_validate(None, None, 1, 1, 1, None, None, None, 1, 1, None, None) == rb.EINVAL
+    assert L.rb_greedy_streamed(None, None, 1, 1, 1, 0.0, 1, -1, 0, None) == rb.EINVAL
+    assert L.rb_streamed_stats(None, None, None, None) == rb.EINVAL
