@@ -485,8 +485,8 @@ def run_streamed_once(args):
     torch.cuda.empty_cache()
     runs = {}
     with Clocks(0) as clk:
-        for label, res, cols in (("all_resident", M, 64), ("half_resident", M // 2, 64),
-                                 ("quarter_resident", M // 4, 64), ("quarter_resident_cols32", M // 4, 32)):
+        for label, res, cols in (("all_resident", M, 0), ("half_resident", M // 2, 1),
+                                 ("half_resident_cols64", M // 2, 64), ("quarter_resident", M // 4, 1)):
             c.greedy_streamed(Sh, 1e-12, 800, resident=res, chunk_cols=cols)   # warm-up (workspace)
             g = c.greedy_streamed(Sh, 1e-12, 800, resident=res, chunk_cols=cols)
             st = c.streamed_stats()

@@ -306,7 +306,7 @@ rb_status rb_greedy_host(rb_ctx *ctx, const void *S, long long N, long long M, l
  *   resident: columns 0..resident-1 keep a hi/lo split copy (16 ldH bytes per
  *      column, ldH = N rounded up to 64) on the device; < 0 = as many as the
  *      free device memory holds (after 4 GB of headroom).  The other columns
- *      are read from host memory in chunks of chunk_cols (0 = 64) columns.
+ *      are read from host memory in chunks of chunk_cols (0 = 1) columns.
  *   out: as for rb_greedy (DEVICE arrays).
  * A chunk is read only when its errors, as of its last read plus a bound on
  * their rounding drift, may reach the best error of the iteration; it then

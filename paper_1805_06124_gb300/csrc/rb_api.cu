@@ -1270,7 +1270,7 @@ rb_status rb_greedy_streamed(rb_ctx *ctx, const void *S, long long N, long long 
         return fail(ctx, RB_EINVAL, "rb_greedy_streamed: needs the double-float sweep (RB_SWEEP_DF32)");
     if (chunk_cols < 0 || chunk_cols > (1LL << 20))
         return fail(ctx, RB_EINVAL, "rb_greedy_streamed: chunk_cols must be in [0, 2^20]");
-    if (chunk_cols == 0) chunk_cols = 64;
+    if (chunk_cols == 0) chunk_cols = 1;
     if ((M + chunk_cols - 1) / chunk_cols > (1LL << 30))
         return fail(ctx, RB_EINVAL, "rb_greedy_streamed: too many chunks");
     RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");

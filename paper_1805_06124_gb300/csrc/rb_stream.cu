@@ -4,7 +4,8 @@
 // The paper's largest runs hold S of about half a terabyte (Sec. 1, Sec. 6),
 // more than one GPU's HBM.  Here the hi/lo split copy of the leading
 // `resident` columns lives on the device and every other column is read from
-// host memory (mapped, over the host link) in chunks of `cols` columns.
+// host memory (mapped, over the host link) in chunks of `cols` columns (one
+// column by default: the finest bounds, the fewest reads).
 //
 // Lazy chunk updates.  A chunk keeps `last` (the first basis vector it has
 // not seen) and `bound` (the largest error of its unpicked columns when it
@@ -198,22 +199,23 @@ __device__ __forceinline__ double2 dot_from_stage(const float2 *hs, const float2
     return make_double2((double)rh + (double)rl, (double)ih + (double)il);
 }
 
-// Brings the listed chunks up to date: for each column, every pending basis
-// vector l = last..kend in order (recompute first where l is a positive
-// multiple of the period, as the in-core loop does before its sweep l).  In
-// rounds A and B the best (err, idx) is merged into the state; a flush only
-// completes C and acc.
+// Brings the listed chunks up to date, one warp per chunk: for each column,
+// every pending basis vector l = last..kend in order (recompute first where l
+// is a positive multiple of the period, as the in-core loop does before its
+// sweep l).  In rounds A and B the best (err, idx) is merged into the state;
+// a flush only completes C and acc.
 __global__ void __launch_bounds__(kThreads) k_str_sweep(Prob p, StreamPart sp, int mode) {
     DevState *st = p.st;
     if (mode != ST_FLUSH && ld_volatile(&st->stop)) return;
     const int kend = mode == ST_FLUSH ? st->k - 1 : st->k;
     const int n = sp.cnt[0];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    float2 *hs = sp.stage + (long long)(blockIdx.x * nwarp + warp) * 2 * sp.stage_ld;
+    const int gwarp = blockIdx.x * nwarp + warp, twarps = gridDim.x * nwarp;
+    float2 *hs = sp.stage + (long long)gwarp * 2 * sp.stage_ld;
     float2 *ls = hs + sp.stage_ld;
-    double tbe = -INFINITY;
+    double tbe = -INFINITY;  // lane 0: best over this warp's chunks
     long long tbi = kNoIdx;
-    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+    for (int e = gwarp; e < n; e += twarps) {
         const int c = sp.list[e];
         const int l0 = sp.last[c];
         const long long j0 = sp.Mr + (long long)c * sp.cols;
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_str_sweep(Prob p, StreamPart sp, i
         if (j1 > p.M) j1 = p.M;
         double be = -INFINITY;
         long long bi = kNoIdx;
-        for (long long j = j0 + warp; j < j1; j += nwarp) {
+        for (long long j = j0; j < j1; j++) {
             double a = lane == 0 ? p.acc[j] : 0.0;
             for (int l = l0; l <= kend; l++) {
                 if (lane == 0 && l > 0 && sp.period > 0 && l % sp.period == 0) a = acc_recompute(p.C, p.ldC, j, l);
@@ -240,8 +242,7 @@ __global__ void __launch_bounds__(kThreads) k_str_sweep(Prob p, StreamPart sp, i
                 if (!p.picked[j] && better(err, j, be, bi)) { be = err; bi = j; }
             }
         }
-        block_best(be, bi);
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             sp.bound[c] = bi == kNoIdx ? -INFINITY : be;
             sp.last[c] = kend + 1;
             atomicAdd(sp.updates, 1ull);
@@ -249,6 +250,11 @@ __global__ void __launch_bounds__(kThreads) k_str_sweep(Prob p, StreamPart sp, i
         }
     }
     if (mode == ST_FLUSH) return;
+    if (lane != 0) {
+        tbe = -INFINITY;
+        tbi = kNoIdx;
+    }
+    block_best(tbe, tbi);
     if (threadIdx.x == 0) {
         p.bpart_err[blockIdx.x] = tbe;
         p.bpart_idx[blockIdx.x] = tbi;

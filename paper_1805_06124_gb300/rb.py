@@ -337,7 +337,7 @@ class RB:
         (a CPU tensor; pinned memory is used in place, pageable memory is
         mapped for the call).  Columns 0..resident-1 keep a split copy on the
         device (-1: as many as fit); the rest are read in chunks of
-        ``chunk_cols`` (0: 64).  Outputs are device tensors, bit-identical to
+        ``chunk_cols`` (0: 1).  Outputs are device tensors, bit-identical to
         ``greedy``'s."""
         torch = _torch()
         if (not isinstance(S, torch.Tensor) or S.dim() != 2 or S.dtype != torch.complex128 or S.is_cuda

@@ -54,7 +54,7 @@ def in_core(ctx, S, tol, kmax):
     return npy(ctx.greedy(torch.from_numpy(np.ascontiguousarray(S)).cuda(), tol, kmax))
 
 
-@pytest.mark.parametrize("resident,cols", [(0, 64), (1000, 64), (1000, 37), (2999, 64), (3000, 64), (-1, 0)])
+@pytest.mark.parametrize("resident,cols", [(0, 64), (1000, 64), (1000, 37), (1000, 1), (2999, 64), (3000, 64), (-1, 0)])
 def test_identical_to_in_core(ctx, resident, cols):
     """1024 x 3000 chirps (seed 4, tol 1e-10): every output bit-identical to
     rb_greedy for resident parts from none to all; 3000 - 1000 = 2000
@@ -68,7 +68,7 @@ def test_identical_to_in_core(ctx, resident, cols):
     if resident < 0:
         assert st["resident"] == 3000 and st["chunks"] == 0
     else:
-        assert st["resident"] == resident and st["chunk_cols"] == cols
+        assert st["resident"] == resident and st["chunk_cols"] == (cols or 1)
         assert st["chunks"] == -(-(3000 - resident) // cols)
         # every chunk is read at least once (iteration 0) and at most once per
         # iteration plus the flush
@@ -81,12 +81,14 @@ def test_lazy_reads_skip_chunks(ctx):
     iterations, with the same result."""
     S = synth.chirps(1024, 8192, seed=6)
     ref = in_core(ctx, S, 1e-10, 300)
-    g = npy(ctx.greedy_streamed(host(S), 1e-10, 300, resident=4096, chunk_cols=32))
-    assert_identical(g, ref)
-    st = ctx.streamed_stats()
-    frac = st["chunk_reads"] / (st["chunks"] * g["k"])
-    print("chunk read fraction", frac, st)
-    assert frac < 0.8
+    fr = {}
+    for cols in (32, 1):
+        g = npy(ctx.greedy_streamed(host(S), 1e-10, 300, resident=4096, chunk_cols=cols))
+        assert_identical(g, ref)
+        st = ctx.streamed_stats()
+        fr[cols] = st["chunk_reads"] / (st["chunks"] * g["k"])
+        print("chunk read fraction", cols, fr[cols], st)
+    assert fr[32] < 0.8 and fr[1] < fr[32]
 
 
 def test_oracle_parity_and_odd_n(ctx, orc):
