@@ -1059,6 +1059,8 @@ static rb_status host_view(rb_ctx *ctx, const void *S, size_t bytes, const doubl
     return RB_OK;
 }
 
+// Sd: S in host memory (device-visible pointer); columns Mr.. are read lazily
+// over the host link.
 static rb_status greedy_streamed_device(rb_ctx *ctx, const double2 *Sd, long long N, long long M, long long ldS,
                                        double tol, int kmax, long long Mr, long long cols, rb_result *out) {
     const rb_options &o = ctx->opt;
@@ -1085,7 +1087,7 @@ static rb_status greedy_streamed_device(rb_ctx *ctx, const double2 *Sd, long lon
     const bool ws_C = !out->C && o.recompute_period > 0;
     size_t o_C = ws_C ? L.add((size_t)kcap * M * sizeof(double2)) : 0;
     size_t o_last = L.add((size_t)nch * 4), o_bound = L.add((size_t)nch * 8), o_nmax = L.add((size_t)nch * 8);
-    size_t o_list = L.add((size_t)nch * 4), o_cnt = L.add(16), o_upd = L.add(8);
+    size_t o_list = L.add((size_t)nch * 4), o_cnt = L.add(16), o_upd = L.add(8), o_part = L.add(1024 * 8);
     size_t o_stage = nch ? L.add((size_t)nwarps * 2 * ldH * sizeof(float2)) : 0;
     rb_status s = ensure(ctx, &ctx->ws, &ctx->ws_cap, L.off);
     if (s != RB_OK) return s;
@@ -1129,11 +1131,12 @@ static rb_status greedy_streamed_device(rb_ctx *ctx, const double2 *Sd, long lon
 
     rbk::StreamPart sp{};
     sp.Sd = Sd;
+    sp.part = (double *)(w + o_part);
     sp.Mr = Mr;
     sp.cols = cols;
     sp.nch = nch;
     sp.period = o.recompute_period;
-    sp.gamma = 0.5;
+    sp.gamma = 0.99;
     sp.last = (int *)(w + o_last);
     sp.bound = (double *)(w + o_bound);
     sp.nmax = (double *)(w + o_nmax);
@@ -1180,7 +1183,7 @@ static rb_status greedy_streamed_device(rb_ctx *ctx, const double2 *Sd, long lon
     }
     rbk::Prob pres = p;  // the recompute of the resident columns
     pres.M = Mr;
-    const int per_iter = 1 + 4 * (nch > 0) + 1;
+    const int per_iter = 1 + 5 * (nch > 0) + 1;
 
     int it = 0;
     bool stopped = false;

@@ -46,6 +46,9 @@ struct DevState {
     int pad1;
     double hbest_err;           // streamed form: best (err, idx) of the current sweep so far
     long long hbest_idx;
+    double sel_max;             // streamed form: largest stale bound of the iteration
+    unsigned int ticket_sel;
+    int pad2;
 };
 
 // Problem description passed by value to every kernel of a greedy call.
@@ -112,8 +115,9 @@ struct StreamPart {
     int *last;            // [nch] first basis vector not yet applied
     double *bound;        // [nch] largest unpicked error when last updated (-inf: none)
     double *nmax;         // [nch] largest ||s_j||^2 of the chunk
+    double *part;         // [grid] per-block maxima of the selection
     int *list;            // [nch] chunks selected for the current launch
-    int *cnt;             // [0] = length of list
+    int *cnt;             // list lengths: [0] round A, [1] round B, [2] flush
     unsigned long long *updates;  // chunk updates so far
     float2 *stage;        // per warp: hi then lo, stage_ld each
     long long stage_ld;

@@ -31,13 +31,13 @@
 namespace rbk {
 
 enum { ST_ROUND_A = 0, ST_ROUND_B = 1, ST_FLUSH = 2 };
-constexpr int kSelThreads = 1024;
 
 __device__ __forceinline__ double stream_margin(int k, double nmax) { return (double)(k + 16) * 0x1p-51 * nmax; }
 
 // Resident sweep: the in-core DF32 sweep over columns 0..Mr-1, ending with
 // the best (err, idx) in the state instead of a published pivot.
-__global__ void __launch_bounds__(kThreads) k_str_resident(Prob p, long long Mr) {
+__global__ void __launch_bounds__(kThreads) k_str_resident(Prob p, StreamPart sp) {
+    const long long Mr = sp.Mr;
     DevState *st = p.st;
     if (ld_volatile(&st->stop)) return;
     const int k = st->k;
@@ -75,46 +75,58 @@ __global__ void __launch_bounds__(kThreads) k_str_resident(Prob p, long long Mr)
         st->ticket_host = 0;
         st->hbest_err = be;
         st->hbest_idx = bi;
+        if (sp.cnt) {
+            sp.cnt[0] = 0;
+            sp.cnt[1] = 0;
+        }
     }
 }
 
-// Chunk selection (one block).  Round A: stale chunks with bound + margin >=
+// Largest stale bound (plus margin) over the chunks not yet brought up to
+// this iteration (grid; the last block stores it in the state).
+__global__ void __launch_bounds__(kThreads) k_str_maxub(Prob p, StreamPart sp) {
+    DevState *st = p.st;
+    if (ld_volatile(&st->stop)) return;
+    const int k = st->k;
+    double mx = -INFINITY;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < sp.nch; c += gridDim.x * blockDim.x)
+        if (sp.last[c] <= k && sp.bound[c] > -INFINITY) mx = fmax(mx, sp.bound[c] + stream_margin(k, sp.nmax[c]));
+    long long dummy = 0;
+    block_best(mx, dummy);
+    if (threadIdx.x == 0) sp.part[blockIdx.x] = mx;
+    if (!last_block(&st->ticket_sel)) return;
+    mx = -INFINITY;
+    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) mx = fmax(mx, __ldcg(sp.part + b));
+    block_best(mx, dummy);
+    if (threadIdx.x == 0) {
+        st->ticket_sel = 0;
+        st->sel_max = mx;
+    }
+}
+
+// Chunk selection (grid).  Round A: stale chunks with bound + margin >=
 // max(R, gamma * largest such value); round B: stale chunks with bound +
 // margin >= the best error so far; flush: every chunk that has not seen all
-// basis vectors.
-__global__ void __launch_bounds__(kSelThreads) k_str_select(Prob p, StreamPart sp, int mode) {
+// basis vectors.  List order does not matter: every chunk's result and the
+// (err, idx) order are independent of it.
+__global__ void __launch_bounds__(kThreads) k_str_select(Prob p, StreamPart sp, int mode) {
     DevState *st = p.st;
-    __shared__ int n;
-    __shared__ double red[kSelThreads / 32];
-    if (threadIdx.x == 0) n = 0;
-    const bool stopped = ld_volatile(&st->stop) != 0;
     const int k = st->k;
-    __syncthreads();
+    const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
     if (mode == ST_FLUSH) {
-        for (int c = threadIdx.x; c < sp.nch; c += blockDim.x)
-            if (sp.last[c] < k) sp.list[atomicAdd(&n, 1)] = c;
-    } else if (!stopped) {
-        const double best = st->hbest_idx == kNoIdx ? -INFINITY : st->hbest_err;
-        double th = best;
-        if (mode == ST_ROUND_A) {
-            double mx = -INFINITY;
-            for (int c = threadIdx.x; c < sp.nch; c += blockDim.x)
-                if (sp.last[c] <= k && sp.bound[c] > -INFINITY)
-                    mx = fmax(mx, sp.bound[c] + stream_margin(k, sp.nmax[c]));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-            __syncthreads();
-            mx = -INFINITY;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) mx = fmax(mx, red[w]);
-            if (mx > 0.0) th = fmax(th, sp.gamma * mx);
-        }
-        for (int c = threadIdx.x; c < sp.nch; c += blockDim.x)
-            if (sp.last[c] <= k && sp.bound[c] > -INFINITY && sp.bound[c] + stream_margin(k, sp.nmax[c]) >= th)
-                sp.list[atomicAdd(&n, 1)] = c;
+        for (int c = g0; c < sp.nch; c += gs)
+            if (sp.last[c] < k) sp.list[atomicAdd(sp.cnt + 2, 1)] = c;
+        return;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) sp.cnt[0] = n;
+    if (ld_volatile(&st->stop)) return;
+    double th = st->hbest_idx == kNoIdx ? -INFINITY : st->hbest_err;
+    if (mode == ST_ROUND_A) {
+        const double mx = st->sel_max;
+        if (mx > 0.0) th = fmax(th, sp.gamma * mx);
+    }
+    for (int c = g0; c < sp.nch; c += gs)
+        if (sp.last[c] <= k && sp.bound[c] > -INFINITY && sp.bound[c] + stream_margin(k, sp.nmax[c]) >= th)
+            sp.list[atomicAdd(sp.cnt + mode, 1)] = c;
 }
 
 // c = q^H s_j from the complex128 column in host memory, split on the fly
@@ -204,11 +216,11 @@ __device__ __forceinline__ double2 dot_from_stage(const float2 *hs, const float2
 // is a positive multiple of the period, as the in-core loop does before its
 // sweep l).  In rounds A and B the best (err, idx) is merged into the state;
 // a flush only completes C and acc.
-__global__ void __launch_bounds__(kThreads) k_str_sweep(Prob p, StreamPart sp, int mode) {
+__global__ void __launch_bounds__(kThreads, 2) k_str_sweep(Prob p, StreamPart sp, int mode) {
     DevState *st = p.st;
     if (mode != ST_FLUSH && ld_volatile(&st->stop)) return;
     const int kend = mode == ST_FLUSH ? st->k - 1 : st->k;
-    const int n = sp.cnt[0];
+    const int n = sp.cnt[mode];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int gwarp = blockIdx.x * nwarp + warp, twarps = gridDim.x * nwarp;
     float2 *hs = sp.stage + (long long)gwarp * 2 * sp.stage_ld;
@@ -226,7 +238,8 @@ __global__ void __launch_bounds__(kThreads) k_str_sweep(Prob p, StreamPart sp, i
         for (long long j = j0; j < j1; j++) {
             double a = lane == 0 ? p.acc[j] : 0.0;
             for (int l = l0; l <= kend; l++) {
-                if (lane == 0 && l > 0 && sp.period > 0 && l % sp.period == 0) a = acc_recompute(p.C, p.ldC, j, l);
+                if (lane == 0 && l > 0 && sp.period > 0 && l % sp.period == 0)
+                    a = acc_recompute(p.C, p.ldC, j, l);
                 const float2 *qh = p.qh + (long long)l * p.qs_stride, *ql = p.ql + (long long)l * p.qs_stride;
                 const double2 c2 = l == l0 ? dot_from_host(sp.Sd + j * p.ldS, qh, ql, p.N, lane,
                                                            l < kend ? hs : nullptr, ls)
@@ -293,7 +306,10 @@ __global__ void __launch_bounds__(kThreads) k_str_init(Prob p, StreamPart sp) {
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)(((long long)gridDim.x * blockDim.x) >> 5);
-    if (gw == 0 && lane == 0) p.st->phase = 1;
+    if (gw == 0 && lane == 0) {
+        p.st->phase = 1;
+        sp.cnt[0] = sp.cnt[1] = sp.cnt[2] = 0;
+    }
     for (int c = gw; c < sp.nch; c += nw) {
         const long long j0 = sp.Mr + (long long)c * sp.cols;
         long long j1 = j0 + sp.cols;
@@ -327,16 +343,24 @@ cudaError_t launch_stream_init(const Prob &p, const StreamPart &sp, cudaStream_t
     return cudaGetLastError();
 }
 
+int stream_select_grid(const StreamPart &sp) {
+    long long g = ((long long)sp.nch + kThreads - 1) / kThreads;
+    if (g > 1024) g = 1024;
+    return g < 1 ? 1 : (int)g;
+}
+
 cudaError_t launch_stream_iteration(const Prob &p, const StreamPart &sp, int res_grid, int str_grid,
                                     cudaStream_t s) {
     long long g = (sp.Mr * 32 + kThreads - 1) / kThreads;
     if (g > res_grid) g = res_grid;
     if (g < 1) g = 1;
-    k_str_resident<<<(int)g, kThreads, 0, s>>>(p, sp.Mr);
+    k_str_resident<<<(int)g, kThreads, 0, s>>>(p, sp);
     if (sp.nch > 0) {
-        k_str_select<<<1, kSelThreads, 0, s>>>(p, sp, ST_ROUND_A);
+        const int gs = stream_select_grid(sp);
+        k_str_maxub<<<gs, kThreads, 0, s>>>(p, sp);
+        k_str_select<<<gs, kThreads, 0, s>>>(p, sp, ST_ROUND_A);
         k_str_sweep<<<str_grid, kThreads, 0, s>>>(p, sp, ST_ROUND_A);
-        k_str_select<<<1, kSelThreads, 0, s>>>(p, sp, ST_ROUND_B);
+        k_str_select<<<gs, kThreads, 0, s>>>(p, sp, ST_ROUND_B);
         k_str_sweep<<<str_grid, kThreads, 0, s>>>(p, sp, ST_ROUND_B);
     }
     k_str_publish<<<1, 32, 0, s>>>(p);
@@ -345,7 +369,7 @@ cudaError_t launch_stream_iteration(const Prob &p, const StreamPart &sp, int res
 
 cudaError_t launch_stream_flush(const Prob &p, const StreamPart &sp, int str_grid, cudaStream_t s) {
     if (sp.nch == 0) return cudaSuccess;
-    k_str_select<<<1, kSelThreads, 0, s>>>(p, sp, ST_FLUSH);
+    k_str_select<<<stream_select_grid(sp), kThreads, 0, s>>>(p, sp, ST_FLUSH);
     k_str_sweep<<<str_grid, kThreads, 0, s>>>(p, sp, ST_FLUSH);
     return cudaGetLastError();
 }
