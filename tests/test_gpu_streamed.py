@@ -138,6 +138,16 @@ def test_rejects_device_memory(ctx, rbm):
     r.err_curve = ctypes.cast(ec.data_ptr(), ctypes.POINTER(ctypes.c_double))
     st = ctx.lib.rb_greedy_streamed(ctx._h, S.data_ptr(), 32, 16, 32, 0.0, 4, -1, 0, ctypes.byref(r))
     assert st == rbm.EINVAL
+    # bad chunk widths and the plain-FP64 sweep option are refused
+    Sh = host(synth.chirps(64, 40, seed=2))
+    with pytest.raises(rbm.RBError) as e:
+        ctx.greedy_streamed(Sh, 0.0, 4, chunk_cols=-1)
+    assert e.value.status == rbm.EINVAL
+    c64 = rbm.RB(device=0, sweep="fp64")
+    with pytest.raises(rbm.RBError) as e:
+        c64.greedy_streamed(Sh, 0.0, 4)
+    assert e.value.status == rbm.EINVAL
+    c64.close()
     # the context stays usable
     S2 = synth.chirps(128, 300, seed=3)
     assert_identical(npy(ctx.greedy_streamed(host(S2), 1e-8, 50, resident=100)), in_core(ctx, S2, 1e-8, 50))
