@@ -104,7 +104,7 @@ def test_oracle_parity_and_odd_n(ctx, orc):
     assert_identical(g, in_core(ctx, S, 1e-10, 300))
 
 
-@pytest.mark.parametrize("case", ["low_rank", "kmax", "tiny"])
+@pytest.mark.parametrize("case", ["low_rank", "kmax", "tiny", "kmax0"])
 def test_stops(ctx, case):
     """Exact rank (IMGS finds nothing new or the error drops below tol), the
     kmax stop with skipped chunks pending (the flush completes C), and tiny
@@ -115,14 +115,28 @@ def test_stops(ctx, case):
     elif case == "kmax":
         S = synth.chirps(512, 2000, seed=2)
         tol, kmax, res, cols = 1e-12, 7, 500, 16
-    else:
+    elif case == "tiny":
         S = synth.chirps(64, 5, seed=1)
         tol, kmax, res, cols = 1e-10, 5, 1, 64
+    else:
+        S = synth.chirps(128, 300, seed=1)
+        tol, kmax, res, cols = 1e-10, 0, 100, 8
     ref = in_core(ctx, S, tol, kmax)
     g = npy(ctx.greedy_streamed(host(S), tol, kmax, resident=res, chunk_cols=cols))
     assert_identical(g, ref)
     if case == "kmax":
         assert g["status"] == 1 and g["k"] == 7
+
+
+def test_nonfinite_input(ctx, rbm):
+    """A NaN in a streamed column: the same RB_ENONFINITE as the in-core call."""
+    S = synth.chirps(128, 300, seed=1)
+    S[250, 17] = np.nan
+    for run in (lambda: ctx.greedy(torch.from_numpy(S).cuda(), 1e-10, 50),
+                lambda: ctx.greedy_streamed(host(S), 1e-10, 50, resident=100)):
+        with pytest.raises(rbm.RBError) as e:
+            run()
+        assert e.value.status == rbm.ENONFINITE
 
 
 def test_rejects_device_memory(ctx, rbm):
