@@ -611,7 +611,23 @@ def run_ours(args):
         h2d = 16 * N * M
         d2h = kh * N * 16 + kh * M * 16 + kh * 8 * 2 + (kh + 1) * 8 + M * 8
         e2e = {"value": round(byts / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": round(dt / nst * 1e3, 2)}
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(dt / nst * 1e3, 2),
+               "path": "pinned S read in place by the kernels over the host link"}
+        # the same pinned S with only half of its columns given a device copy
+        # (rb_greedy_streamed): the other half is read from host memory when
+        # its errors may hold the pivot
+        if world == 1 and not args.no_next:
+            piv_h = torch.from_numpy(outb["pivots"][:kh].numpy().copy())
+            with torch.cuda.stream(stream):
+                ctx_h.greedy_streamed(Sh, TOL, KMAX, resident=M // 2)          # warm-up (workspace)
+                gs = ctx_h.greedy_streamed(Sh, TOL, KMAX, resident=M // 2)
+            sts = ctx_h.streamed_stats()
+            e2e["half_resident"] = {
+                "ms": round(gs["ms_total"], 3), "k": gs["k"],
+                "same_pivots": bool(torch.equal(gs["pivots"].cpu(), piv_h)),
+                "host_GBps": round(sts["host_bytes"] / (gs["ms_total"] * 1e-3) / 1e9, 1),
+                "host_columns_read_per_iteration": round(sts["chunk_reads"] / max(1, sts["chunks"] * gs["k"]), 4)}
+            del gs
         ctx_h.close()
         del Sh, outb, rh
 
