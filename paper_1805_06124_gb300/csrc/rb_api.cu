@@ -231,7 +231,8 @@ rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long l
               "project");
         return RB_OK;
     }
-    // tensor-core path, in column batches whose slice planes stay under ~4 GB
+    // tensor-core path, in column batches whose workspace (the basis slice planes and the
+    // column scales) stays under ~4 GB
     long long Mb = Mx;
     while (Mb > 64 && rbk::oz_workspace(N, k, Mb) > (4ull << 30)) Mb = (Mb + 1) / 2;
     const size_t need = rbk::oz_workspace(N, k, Mb) + 256;

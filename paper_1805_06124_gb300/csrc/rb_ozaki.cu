@@ -134,7 +134,8 @@ __global__ void k_oz_slice_A(const double2 *__restrict__ Q, long long N, int k, 
     }
 }
 
-// B, pass 1: one warp per column j of this batch.  The scale comes from the
+// B: one warp per column j of this batch finds its scale; the slices
+// themselves are made inside the GEMM (k_oz_gemm).  The scale comes from the
 // largest biased exponent (integer max over the IEEE bits, no FP64 work):
 // max|x| < 2^(e_max - 1022), so E = e_max - 1021, as frexp of the maximum
 // would give.
@@ -155,71 +156,62 @@ __global__ void k_oz_exp_B(const double2 *__restrict__ X, long long N, long long
     }
 }
 
-// B, pass 2: block (column tile ct, range of OZ_SLICE_ST stages).  Thread t
-// slices complex elements 2(t & 3) and 2(t & 3) + 1 of each stage of column
-// 64 ct + (t >> 2): the four threads of a column read 128 contiguous bytes and
-// each warp writes whole 256-byte groups (8 columns x 16 K) of every plane.
-// K positions past 2N and columns Mb..Cp-1 are written as zero slices.
-constexpr int OZ_SLICE_ST = 32;
-
-__global__ void __launch_bounds__(256) k_oz_slice_B(const double2 *__restrict__ X, long long N, long long Mb,
-                                                    long long ldX, long long Kp, const int *__restrict__ Eb,
-                                                    __nv_bfloat16 *__restrict__ Bs) {
-    const long long ct = blockIdx.x, nst = Kp / OZ_KS;
-    const int jj = threadIdx.x >> 2, p0 = (threadIdx.x & 3) * 2;
-    const long long j = ct * OZ_N + jj;
-    const bool live = j < Mb;
-    const int E = live ? Eb[j] : 0;
-    const double2 *x = X + (live ? j : 0) * ldX;
-    constexpr long long pstride2 = OZ_N * OZ_KS / 2;
-    const uint32_t off0 = kmajor_off(jj, 2 * p0, OZ_KS) >> 1, off1 = kmajor_off(jj, 2 * p0 + 2, OZ_KS) >> 1;
-    const __nv_bfloat162 z2 = __floats2bfloat162_rn(0.f, 0.f);
-    const long long s0 = (long long)blockIdx.y * OZ_SLICE_ST, s1 = s0 + OZ_SLICE_ST < nst ? s0 + OZ_SLICE_ST : nst;
-    for (long long st = s0; st < s1; st++) {
-        __nv_bfloat16 *blk = Bs + (ct * nst + st) * (long long)(OZ_S * OZ_N * OZ_KS);
-        const long long i0 = st * (OZ_KS / 2) + p0;
-        double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
-        if (live && i0 < N) v0 = x[i0];
-        if (live && i0 + 1 < N) v1 = x[i0 + 1];
-        __nv_bfloat162 *o0 = (__nv_bfloat162 *)(blk + off0), *o1 = (__nv_bfloat162 *)(blk + off1);
-        if (live && i0 < N) slice7_pair(v0.x, v0.y, E, o0, pstride2);
-        else
-#pragma unroll
-            for (int sl = 0; sl < OZ_S; sl++) o0[sl * pstride2] = z2;
-        if (live && i0 + 1 < N) slice7_pair(v1.x, v1.y, E, o1, pstride2);
-        else
-#pragma unroll
-            for (int sl = 0; sl < OZ_S; sl++) o1[sl * pstride2] = z2;
-    }
-}
-
 // (hi, lo) += x, both double-float
 __device__ __forceinline__ void dfs_add(float &ah, float &al, float bh, float bl) { df_add(ah, al, bh, bl); }
 
-// Ring of OZ_NBUF stage buffers filled by bulk copies: one thread issues the
-// copies of stage st + OZ_NBUF - 1 (the A and the B block, 28 KB + 14 KB) as
-// soon as the MMAs of stage st - 1, the last user of that buffer, have
-// completed, waits for the bytes of stage st, and issues its 28 MMAs.  "full"
-// barriers count the copied bytes; "done" barriers receive the MMA commits;
-// the n-th phase of buffer b's barriers belongs to stage b + OZ_NBUF n.  At
-// the end of each exact chunk (OZ_DRAIN K values) all 256 threads drain the
+// Four FP32 columns of this thread's TMEM lane from each of the seven level
+// accumulators (level L at column offset L * OZ_N), with one wait for all
+// 28 values: the wait names every register, so no use can move above it.
+__device__ __forceinline__ void tmem_ld4_levels(uint32_t taddr, float (&v)[OZ_LV][4]) {
+    uint32_t r[OZ_LV][4];
+#pragma unroll
+    for (int L = 0; L < OZ_LV; L++)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r[L][0]), "=r"(r[L][1]), "=r"(r[L][2]), "=r"(r[L][3])
+                     : "r"(taddr + (uint32_t)(L * OZ_N)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[1][0]), "+r"(r[1][1]),
+                   "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]),
+                   "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]), "+r"(r[4][0]), "+r"(r[4][1]),
+                   "+r"(r[4][2]), "+r"(r[4][3]), "+r"(r[5][0]), "+r"(r[5][1]), "+r"(r[5][2]), "+r"(r[5][3]),
+                   "+r"(r[6][0]), "+r"(r[6][1]), "+r"(r[6][2]), "+r"(r[6][3]));
+#pragma unroll
+    for (int L = 0; L < OZ_LV; L++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) v[L][e] = __uint_as_float(r[L][e]);
+}
+
+// The GEMM with the snapshot slicing inside it.  Warps 0-7 (256 producer
+// threads) read X and write the seven B slice planes of each K stage straight
+// into the stage's shared-memory buffer (thread t: column 64 ct + t / 4,
+// complex elements 2 (t % 4) and 2 (t % 4) + 1 of the stage, X read
+// OZ_AHEAD stages ahead into registers); lane 0 of warp 8 fills the A half of
+// the buffer with one bulk copy of the pre-sliced basis (28 KB, L2-resident)
+// and issues the stage's 28 MMAs.  Barriers per buffer: "afull" counts the
+// A bytes, "bfull" the 256 producer arrivals, "done" receives the MMA
+// commit; the n-th phase of buffer b belongs to stage b + OZ_NBUF n.  At the
+// end of each exact chunk (OZ_DRAIN K values) the producer threads drain the
 // TMEM levels into double-float running sums held in registers: thread
 // (warp w, lane l) owns row 32 (w % 4) + l and columns 32 (w / 4) .. + 31.
 constexpr int OZ_NBUF = 5;
-constexpr int OZ_THREADS = 256;
+constexpr int OZ_PRODUCERS = 256;
+constexpr int OZ_THREADS = OZ_PRODUCERS + 32;
+constexpr int OZ_AHEAD = 2;  // equals the number of register sets in k_oz_gemm
+static_assert((OZ_DRAIN / OZ_KS) % OZ_AHEAD == 0, "chunks hold whole register-set rounds");
 
-__global__ void __launch_bounds__(OZ_THREADS) k_oz_gemm(const __nv_bfloat16 *__restrict__ As,
-                                                        const __nv_bfloat16 *__restrict__ Bs,
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *__restrict__ As,
+                                                        const double2 *__restrict__ X, long long N, long long ldX,
                                                         const int *__restrict__ Ea, const int *__restrict__ Eb, int k,
-                                                        long long Mb, long long Kp, long long Rp, long long Cp,
-                                                        double2 *__restrict__ C, long long ldC, long long col_off,
-                                                        int *err) {
+                                                        long long Mb, long long Kp, double2 *__restrict__ C,
+                                                        long long ldC, long long col_off, int *err) {
     extern __shared__ __align__(1024) uint8_t dsm[];
     constexpr int SA = OZ_S * OZ_M * OZ_KS * 2, SB = OZ_S * OZ_N * OZ_KS * 2;  // 28 KB, 14 KB per buffer
-    __shared__ __align__(8) uint64_t full[OZ_NBUF], done[OZ_NBUF], cdone;
+    __shared__ __align__(8) uint64_t afull[OZ_NBUF], bfull[OZ_NBUF], done[OZ_NBUF], cdone;
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = 32 * (warp & 3) + lane, cbase = 32 * (warp >> 2);
+    const bool producer = threadIdx.x < OZ_PRODUCERS;
+    const bool issuer = threadIdx.x == OZ_PRODUCERS;
+    const int row = 32 * (warp & 3) + lane, cbase = 32 * ((warp >> 2) & 1);
     const long long ct = blockIdx.x, rt = blockIdx.y;
     const long long j0 = ct * OZ_N, r0 = rt * OZ_M;
     float acc_h[32], acc_l[32];
@@ -228,7 +220,8 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gemm(const __nv_bfloat16 *__r
     if (warp == 0) tmem_alloc(&tslot, OZ_TCOLS);
     if (threadIdx.x == 0) {
         for (int b = 0; b < OZ_NBUF; b++) {
-            mbar_init(&full[b], 1);
+            mbar_init(&afull[b], 1);
+            mbar_init(&bfull[b], OZ_PRODUCERS);
             mbar_init(&done[b], 1);
         }
         mbar_init(&cdone, 1);
@@ -244,19 +237,65 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gemm(const __nv_bfloat16 *__r
     auto bufA = [&](long long st) { return dsm + (int)(st % OZ_NBUF) * (SA + SB); };
     auto bufB = [&](long long st) { return dsm + (int)(st % OZ_NBUF) * (SA + SB) + SA; };
     auto par = [&](long long st) { return (uint32_t)((st / OZ_NBUF) & 1); };
-    auto load = [&](long long st) {  // thread 0 only
-        uint64_t *fb = &full[st % OZ_NBUF];
-        mbar_expect_tx(fb, SA + SB);
-        bulk_g2s(bufA(st), As + (rt * nst + st) * (long long)(OZ_S * OZ_M * OZ_KS), SA, fb);
-        bulk_g2s(bufB(st), Bs + (ct * nst + st) * (long long)(OZ_S * OZ_N * OZ_KS), SB, fb);
+    // producer: this thread's column and the two complex elements of a stage
+    const int jj = threadIdx.x >> 2, p0 = (threadIdx.x & 3) * 2;
+    const long long j = j0 + jj;
+    const bool live = producer && j < Mb;
+    const int E = live ? Eb[j] : 0;
+    const double2 *x = X + (live ? j : 0) * ldX;
+    constexpr long long pstride2 = OZ_N * OZ_KS / 2;
+    const uint32_t off0 = kmajor_off(jj & (OZ_N - 1), 2 * p0, OZ_KS) >> 1,
+                   off1 = kmajor_off(jj & (OZ_N - 1), 2 * p0 + 2, OZ_KS) >> 1;
+    // two register sets: stage st uses set st % 2 (X read OZ_AHEAD = 2 stages ahead)
+    double2 xa0, xa1, xb0, xb1;
+    auto fetch = [&](long long st, double2 &v0, double2 &v1) {
+        const long long i0 = st * (OZ_KS / 2) + p0;
+        v0 = (live && i0 < N) ? x[i0] : make_double2(0.0, 0.0);
+        v1 = (live && i0 + 1 < N) ? x[i0 + 1] : make_double2(0.0, 0.0);
     };
-    if (threadIdx.x == 0)
-        for (long long st = 0; st < OZ_NBUF - 1 && st < nst; st++) load(st);
+    if (producer) {
+        fetch(0, xa0, xa1);
+        if (nst > 1) fetch(1, xb0, xb1);
+    }
+    auto produce = [&](long long st, double2 &v0, double2 &v1) {
+        if (st >= OZ_NBUF) ok = mbar_wait(&done[st % OZ_NBUF], par(st - OZ_NBUF)) && ok;
+        __nv_bfloat16 *blk = (__nv_bfloat16 *)bufB(st);
+        const long long i0 = st * (OZ_KS / 2) + p0;
+        __nv_bfloat162 *o0 = (__nv_bfloat162 *)(blk + off0), *o1 = (__nv_bfloat162 *)(blk + off1);
+        const __nv_bfloat162 z2 = __floats2bfloat162_rn(0.f, 0.f);
+        if (live && i0 < N) slice7_pair(v0.x, v0.y, E, o0, pstride2);
+        else
+#pragma unroll
+            for (int sl = 0; sl < OZ_S; sl++) o0[sl * pstride2] = z2;
+        if (live && i0 + 1 < N) slice7_pair(v1.x, v1.y, E, o1, pstride2);
+        else
+#pragma unroll
+            for (int sl = 0; sl < OZ_S; sl++) o1[sl * pstride2] = z2;
+        if (st + OZ_AHEAD < nst) fetch(st + OZ_AHEAD, v0, v1);
+        // this thread's stores become visible to the tensor core, then it arrives
+        fence_async_smem();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[st % OZ_NBUF])) : "memory");
+    };
+    auto load_a = [&](long long st) {  // issuer only
+        uint64_t *fb = &afull[st % OZ_NBUF];
+        mbar_expect_tx(fb, SA);
+        bulk_g2s(bufA(st), As + (rt * nst + st) * (long long)(OZ_S * OZ_M * OZ_KS), SA, fb);
+    };
+    if (issuer)
+        for (long long st = 0; st < OZ_NBUF - 1 && st < nst; st++) load_a(st);
     for (long long cs = 0; cs < nst; cs += per_drain) {
         const long long ce = cs + per_drain < nst ? cs + per_drain : nst;
-        if (threadIdx.x == 0) {
+        if (producer) {
+            // per_drain is even, so stage st always meets set st % 2
+            for (long long st = cs; st < ce; st += 2) {
+                produce(st, xa0, xa1);
+                if (st + 1 < ce) produce(st + 1, xb0, xb1);
+            }
+        } else if (issuer) {
             for (long long st = cs; st < ce; st++) {
-                ok = mbar_wait(&full[st % OZ_NBUF], par(st)) && ok;
+                const int b = (int)(st % OZ_NBUF);
+                ok = mbar_wait(&afull[b], par(st)) && ok;
+                ok = mbar_wait(&bfull[b], par(st)) && ok;
                 tc_fence_after();
                 // one descriptor per operand and stage; slices and K steps are
                 // constant offsets of its 16-byte address field
@@ -274,40 +313,42 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gemm(const __nv_bfloat16 *__r
                             const uint64_t ad = ad0 + (uint64_t)((sa * (OZ_M * OZ_KS * 2) + kk * 256) >> 4);
                             const uint64_t bd = bd0 + (uint64_t)((sb * (OZ_N * OZ_KS * 2) + kk * 256) >> 4);
                             // level L is first reached at sa = 0 (sb = L <= 6)
-                            const uint32_t a = (sa == 0 && kk == 0) ? acc0 : 1u;
-                            tc_mma_bf16(tmem + (uint32_t)(L * OZ_N), ad, bd, idesc, a);
+                            const uint32_t ac = (sa == 0 && kk == 0) ? acc0 : 1u;
+                            tc_mma_bf16(tmem + (uint32_t)(L * OZ_N), ad, bd, idesc, ac);
                         }
                     }
-                tc_commit(&done[st % OZ_NBUF]);
+                tc_commit(&done[b]);
+                // A of stage st + OZ_NBUF - 1 into the buffer of stage st - 1
                 if (st + OZ_NBUF - 1 < nst) {
                     if (st >= 1) ok = mbar_wait(&done[(st - 1) % OZ_NBUF], par(st - 1)) && ok;
-                    load(st + OZ_NBUF - 1);
+                    load_a(st + OZ_NBUF - 1);
                 }
             }
             tc_commit(&cdone);
         }
-        // drain: every thread waits for the chunk's MMAs (cdone completes once
-        // per chunk; the other threads run at most one chunk behind thread 0,
-        // so the parity of the chunk index is unambiguous), then reads its
-        // TMEM lane; levels combined smallest first, in double-float
-        ok = mbar_wait(&cdone, (uint32_t)((cs / per_drain) & 1)) && ok;
-        tc_fence_after();
-        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        // drain (producer threads): wait for the chunk's MMAs (cdone completes
+        // once per chunk and no thread runs more than one chunk behind), then
+        // read this thread's TMEM lane; levels combined smallest first, in
+        // double-float
+        if (producer) {
+            ok = mbar_wait(&cdone, (uint32_t)((cs / per_drain) & 1)) && ok;
+            tc_fence_after();
+            const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            float v[OZ_LV][16];
+            for (int h = 0; h < 8; h++) {
+                float v[OZ_LV][4];
+                tmem_ld4_levels(tmem + lane_off + (uint32_t)(cbase + 4 * h), v);
 #pragma unroll
-            for (int L = 0; L < OZ_LV; L++) tmem_ld16(tmem + lane_off + (uint32_t)(L * OZ_N + cbase + 16 * h), v[L]);
+                for (int e = 0; e < 4; e++) {
+                    float th = 0.f, tl = 0.f;
 #pragma unroll
-            for (int e = 0; e < 16; e++) {
-                float th = 0.f, tl = 0.f;
-#pragma unroll
-                for (int L = OZ_LV - 1; L >= 0; L--) {
-                    // level L+2 carries 2^(-7 (L+2)): an exact power-of-two factor
-                    float x = v[L][e] * __int_as_float((127 - OZ_BITS * (L + 2)) << 23);
-                    dfs_add(th, tl, x, 0.f);
+                    for (int L = OZ_LV - 1; L >= 0; L--) {
+                        // level L+2 carries 2^(-7 (L+2)): an exact power-of-two factor
+                        float xl = v[L][e] * __int_as_float((127 - OZ_BITS * (L + 2)) << 23);
+                        dfs_add(th, tl, xl, 0.f);
+                    }
+                    dfs_add(acc_h[4 * h + e], acc_l[4 * h + e], th, tl);
                 }
-                dfs_add(acc_h[16 * h + e], acc_l[16 * h + e], th, tl);
             }
         }
         tc_fence_before();
@@ -317,14 +358,14 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gemm(const __nv_bfloat16 *__r
     if (!ok && err) atomicExch(err, 1);
     // write: row of the tile -> basis vector (r0 + row) / 2, Re or Im part
     const long long R = r0 + row;
-    if (R < 2LL * k) {
+    if (producer && R < 2LL * k) {
         const int l = (int)(R >> 1);
         const int Ex = Ea[l];
         double *crow = (double *)(C + (long long)l * ldC) + (R & 1);
 #pragma unroll
         for (int c = 0; c < 32; c++) {
-            const long long j = j0 + cbase + c;
-            if (j < Mb) crow[2 * (col_off + j)] = ldexp((double)acc_h[c] + (double)acc_l[c], Ex + Eb[j]);
+            const long long jc = j0 + cbase + c;
+            if (jc < Mb) crow[2 * (col_off + jc)] = ldexp((double)acc_h[c] + (double)acc_l[c], Ex + Eb[jc]);
         }
     }
     tc_fence_before();
@@ -356,8 +397,7 @@ cudaError_t launch_wait_selftest(long long polls, int arrive, int *flag, cudaStr
 size_t oz_workspace(long long N, int k, long long Mb) {
     long long Kp = (2 * N + OZ_KS - 1) / OZ_KS * OZ_KS;
     long long Rp = (2LL * k + OZ_M - 1) / OZ_M * OZ_M;
-    long long Cp = (Mb + OZ_N - 1) / OZ_N * OZ_N;
-    return (size_t)OZ_S * (Rp + Cp) * Kp * 2 + (size_t)(k + Cp) * 4 + 4096;
+    return (size_t)OZ_S * Rp * Kp * 2 + (size_t)(k + Mb) * 4 + 4096;
 }
 
 // C[:, col_off : col_off + Mb] for one batch of Mb columns; ws from oz_workspace.
@@ -369,19 +409,14 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
     const long long Rp = (2LL * k + OZ_M - 1) / OZ_M * OZ_M;
     const long long Cp = (Mb + OZ_N - 1) / OZ_N * OZ_N;
     __nv_bfloat16 *As = (__nv_bfloat16 *)ws;
-    __nv_bfloat16 *Bs = As + (size_t)OZ_S * Rp * Kp;
-    int *Ea = (int *)(Bs + (size_t)OZ_S * Cp * Kp);
+    int *Ea = (int *)(As + (size_t)OZ_S * Rp * Kp);
     int *Eb = Ea + k;
-    // zero fill of the A planes (small: rows 2k..Rp-1 and the K padding);
-    // k_oz_slice_B writes every B entry, K padding and padded columns included
+    // zero fill of the A planes (small: rows 2k..Rp-1 and the K padding)
     cudaError_t e = cudaMemsetAsync(As, 0, (size_t)OZ_S * Rp * Kp * 2, s);
     if (e != cudaSuccess) return e;
     k_oz_slice_A<<<k, 256, 0, s>>>(Q, N, k, ldQ, Kp, Rp, As, Ea);
     const long long ge = (Mb * 32 + 255) / 256;
     k_oz_exp_B<<<(unsigned)(ge < 4096 ? ge : 4096), 256, 0, s>>>(X, N, Mb, ldX, Eb);
-    const long long nst = Kp / OZ_KS;
-    k_oz_slice_B<<<dim3((unsigned)(Cp / OZ_N), (unsigned)((nst + OZ_SLICE_ST - 1) / OZ_SLICE_ST)), 256, 0, s>>>(
-        X, N, Mb, ldX, Kp, Eb, Bs);
     const size_t dsm = (size_t)OZ_NBUF * OZ_S * (OZ_M + OZ_N) * OZ_KS * 2;  // 210 KB ring
     static bool attr = false;
     if (!attr) {
@@ -389,7 +424,7 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
         attr = true;
     }
     dim3 grid((unsigned)(Cp / OZ_N), (unsigned)(Rp / OZ_M));
-    k_oz_gemm<<<grid, OZ_THREADS, dsm, s>>>(As, Bs, Ea, Eb, k, Mb, Kp, Rp, Cp, C, ldC, col_off, err);
+    k_oz_gemm<<<grid, OZ_THREADS, dsm, s>>>(As, X, N, ldX, Ea, Eb, k, Mb, Kp, C, ldC, col_off, err);
     return cudaGetLastError();
 }
 

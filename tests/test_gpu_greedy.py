@@ -233,10 +233,9 @@ def test_project_tc_row_tiles(orc, rbm, k):
 
 
 def test_project_tc_column_batches(orc, rbm):
-    """N = 8192 and 20,000 columns: the slice planes would exceed the 4 GB
-    batch limit, so the columns go in two batches of 10,000 (the batch width is
-    halved until it fits); checked against the oracle on columns at both ends,
-    around the batch boundary and inside the second batch."""
+    """N = 8192 and 20,000 columns: 313 column tiles, more than two waves of
+    the GPU's SMs, each slicing its columns inside the GEMM; checked against
+    the oracle on columns at both ends, in the middle and in the last wave."""
     c = rbm.RB(device=0)
     N, M = 8192, 20000
     rng = np.random.default_rng(11)
