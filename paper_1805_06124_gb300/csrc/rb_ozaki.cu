@@ -64,43 +64,45 @@ __device__ __forceinline__ long long oz_fixed(double v, int E) {
     return X;
 }
 
-// Slices of a (re, im) pair stored as BF16x2 into each of the 7 planes.
-__device__ __forceinline__ void slice7_pair(double re, double im, int E, __nv_bfloat162 *out, long long stride2) {
-    long long X = oz_fixed(re, E), Y = oz_fixed(im, E);
-#pragma unroll
-    for (int s = 0; s < OZ_S; s++) {
-        const int sh = 49 - OZ_BITS * (s + 1);
-        long long a = (sh > 0) ? ((X + (1LL << (sh - 1))) >> sh) : X;
-        long long c = (sh > 0) ? ((Y + (1LL << (sh - 1))) >> sh) : Y;
-        X -= a << sh;
-        Y -= c << sh;
-        // |a|, |c| <= 64: exact through a 32-bit conversion
-        out[s * stride2] = __floats2bfloat162_rn(__int2float_rn((int)a), __int2float_rn((int)c));
-    }
+// Balanced base-128 digits of a fixed-point value X (|X| < 2^48):
+// alpha_s = round(X_s / 2^(49-7s)) (halves up), X_{s+1} = X_s - alpha_s 2^(49-7s),
+// s = 1..7, computed in 32-bit pieces.  The digits with 2^(49-7s) >= 2^28
+// depend only on the bits of X from 2^27 up, so they come from hi = X / 2^21
+// (rounded down); the 2^21 digit adds the rounding bit of lo = X mod 2^21,
+// and the remainder below it fits in 22 bits.  |alpha_s| <= 64.
+__device__ __forceinline__ void digits7(long long X, int (&a)[OZ_S]) {
+    int hi = (int)(X >> 21);
+    const int lo = (int)(X & 0x1FFFFF);
+    int d;
+    d = (hi + (1 << 20)) >> 21;
+    hi -= d * (1 << 21);
+    a[0] = d;
+    d = (hi + (1 << 13)) >> 14;
+    hi -= d * (1 << 14);
+    a[1] = d;
+    d = (hi + (1 << 6)) >> 7;
+    hi -= d * (1 << 7);
+    a[2] = d;
+    d = hi + ((lo + (1 << 20)) >> 21);
+    int r = lo - (d - hi) * (1 << 21);
+    a[3] = d;
+    d = (r + (1 << 13)) >> 14;
+    r -= d * (1 << 14);
+    a[4] = d;
+    d = (r + (1 << 6)) >> 7;
+    r -= d * (1 << 7);
+    a[5] = d;
+    a[6] = r;
 }
 
-// value -> 7 balanced slices of 7 bits.  Integer arithmetic on the IEEE
-// bits (the FP64 pipe of this GPU is slow): X = round(v 2^(49-E)), an integer
-// below 2^48 in magnitude since |v| < 2^(E-1); then balanced base-128 digits
-// from the top, alpha_s = round(X / 2^(49-7s)), X -= alpha_s 2^(49-7s).
-__device__ __forceinline__ void slice7(double v, int E, __nv_bfloat16 *out, long long stride) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const int e = (int)((b >> 52) & 0x7FF);
-    long long X = 0;
-    if (e != 0) {  // zero and subnormal inputs give zero slices
-        const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
-        const int sh = e - 1026 - E;  // v = m 2^(e-1075) -> X = m 2^(e-1075+49-E)
-        if (sh >= 0) X = m << sh;
-        else if (sh > -64) X = (m + (1LL << (-sh - 1))) >> (-sh);  // round half up
-        if (b >> 63) X = -X;
-    }
+// Slices of a (re, im) pair stored as BF16x2 into each of the 7 planes.
+__device__ __forceinline__ void slice7_pair(double re, double im, int E, __nv_bfloat162 *out, long long stride2) {
+    int a[OZ_S], c[OZ_S];
+    digits7(oz_fixed(re, E), a);
+    digits7(oz_fixed(im, E), c);
 #pragma unroll
-    for (int s = 0; s < OZ_S; s++) {
-        const int sh = 49 - OZ_BITS * (s + 1);
-        long long a = (sh > 0) ? ((X + (1LL << (sh - 1))) >> sh) : X;
-        X -= a << sh;
-        out[s * stride] = __float2bfloat16_rn((float)a);
-    }
+    for (int s = 0; s < OZ_S; s++)  // |a|, |c| <= 64: exact in BF16
+        out[s * stride2] = __floats2bfloat162_rn(__int2float_rn(a[s]), __int2float_rn(c[s]));
 }
 
 // A: one block per basis vector l; E_l from max |a_i|, |b_i|; slices of both rows.
