@@ -27,16 +27,17 @@ constexpr int OZ_BITS = 7;       // bits per slice
 constexpr int OZ_LV = OZ_S;      // levels 2..8 -> 7 accumulators
 constexpr int OZ_M = 128;        // A rows per tile
 constexpr int OZ_N = 64;         // B rows (columns of C) per tile
-constexpr int OZ_KS = 16;        // K per shared-memory stage (double-buffered)
+constexpr int OZ_KS = 16;        // K per shared-memory stage (a ring of OZ_NBUF stage buffers)
 constexpr int OZ_DRAIN = 512;    // K per exact TMEM chunk
 constexpr int OZ_TCOLS = 512;    // TMEM columns allocated (7 levels x 64 used)
 
-// Slice planes are stored tile by tile in the K-major shared-memory layout the
-// MMAs read (8-row x 16-byte core matrices, see kmajor_off), so that the A
-// tile of one K stage (7 planes x 128 rows x OZ_KS) and the B tile of one
-// column tile (7 planes x 64 rows x OZ_KS) are each one contiguous block that
-// a single bulk copy moves:  block (tile t, stage st, plane s) starts at
-// ((t * nst + st) * OZ_S + s) * R * OZ_KS elements, R = OZ_M or OZ_N.
+// The basis slice planes are stored tile by tile in the K-major shared-memory
+// layout the MMAs read (8-row x 16-byte core matrices, see kmajor_off), so that
+// the A tile of one K stage (7 planes x 128 rows x OZ_KS) is one contiguous
+// block that a single bulk copy moves:  block (tile t, stage st, plane s)
+// starts at ((t * nst + st) * OZ_S + s) * OZ_M * OZ_KS elements.  The snapshot
+// (B) slices use the same layout for 64 rows, written by the GEMM's producer
+// warps straight into the stage buffer.
 __device__ __forceinline__ long long oz_tile_off(long long r, long long kpos, int R, long long nst) {
     const long long t = r / R, st = kpos / OZ_KS;
     const int rr = (int)(r % R), kk = (int)(kpos % OZ_KS);
