@@ -83,6 +83,17 @@ typedef struct rb_options {
                               acc_j = sum_l |C[l, j]|^2 is rebuilt from the stored coefficients with
                               compensated summation before the sweep (the periodic exact recompute of the
                               bookkeeping); 0 = off.  >= 0 (default 16) */
+    int batched_variant;   /* rb_greedy_batched sweep: -1 (default) = chosen by the autotuner; otherwise
+                              2 * v + c forces sweep variant v (0..5: complex128 read and split in
+                              registers, 6..11: pre-split hi/lo copy; unroll 2 << (v % 3), block width
+                              by v / 3 within each half) and c (0: 32, 1: 128 columns per chunk).
+                              Forcing a pre-split variant when the copy does not fit in free device memory
+                              returns RB_EINVAL.  In [-1, 23]. */
+    unsigned long long timeout_cycles; /* budget of every device-side wait of the tensor-core kernels
+                              (mbarrier waits), in SM clock cycles; a wait that runs out sets an error
+                              flag, the kernel returns and the call reports RB_ETIMEOUT.  0 (default) =
+                              2^31 cycles, about one second at 2 GHz; otherwise >= 2^20 (a shorter budget
+                              could end a wait that is only slow) */
 } rb_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -203,13 +214,6 @@ typedef struct rb_problem {
  * problems (an error if any failed, RB_KMAX_REACHED if any stopped at kmax). */
 rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, double tol, int kmax,
                             rb_result *outs);
-
-/* Self-test of the bounded device-side wait every tensor-core kernel uses:
- * one thread waits on an mbarrier that nothing arrives on (arrive = 0) for at
- * most `polls` polls, then records a time-out and the kernel returns normally.
- * Returns RB_ETIMEOUT when the wait ran out (expected for arrive = 0), RB_OK
- * when it completed (arrive = 1), RB_EINVAL for polls < 1. */
-rb_status rb_debug_wait_selftest(rb_ctx *ctx, long long polls, int arrive);
 
 /* Reconstruction (Alg. 4, Sec. 5.2.2): from a greedy basis Q_j and its
  * coefficients C = Q_j^H S (= R(1:j, 1:M) up to the column order), the SVD
@@ -386,8 +390,15 @@ rb_status rb_mlp_train(rb_mlp *mlp, const float *X, const float *T, long long ro
  *     kmax <= RB_NOALLOC_MAX_KMAX; larger sizes return RB_EINVAL with a message.
  *   - S and *out as for rb_greedy (device pointers, caller-allocated).
  *   - opt may be NULL: current device, the legacy default stream, default
- *     IMGS options.  opt->sweep and opt->flags are ignored; the timing fields
- *     of *out are left at zero.
+ *     IMGS options, no periodic recompute.  opt->sweep and opt->flags are
+ *     ignored; the timing fields of *out are left at zero.
+ *   - opt->recompute_period is honoured as in rb_greedy when out->C is given
+ *     (the recompute reads the stored coefficients); without out->C the
+ *     fixed array has no room for them and the recompute is off.  With the
+ *     same options the results equal rb_greedy's with RB_SWEEP_FP64 bit for
+ *     bit.
+ *   - The calling thread's current device is the same after the call as
+ *     before it, on every return path.
  *   - errbuf (may be NULL, errlen bytes) receives a message on failure.
  *   - The first call for a device looks up the array's device address with
  *     that device current; make it before any stream capture.

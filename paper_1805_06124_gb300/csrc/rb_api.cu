@@ -116,6 +116,9 @@ int grid_for_variant(rb_ctx *ctx, int variant) {
 namespace rbk {
 cudaStream_t ctx_stream(rb_ctx *ctx) { return ctx->stream; }
 int ctx_device(rb_ctx *ctx) { return ctx->device; }
+unsigned long long ctx_wait_cycles(const rb_ctx *ctx) {
+    return ctx->opt.timeout_cycles ? ctx->opt.timeout_cycles : kWaitCyclesDefault;
+}
 }  // namespace rbk
 
 extern "C" {
@@ -132,6 +135,8 @@ void rb_default_options(rb_options *opt) {
     opt->recompute_period = 16;
     opt->stream = nullptr;
     opt->flags = 0;
+    opt->batched_variant = -1;
+    opt->timeout_cycles = 0;
 }
 
 rb_status rb_create(const rb_options *opt, rb_ctx **out) {
@@ -143,7 +148,8 @@ rb_status rb_create(const rb_options *opt, rb_ctx **out) {
     else
         rb_default_options(&o);
     if (!(o.imgs_kappa > 1.0) || o.imgs_max_passes < 1 || o.iters_per_sync < 1 || o.recompute_period < 0 ||
-        (o.sweep != RB_SWEEP_DF32 && o.sweep != RB_SWEEP_FP64) || !(o.switch_err > 0.0))
+        (o.sweep != RB_SWEEP_DF32 && o.sweep != RB_SWEEP_FP64) || !(o.switch_err > 0.0) ||
+        o.batched_variant < -1 || o.batched_variant > 23 || (o.timeout_cycles && o.timeout_cycles < (1ull << 20)))
         return RB_EINVAL;
     rb_ctx *ctx = new (std::nothrow) rb_ctx();
     if (!ctx) return RB_ENOMEM;
@@ -244,7 +250,7 @@ rb_status rb_project(rb_ctx *ctx, const void *Q, long long N, int k, long long l
     for (long long c0 = 0; c0 < Mx; c0 += Mb) {
         long long nb = Mx - c0 < Mb ? Mx - c0 : Mb;
         RB_CK(rbk::launch_project_tc((const double2 *)Q, N, k, ldQ, (const double2 *)X + c0 * ldX, nb, ldX,
-                                     (double2 *)C, ldC, c0, ctx->gen, err, sm),
+                                     (double2 *)C, ldC, c0, ctx->gen, err, rbk::ctx_wait_cycles(ctx), sm),
               "project (tensor cores)");
     }
     int herr = 0;
@@ -631,6 +637,7 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     p.rtick = (int *)(w + o_rt);
     p.lgcap = lgcap;
     p.tc_err = (int *)(w + o_te);
+    p.wait_cycles = rbk::ctx_wait_cycles(ctx);
 
     cudaStream_t sm = ctx->stream;
     int nlaunch = 0;
@@ -750,7 +757,13 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
     size_t freeb = 0, totalb = 0;
     RB_CK(cudaMemGetInfo(&freeb, &totalb), "cudaMemGetInfo");
     const size_t have = ctx->ws_cap;
-    const bool presplit = (split_bytes + L.off + (4ull << 30)) < (size_t)(0.95 * (double)(freeb + have));
+    const bool fits = (split_bytes + L.off + (4ull << 30)) < (size_t)(0.95 * (double)(freeb + have));
+    // a forced sweep variant (rb_options.batched_variant) fixes the layout too
+    const int force = o.batched_variant;
+    if (force >= 12 && !fits)
+        return fail(ctx, RB_EINVAL, "rb_greedy_batched: forced pre-split variant %d, but the copy does not fit",
+                    force / 2);
+    const bool presplit = force >= 0 ? force >= 12 : fits;
     if (presplit)
         for (int b = 0; b < nprob; b++) {
             o_hi[b] = L.add((size_t)probs[b].M * ldHs[b] * sizeof(float2));
@@ -850,14 +863,17 @@ rb_status rb_greedy_batched(rb_ctx *ctx, int nprob, const rb_problem *probs, dou
     // ---- autotune (dry sweeps of this batch), cached per batch shape
     const int v0 = presplit ? 6 : 0;
     auto key = std::make_tuple(nprob * (presplit ? -1 : 1), sumNM, maxN);
-    if (presplit && ctx->tune.find(key) == ctx->tune.end())  // the tuning sweeps read the copy
+    if (presplit && force < 0 && ctx->tune.find(key) == ctx->tune.end())  // the tuning sweeps read the copy
         for (int b = 0; b < nprob; b++)
             RB_CK(rbk::launch_split(pp[b].S, probs[b].N, probs[b].M, probs[b].ldS, (float2 *)bp[b].hi,
                                     (float2 *)bp[b].lo, ldHs[b], pp[b].norm2, sm),
                   "split");
     int best_v = v0 + 3, best_cw = 32;
     auto it_t = ctx->tune.find(key);
-    if (it_t != ctx->tune.end()) {
+    if (force >= 0) {
+        best_v = force / 2;
+        best_cw = CWs[force % 2];
+    } else if (it_t != ctx->tune.end()) {
         best_v = it_t->second.first;
         best_cw = it_t->second.second;
     } else {
@@ -1325,19 +1341,19 @@ rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long
     return greedy_split_device(ctx, hi, lo, N, M, ld, tol, kmax, out);
 }
 
-rb_status rb_debug_wait_selftest(rb_ctx *ctx, long long polls, int arrive) {
-    if (!ctx || polls < 1) return RB_EINVAL;
+rb_status rb_debug_wait_selftest(rb_ctx *ctx, long long cycles, int arrive) {
+    if (!ctx || cycles < 1) return RB_EINVAL;
     RB_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     rb_status s = ensure(ctx, &ctx->gen, &ctx->gen_cap, 256);
     if (s != RB_OK) return s;
     int *flag = (int *)ctx->gen;
     cudaStream_t sm = ctx->stream;
     RB_CK(cudaMemsetAsync(flag, 0, sizeof(int), sm), "memset flag");
-    RB_CK(rbk::launch_wait_selftest(polls, arrive, flag, sm), "wait selftest");
+    RB_CK(rbk::launch_wait_selftest(cycles, arrive, flag, sm), "wait selftest");
     int h = 0;
     RB_CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, sm), "flag copy");
     RB_CK(cudaStreamSynchronize(sm), "stream sync");
-    if (h) return fail(ctx, RB_ETIMEOUT, "bounded wait ran out after %lld polls (self-test)", polls);
+    if (h) return fail(ctx, RB_ETIMEOUT, "bounded wait ran out after %lld cycles (self-test)", cycles);
     return RB_OK;
 }
 

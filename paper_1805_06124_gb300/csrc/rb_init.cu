@@ -49,7 +49,12 @@ __global__ void __launch_bounds__(kThreads) k_generate(const double *q, const do
 
 // Warp per column: hi = fl32(x), lo = fl32(x - hi) (round to nearest) and,
 // when norm2 != null, ||hi + lo||^2 in double-float: the sweep works on
-// hi + lo, so its norms are taken of the same numbers.
+// hi + lo, so its norms are taken of the same numbers.  Lane L handles the
+// element pairs (2t, 2t+1), t = L (mod 32) -- the partition and the steps of
+// norm2_acc4, shared with the split form's init -- reading S with two
+// 16-byte loads per pair (the second hits L1) and storing hi/lo as float4
+// when ldH is even and the arrays are 16-byte aligned.  hi == null: norms
+// only (columns that stay in host memory).
 __global__ void __launch_bounds__(kThreads) k_split(const double2 *__restrict__ S, long long N, long long M,
                                                     long long ldS, float2 *__restrict__ hi,
                                                     float2 *__restrict__ lo, long long ldH,
@@ -57,40 +62,55 @@ __global__ void __launch_bounds__(kThreads) k_split(const double2 *__restrict__ 
     int lane = threadIdx.x & 31;
     long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long n2 = N >> 1;
+    const bool vec = hi && !(ldH & 1) && !(reinterpret_cast<uintptr_t>(hi) & 15) &&
+                     !(reinterpret_cast<uintptr_t>(lo) & 15);
     for (long long j = gw; j < M; j += nw) {
         const double2 *s = S + j * ldS;
-        float2 *h = hi + j * ldH;
-        float2 *l = lo + j * ldH;
-        float nh = 0.f, nl = 0.f;
-        constexpr int U = 4;
-        long long i = lane;
-        for (; i < N; i += 32 * U) {
-            double2 x[U];
+        float2 *h = hi ? hi + j * ldH : nullptr;
+        float2 *l = hi ? lo + j * ldH : nullptr;
+        Norm2Acc a{0.f, 0.f, 0.f};
+        constexpr int U = 2;
+        for (long long t = lane; t < n2; t += 32 * U) {
+            double2 x[2 * U];
 #pragma unroll
             for (int u = 0; u < U; u++)
-                if (i + 32 * u < N) x[u] = ld_stream_d2(s + i + 32 * u);
+                if (t + 32 * u < n2) {
+                    x[2 * u] = __ldg(s + 2 * (t + 32 * u));
+                    x[2 * u + 1] = __ldg(s + 2 * (t + 32 * u) + 1);
+                }
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                if (i + 32 * u >= N) break;
-                float hr, lr, hm, lm;
-                bool ok = split_rn_fast(x[u].x, hr, lr);
-                ok = split_rn_fast(x[u].y, hm, lm) && ok;
-                if (!ok) {
-                    hr = __double2float_rn(x[u].x);
-                    hm = __double2float_rn(x[u].y);
-                    lr = __double2float_rn(x[u].x - (double)hr);
-                    lm = __double2float_rn(x[u].y - (double)hm);
+                const long long tu = t + 32 * u;
+                if (tu >= n2) break;
+                float2 h0, l0, h1, l1;
+                split_c(x[2 * u], h0, l0);
+                split_c(x[2 * u + 1], h1, l1);
+                const float4 hv = make_float4(h0.x, h0.y, h1.x, h1.y);
+                const float4 lv = make_float4(l0.x, l0.y, l1.x, l1.y);
+                if (vec) {
+                    reinterpret_cast<float4 *>(h)[tu] = hv;
+                    reinterpret_cast<float4 *>(l)[tu] = lv;
+                } else if (h) {
+                    h[2 * tu] = h0;
+                    h[2 * tu + 1] = h1;
+                    l[2 * tu] = l0;
+                    l[2 * tu + 1] = l1;
                 }
-                if (hi) {  // null: norms only (columns that stay in host memory)
-                    h[i + 32 * u] = make_float2(hr, hm);
-                    l[i + 32 * u] = make_float2(lr, lm);
-                }
-                df_sq(nh, nl, hr, lr);
-                df_sq(nh, nl, hm, lm);
+                norm2_acc4(a, hv, lv);
             }
         }
+        if ((N & 1) && lane == 0) {
+            float2 h0, l0;
+            split_c(__ldg(s + N - 1), h0, l0);
+            if (h) {
+                h[N - 1] = h0;
+                l[N - 1] = l0;
+            }
+            norm2_acc2(a, h0, l0);
+        }
         if (norm2) {
-            double nrm = warp_sum((double)nh + (double)nl);
+            const double nrm = norm2_finish(a);
             if (lane == 0) norm2[j] = nrm;
         }
     }

@@ -13,6 +13,11 @@
 
 namespace rbk {
 
+// Default budget of a device-side wait (tensor-core mbarrier waits): 2^31 SM
+// clock cycles, about one second at 2 GHz.
+constexpr unsigned long long kWaitCyclesDefault = 1ull << 31;
+
+
 constexpr int kThreads = 256;
 constexpr long long kNoIdx = 0x7fffffffffffffffLL;
 
@@ -98,6 +103,7 @@ struct Prob {
     int *bcount;       // per-block candidate counts
     int nblk_cand;     // blocks of the candidate kernels
     int *tc_err;       // set when a tensor-core wait ran out
+    unsigned long long wait_cycles;  // budget of each tensor-core wait, SM clock cycles
     double *dacc;      // D_j = sum_l (|c_lj|^2 - |c~_lj|^2) over the rows re-checked so far
     int *dcnt;         // rows covered by D_j
     int *passes_out;   // IMGS passes of iteration k at [k] (may be null)
@@ -318,6 +324,37 @@ __device__ __forceinline__ void df_sq(float &sh, float &sl, float h, float l) {
     sl = __fadd_rn(sl, __fadd_rn(t, e));
 }
 
+// ||hi + lo||^2 of one column, the part of one lane: lane L owns the complex
+// element pairs (2t, 2t+1) with t = L (mod 32), i.e. the float4 slots of
+// hi/lo that the split form's sweep reads.  (ah, al) gathers (h + l)^2 - l^2
+// per real component in double-float, in the order re(2t), im(2t), re(2t+1),
+// im(2t+1); lsq gathers l^2 in FP32 (below 2^-48 relative).  An odd last
+// element is added by lane 0 after the loop.  The FP64 form (k_split) and the
+// split form (its init) both use exactly these steps, so the two forms start
+// from bit-identical norms and resolve the first, tied, pivot alike.
+struct Norm2Acc {
+    float ah, al, lsq;
+};
+
+__device__ __forceinline__ void norm2_acc4(Norm2Acc &a, float4 h, float4 l) {
+    df_mac(a.ah, a.al, h.x, l.x, h.x, l.x);
+    df_mac(a.ah, a.al, h.y, l.y, h.y, l.y);
+    df_mac(a.ah, a.al, h.z, l.z, h.z, l.z);
+    df_mac(a.ah, a.al, h.w, l.w, h.w, l.w);
+    a.lsq = __fmaf_rn(l.x, l.x, __fmaf_rn(l.y, l.y, __fmaf_rn(l.z, l.z, __fmaf_rn(l.w, l.w, a.lsq))));
+}
+
+__device__ __forceinline__ void norm2_acc2(Norm2Acc &a, float2 h, float2 l) {
+    df_mac(a.ah, a.al, h.x, l.x, h.x, l.x);
+    df_mac(a.ah, a.al, h.y, l.y, h.y, l.y);
+    a.lsq = __fmaf_rn(l.x, l.x, __fmaf_rn(l.y, l.y, a.lsq));
+}
+
+// Whole-warp call: the column's norm, valid in every lane.
+__device__ __forceinline__ double norm2_finish(const Norm2Acc &a) {
+    return warp_sum((double)a.ah + (double)a.al + (double)a.lsq);
+}
+
 // Double-float product of a conjugated basis element (hi + lo parts) with a
 // snapshot element (hi + lo parts), accumulated into (re_h, re_l), (im_h, im_l):
 //   Re += qr*sr + qi*si,  Im += qr*si - qi*sr.
@@ -484,10 +521,10 @@ cudaError_t launch_recon_svd(const double2 *C, long long ldC, int j, long long M
 cudaError_t launch_recon_basis(const double2 *Q, long long ldQ, long long N, int j, const double2 *V, int k,
                                double2 *X, long long ldX, cudaStream_t s);
 size_t oz_workspace(long long N, int k, long long Mb);
-cudaError_t launch_wait_selftest(long long polls, int arrive, int *flag, cudaStream_t s);
+cudaError_t launch_wait_selftest(long long cycles, int arrive, int *flag, cudaStream_t s);
 cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mb,
                               long long ldX, double2 *C, long long ldC, long long col_off, void *ws, int *err,
-                              cudaStream_t s);
+                              unsigned long long wait, cudaStream_t s);
 cudaError_t launch_project(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mx,
                            long long ldX, double2 *C, long long ldC, cudaStream_t s);
 int sweep_grid(int variant, int device);
@@ -500,4 +537,5 @@ cudaError_t launch_breduce(const BProb *P, int nprob, const long long *chunk0, c
                            const long long *part_idx, cudaStream_t s);
 cudaStream_t ctx_stream(rb_ctx *ctx);
 int ctx_device(rb_ctx *ctx);
+unsigned long long ctx_wait_cycles(const rb_ctx *ctx);  // rb_options.timeout_cycles, 0 -> the default
 }  // namespace rbk

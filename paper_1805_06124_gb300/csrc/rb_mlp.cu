@@ -41,6 +41,7 @@ struct GemmArgs {
     const float *zin;    // pre-activation for EPI_GELU_BWD, (m, n) at zin[m*ldz + n]
     long long ldz;
     int *err;
+    unsigned long long wait;  // budget of each mbarrier wait, SM clock cycles
 };
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
             }
             tc_commit(&mbar);
         }
-        ok = mbar_wait(&mbar, phase) && ok;
+        ok = mbar_wait(&mbar, phase, g.wait) && ok;
         phase ^= 1;
         tc_fence_after();
         __syncthreads();
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
     if (warp == 0) tmem_dealloc(tmem, GT);
 }
 
-static cudaError_t gemm(const GemmArgs &g, cudaStream_t s) {
+static cudaError_t gemm(GemmArgs g, unsigned long long wait, cudaStream_t s) {
+    g.wait = wait;
     dim3 grid((g.M + GT - 1) / GT, (g.N + GT - 1) / GT);
     k_gemm_bf16<<<grid, 128, 0, s>>>(g);
     return cudaGetLastError();
@@ -321,6 +323,7 @@ using namespace rbk;
 
 struct rb_mlp {
     rb_ctx *ctx = nullptr;
+    unsigned long long wait = 0;  // device wait budget (rb_options.timeout_cycles)
     cudaStream_t stream = nullptr;
     int device = 0;
     int O = 0;
@@ -352,15 +355,15 @@ cudaError_t forward(rb_mlp *n, const float *X, int B, float *y, cudaStream_t s) 
     GemmArgs a{};
     a.M = B; a.N = MW; a.K = MW; a.A = n->h1; a.sam = MW; a.sak = 1; a.B = n->pb + L.w2; a.sbn = MW; a.sbk = 1;
     a.epi = EPI_BIAS_GELU; a.bias = n->p + L.b2; a.out = n->z2; a.ldo = MW; a.outb = n->h2; a.ldb = MW; a.err = n->err;
-    cudaError_t e = gemm(a, s);
+    cudaError_t e = gemm(a, n->wait, s);
     if (e != cudaSuccess) return e;
     a.A = n->h2; a.B = n->pb + L.w3; a.bias = n->p + L.b3; a.out = n->z3; a.outb = n->h3;
-    e = gemm(a, s);
+    e = gemm(a, n->wait, s);
     if (e != cudaSuccess) return e;
     GemmArgs c{};
     c.M = B; c.N = O; c.K = MW; c.A = n->h3; c.sam = MW; c.sak = 1; c.B = n->pb + L.w4; c.sbn = MW; c.sbk = 1;
     c.epi = EPI_STORE; c.bias = n->p + L.b4; c.out = y; c.ldo = O; c.outb = nullptr; c.err = n->err;
-    return gemm(c, s);
+    return gemm(c, n->wait, s);
 }
 
 // backward of the batch held in the buffers; gradients into n->g
@@ -371,26 +374,26 @@ cudaError_t backward(rb_mlp *n, const float *X, int B, cudaStream_t s) {
     GemmArgs a{};
     a.M = O; a.N = MW; a.K = B; a.A = n->dyb; a.sam = 1; a.sak = O; a.B = n->h3; a.sbn = 1; a.sbk = MW;
     a.epi = EPI_STORE; a.out = n->g + L.w4; a.ldo = MW; a.err = n->err;
-    cudaError_t e = gemm(a, s);
+    cudaError_t e = gemm(a, n->wait, s);
     if (e != cudaSuccess) return e;
     // dz3 = (dy W4) * gelu'(z3)
     GemmArgs b{};
     b.M = B; b.N = MW; b.K = O; b.A = n->dyb; b.sam = O; b.sak = 1; b.B = n->pb + L.w4; b.sbn = 1; b.sbk = MW;
     b.epi = EPI_GELU_BWD; b.out = n->dz3; b.ldo = MW; b.outb = n->dz3b; b.ldb = MW; b.zin = n->z3; b.ldz = MW;
     b.err = n->err;
-    if ((e = gemm(b, s)) != cudaSuccess) return e;
+    if ((e = gemm(b, n->wait, s)) != cudaSuccess) return e;
     // dW3 = dz3^T h2
     a.M = MW; a.K = B; a.A = n->dz3b; a.sam = 1; a.sak = MW; a.B = n->h2; a.out = n->g + L.w3;
-    if ((e = gemm(a, s)) != cudaSuccess) return e;
+    if ((e = gemm(a, n->wait, s)) != cudaSuccess) return e;
     // dz2 = (dz3 W3) * gelu'(z2)
     b.K = MW; b.A = n->dz3b; b.sam = MW; b.B = n->pb + L.w3; b.out = n->dz2; b.outb = n->dz2b; b.zin = n->z2;
-    if ((e = gemm(b, s)) != cudaSuccess) return e;
+    if ((e = gemm(b, n->wait, s)) != cudaSuccess) return e;
     // dW2 = dz2^T h1
     a.A = n->dz2b; a.B = n->h1; a.out = n->g + L.w2;
-    if ((e = gemm(a, s)) != cudaSuccess) return e;
+    if ((e = gemm(a, n->wait, s)) != cudaSuccess) return e;
     // dz1 = (dz2 W2) * gelu'(z1)
     b.A = n->dz2b; b.B = n->pb + L.w2; b.out = n->dz1; b.outb = nullptr; b.zin = n->z1;
-    if ((e = gemm(b, s)) != cudaSuccess) return e;
+    if ((e = gemm(b, n->wait, s)) != cudaSuccess) return e;
     k_l1_bwd<<<MW, 256, 0, s>>>(n->dz1, X, B, n->g, O);
     k_colsum<<<MW, 256, 0, s>>>(n->dz2, B, MW, n->g + L.b2);
     k_colsum<<<MW, 256, 0, s>>>(n->dz3, B, MW, n->g + L.b3);
@@ -408,6 +411,7 @@ rb_status rb_mlp_create(rb_ctx *ctx, int n_out, int batch_cap, unsigned long lon
     rb_mlp *n = new (std::nothrow) rb_mlp();
     if (!n) return RB_ENOMEM;
     n->ctx = ctx;
+    n->wait = rbk::ctx_wait_cycles(ctx);
     n->stream = rbk::ctx_stream(ctx);
     n->device = rbk::ctx_device(ctx);
     n->O = n_out;

@@ -104,6 +104,22 @@ extern "C" rb_status rb_greedy_noalloc(const void *S, long long N, long long M, 
         set_err(errbuf, errlen, "rb_greedy_noalloc: bad options");
         return RB_EINVAL;
     }
+    int period = opt ? opt->recompute_period : 0;
+    if (period < 0) {
+        set_err(errbuf, errlen, "rb_greedy_noalloc: bad options");
+        return RB_EINVAL;
+    }
+    if (!out->C) period = 0;  // the recompute reads the stored coefficients; without C there is no room for them
+    // the caller's current device is put back on every return path
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+        set_err(errbuf, errlen, "rb_greedy_noalloc: cannot read the current device");
+        return RB_ECUDA;
+    }
+    struct DeviceGuard {
+        int d;
+        ~DeviceGuard() { cudaSetDevice(d); }
+    } guard{prev};
     int dev = 0;
     cudaError_t e = opt ? cudaSetDevice(opt->device) : cudaSuccess;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -185,6 +201,10 @@ extern "C" rb_status rb_greedy_noalloc(const void *S, long long N, long long M, 
     for (;;) {
         for (int t = 0; t < per_sync && it < kcap; t++, it++) {
             NA_CK(rbk::launch_imgs(p, G, false, sm, &nlaunch));
+            if (period > 0) {  // the periodic exact recompute, as in rb_greedy
+                NA_CK(rbk::launch_recompute(p, period, G, sm));
+                nlaunch += 1;
+            }
             NA_CK(rbk::launch_sweep(p, 1, G, sm));
             nlaunch += 1;
         }
@@ -203,6 +223,7 @@ extern "C" rb_status rb_greedy_noalloc(const void *S, long long N, long long M, 
     NA_CK(cudaStreamSynchronize(sm));
 #undef NA_CK
     out->k = hs.k;
+    out->status = hs.status;
     out->imgs_passes = hs.total_passes;
     out->switch_iter = -1;
     out->n_launches = nlaunch;

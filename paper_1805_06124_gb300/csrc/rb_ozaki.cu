@@ -206,7 +206,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                                                         const double2 *__restrict__ X, long long N, long long ldX,
                                                         const int *__restrict__ Ea, const int *__restrict__ Eb, int k,
                                                         long long Mb, long long Kp, double2 *__restrict__ C,
-                                                        long long ldC, long long col_off, int *err) {
+                                                        long long ldC, long long col_off, int *err,
+                                                        unsigned long long wait) {
     extern __shared__ __align__(1024) uint8_t dsm[];
     constexpr int SA = OZ_S * OZ_M * OZ_KS * 2, SB = OZ_S * OZ_N * OZ_KS * 2;  // 28 KB, 14 KB per buffer
     __shared__ __align__(8) uint64_t afull[OZ_NBUF], bfull[OZ_NBUF], done[OZ_NBUF], cdone;
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         if (nst > 1) fetch(1, xb0, xb1);
     }
     auto produce = [&](long long st, double2 &v0, double2 &v1) {
-        if (st >= OZ_NBUF) ok = mbar_wait(&done[st % OZ_NBUF], par(st - OZ_NBUF)) && ok;
+        if (st >= OZ_NBUF) ok = mbar_wait(&done[st % OZ_NBUF], par(st - OZ_NBUF), wait) && ok;
         __nv_bfloat16 *blk = (__nv_bfloat16 *)bufB(st);
         const long long i0 = st * (OZ_KS / 2) + p0;
         __nv_bfloat162 *o0 = (__nv_bfloat162 *)(blk + off0), *o1 = (__nv_bfloat162 *)(blk + off1);
@@ -297,8 +298,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         } else if (issuer) {
             for (long long st = cs; st < ce; st++) {
                 const int b = (int)(st % OZ_NBUF);
-                ok = mbar_wait(&afull[b], par(st)) && ok;
-                ok = mbar_wait(&bfull[b], par(st)) && ok;
+                ok = mbar_wait(&afull[b], par(st), wait) && ok;
+                ok = mbar_wait(&bfull[b], par(st), wait) && ok;
                 tc_fence_after();
                 // one descriptor per operand and stage; slices and K steps are
                 // constant offsets of its 16-byte address field
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                 tc_commit(&done[b]);
                 // A of stage st + OZ_NBUF - 1 into the buffer of stage st - 1
                 if (st + OZ_NBUF - 1 < nst) {
-                    if (st >= 1) ok = mbar_wait(&done[(st - 1) % OZ_NBUF], par(st - 1)) && ok;
+                    if (st >= 1) ok = mbar_wait(&done[(st - 1) % OZ_NBUF], par(st - 1), wait) && ok;
                     load_a(st + OZ_NBUF - 1);
                 }
             }
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         // read this thread's TMEM lane; levels combined smallest first, in
         // double-float
         if (producer) {
-            ok = mbar_wait(&cdone, (uint32_t)((cs / per_drain) & 1)) && ok;
+            ok = mbar_wait(&cdone, (uint32_t)((cs / per_drain) & 1), wait) && ok;
             tc_fence_after();
             const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
 #pragma unroll
@@ -378,9 +379,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
 
 // Self-test of the bounded mbarrier wait used by every tensor-core kernel: one
 // thread waits on a barrier that nothing arrives on (unless `arrive`), with a
-// budget of `polls`, and records a time-out in *flag.  No tensor-core work is
+// budget of `cycles` SM clock cycles, and records a time-out in *flag.  No tensor-core work is
 // in flight, so running out of budget leaves nothing behind.
-__global__ void k_wait_selftest(long long polls, int arrive, int *flag) {
+__global__ void k_wait_selftest(long long cycles, int arrive, int *flag) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -388,12 +389,12 @@ __global__ void k_wait_selftest(long long polls, int arrive, int *flag) {
             unsigned long long st;
             asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(smem_u32(&bar)));
         }
-        if (!mbar_wait(&bar, 0, polls)) *flag = 1;
+        if (!mbar_wait(&bar, 0, (unsigned long long)cycles)) *flag = 1;
     }
 }
 
-cudaError_t launch_wait_selftest(long long polls, int arrive, int *flag, cudaStream_t s) {
-    k_wait_selftest<<<1, 32, 0, s>>>(polls, arrive, flag);
+cudaError_t launch_wait_selftest(long long cycles, int arrive, int *flag, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(cycles, arrive, flag);
     return cudaGetLastError();
 }
 
@@ -406,7 +407,7 @@ size_t oz_workspace(long long N, int k, long long Mb) {
 // C[:, col_off : col_off + Mb] for one batch of Mb columns; ws from oz_workspace.
 cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ldQ, const double2 *X, long long Mb,
                               long long ldX, double2 *C, long long ldC, long long col_off, void *ws, int *err,
-                              cudaStream_t s) {
+                              unsigned long long wait, cudaStream_t s) {
     if (k <= 0 || Mb <= 0) return cudaSuccess;
     const long long Kp = (2 * N + OZ_KS - 1) / OZ_KS * OZ_KS;
     const long long Rp = (2LL * k + OZ_M - 1) / OZ_M * OZ_M;
@@ -427,7 +428,7 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
         attr = true;
     }
     dim3 grid((unsigned)(Cp / OZ_N), (unsigned)(Rp / OZ_M));
-    k_oz_gemm<<<grid, OZ_THREADS, dsm, s>>>(As, X, N, ldX, Ea, Eb, k, Mb, Kp, C, ldC, col_off, err);
+    k_oz_gemm<<<grid, OZ_THREADS, dsm, s>>>(As, X, N, ldX, Ea, Eb, k, Mb, Kp, C, ldC, col_off, err, wait);
     return cudaGetLastError();
 }
 

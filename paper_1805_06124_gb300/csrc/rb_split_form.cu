@@ -75,35 +75,30 @@ __global__ void __launch_bounds__(kThreads) k_split_init(Prob p) {
         const float2 *l = p.lo + j * p.ldH;
         const float4 *h4 = reinterpret_cast<const float4 *>(h);
         const float4 *l4 = reinterpret_cast<const float4 *>(l);
-        float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f, lsq = 0.f, c0 = 0.f, c1 = 0.f;
+        Norm2Acc a{0.f, 0.f, 0.f};
+        float bh = 0.f, bl = 0.f, c0 = 0.f, c1 = 0.f;
         for (long long t = lane; t < n2; t += 32) {
             float4 x = h4[t], y = l4[t];
-            df_mac(ah, al, x.x, y.x, x.x, y.x);
-            df_mac(ah, al, x.y, y.y, x.y, y.y);
-            df_mac(ah, al, x.z, y.z, x.z, y.z);
-            df_mac(ah, al, x.w, y.w, x.w, y.w);
+            norm2_acc4(a, x, y);
             df_mac(bh, bl, x.x, 0.f, x.x, 0.f);
             df_mac(bh, bl, x.y, 0.f, x.y, 0.f);
             df_mac(bh, bl, x.z, 0.f, x.z, 0.f);
             df_mac(bh, bl, x.w, 0.f, x.w, 0.f);
-            lsq = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, lsq))));
             c0 = fmaf(x.x, x.x, fmaf(x.y, x.y, c0));
             c1 = fmaf(x.z, x.z, fmaf(x.w, x.w, c1));
         }
         if ((p.N & 1) && lane == 0) {
             float2 x = h[p.N - 1], y = l[p.N - 1];
-            df_mac(ah, al, x.x, y.x, x.x, y.x);
-            df_mac(ah, al, x.y, y.y, x.y, y.y);
+            norm2_acc2(a, x, y);
             df_mac(bh, bl, x.x, 0.f, x.x, 0.f);
             df_mac(bh, bl, x.y, 0.f, x.y, 0.f);
-            lsq = fmaf(y.x, y.x, fmaf(y.y, y.y, lsq));
         }
         p.snorm[j * 64 + lane] = sqrtf(c0) * kNormUp;
         p.snorm[j * 64 + 32 + lane] = sqrtf(c1) * kNormUp;
-        // the lo^2 term dropped by df_mac (2^-48 relative) is added back here
-        double n2s = warp_sum((double)ah + (double)al + (double)lsq);
+        // ||hi + lo||^2 with the steps of the FP64 form's split kernel
+        double n2s = norm2_finish(a);
         double nh = warp_sum((double)bh + (double)bl);
-        double ls = warp_sum((double)lsq);
+        double ls = warp_sum((double)a.lsq);
         if (lane == 0) {
             p.norm2[j] = n2s;
             p.norm2_hi[j] = nh;
@@ -796,7 +791,7 @@ __global__ void __launch_bounds__(LP_THREADS) k_lo_project_tc(Prob p, int *err) 
             if (nstg > 3) proj_load_b(p, j0, 3, bx3, by3);
             auto produce = [&](long long s, float4 (&BX)[PBU], float4 (&BY)[PBU]) {
                 const long long g = g0 + s;
-                if (g >= LP_NBUF) ok = mbar_wait(&done[g % LP_NBUF], par(g - LP_NBUF)) && ok;
+                if (g >= LP_NBUF) ok = mbar_wait(&done[g % LP_NBUF], par(g - LP_NBUF), p.wait_cycles) && ok;
                 proj_store_b(bufA(g) + PTILE, BX, BY);
                 if (s + LP_AHEAD < nstg) proj_load_b(p, j0, s + LP_AHEAD, BX, BY);
                 // each thread makes its own stores visible to the tensor core
@@ -822,8 +817,8 @@ __global__ void __launch_bounds__(LP_THREADS) k_lo_project_tc(Prob p, int *err) 
             for (long long s = 0; s < nstg; s++) {
                 const long long g = g0 + s;
                 const int b = (int)(g % LP_NBUF);
-                ok = mbar_wait(&afull[b], par(g)) && ok;
-                ok = mbar_wait(&bfull[b], par(g)) && ok;
+                ok = mbar_wait(&afull[b], par(g), p.wait_cycles) && ok;
+                ok = mbar_wait(&bfull[b], par(g), p.wait_cycles) && ok;
                 tc_fence_after();
                 const uint64_t ad0 = smem_desc(smem_u32(bufA(g)), 128, (PKC / 8) * 128);
                 const uint64_t bd0 = smem_desc(smem_u32(bufA(g) + PTILE), 128, (PKC / 8) * 128);
@@ -844,14 +839,14 @@ __global__ void __launch_bounds__(LP_THREADS) k_lo_project_tc(Prob p, int *err) 
                 tc_commit(&done[b]);
                 // A of stage s + LP_NBUF - 1 into the buffer of stage s - 1
                 if (s + LP_NBUF - 1 < nstg) {
-                    if (s >= 1) ok = mbar_wait(&done[(g - 1) % LP_NBUF], par(g - 1)) && ok;
+                    if (s >= 1) ok = mbar_wait(&done[(g - 1) % LP_NBUF], par(g - 1), p.wait_cycles) && ok;
                     load_a(s + LP_NBUF - 1);
                 }
             }
         }
         gs = g0 + nstg;
         // every thread: the tile's last MMAs (the latest phase of that barrier)
-        ok = mbar_wait(&done[(gs - 1) % LP_NBUF], par(gs - 1)) && ok;
+        ok = mbar_wait(&done[(gs - 1) % LP_NBUF], par(gs - 1), p.wait_cycles) && ok;
         tc_fence_after();
         // epilogue: thread = A row (TMEM lane); row 2l adds to Re C[l, j], row 2l+1 to Im
         if (warp < 4) {

@@ -69,15 +69,25 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
 }
 
-// Bounded wait on an mbarrier phase; returns false when the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long budget = (1L << 26)) {
-    uint32_t done = 0;
-    for (long it = 0; it < budget && !done; it++) {
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done)
-                     : "r"(smem_u32(bar)), "r"(parity));
+__device__ __forceinline__ uint32_t mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return done;
+}
+
+// Bounded wait on an mbarrier phase: polls until the phase completes or more
+// than `cycles` SM clock cycles have passed since the first poll; returns
+// false when the budget ran out (the caller records the time-out and returns).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long cycles) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = (unsigned long long)clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if ((unsigned long long)clock64() - t0 > cycles) return false;
     }
-    return done != 0;
 }
 
 // mbarrier arrive that also announces `bytes` of asynchronous transfers

@@ -31,7 +31,7 @@ FLAG_PROJECT_FP64 = 2
 class Options(ctypes.Structure):
     _fields_ = [("device", c_int), ("sweep", c_int), ("imgs_kappa", c_double), ("imgs_max_passes", c_int),
                 ("switch_err", c_double), ("iters_per_sync", c_int), ("stream", c_void_p), ("flags", c_uint),
-                ("recompute_period", c_int)]
+                ("recompute_period", c_int), ("batched_variant", c_int), ("timeout_cycles", ctypes.c_ulonglong)]
 
 
 class Result(ctypes.Structure):
@@ -132,7 +132,8 @@ class RB:
 
     def __init__(self, device: int = 0, sweep: str = "df32", kappa: float = 2.0, max_passes: int = 4,
                  switch_err: float = 1e-6, iters_per_sync: int = 8, stream=None, timing: bool = False,
-                 project_fp64: bool = False, recompute_period: int = 16):
+                 project_fp64: bool = False, recompute_period: int = 16, batched_variant: int = -1,
+                 timeout_cycles: int = 0):
         torch = _torch()
         self.lib = load()
         self.device = device
@@ -145,6 +146,8 @@ class RB:
         opt.switch_err = switch_err
         opt.iters_per_sync = iters_per_sync
         opt.recompute_period = recompute_period
+        opt.batched_variant = batched_variant
+        opt.timeout_cycles = timeout_cycles
         if stream is None:
             stream = torch.cuda.current_stream(device)
         self.stream = stream

@@ -17,12 +17,14 @@ def delta(l, N, scale, c0=4.0):
     return c0 * (l + math.log2(max(N, 2))) * U * scale
 
 
-def replay_and_check(orc, S, gpu, tol, kmax, rel_gap=1e-12):
-    """Returns the replayed oracle result; asserts the pivot protocol."""
+def replay_and_check(orc, S, gpu, tol, kmax, rel_gap=1e-12, omp=False):
+    """Returns the replayed oracle result; asserts the pivot protocol.
+    omp: the oracle's OpenMP build (column loops on all host cores, results
+    bit-identical to the single-threaded build) for full-size replays."""
     M, N = S.shape
     piv = np.asarray(gpu["pivots"])
     k = len(piv)
-    rep = orc.rb_greedy(S, tol, kmax, forced=piv)
+    rep = orc.rb_greedy(S, tol, kmax, forced=piv, omp=omp)
     assert rep["k"] == k, (rep["k"], k)
     assert list(rep["pivots"]) == list(piv)
     scale = rep["err_curve"][0]
@@ -41,25 +43,42 @@ def basis_tol(err_curve, k):
     return np.maximum(1e-12, 64 * U * math.sqrt(max(k, 1)) / d)
 
 
-def compare(gpu, rep, S, err_atol=1e-12, c_rel=0.0):
+def column_norms(S, block=4096):
+    """||s_j|| for every row of S, in blocks (S may be tens of GB)."""
+    out = np.empty(S.shape[0])
+    for a in range(0, S.shape[0], block):
+        x = S[a:a + block].view(np.float64)
+        out[a:a + block] = np.sqrt(np.einsum("ij,ij->i", x, x))
+    return out
+
+
+def compare(gpu, rep, S, err_atol=1e-12, c_rel=0.0, norms=None):
     """c_rel: extra C tolerance relative to ||s_j|| (the split form's sweep
-    rounding, a stated bound of that form)."""
+    rounding, a stated bound of that form); norms: ||s_j|| if already known.
+    Returns the measured deviations from the oracle."""
     k = rep["k"]
     ec_g, ec_r = np.asarray(gpu["err_curve"]), rep["err_curve"]
     assert np.max(np.abs(ec_g - ec_r)) <= err_atol, np.max(np.abs(ec_g - ec_r))
     bt = basis_tol(ec_r, k)
     dq = np.max(np.abs(np.asarray(gpu["Q"]) - rep["Q"]), axis=1) if k else np.zeros(0)
     assert np.all(dq <= bt), (np.max(dq / bt), int(np.argmax(dq / bt)))
-    if "C" in gpu:
+    info = dict(k=int(k), max_err_curve_diff=float(np.max(np.abs(ec_g - ec_r))),
+                max_dq=float(np.max(dq)) if k else 0.0,
+                max_dq_over_tol=float(np.max(dq / bt)) if k else 0.0)
+    if "C" in gpu and k:
         Cg = np.asarray(gpu["C"])[:k]
-        ctol = bt[:, None] + 1e-13 + c_rel * np.linalg.norm(S, axis=1)[None, :]
-        r = np.abs(Cg - rep["C"]) / ctol if k else np.zeros((0, 1))
+        if c_rel > 0.0 and norms is None:
+            norms = column_norms(S)
+        ctol = bt[:, None] + 1e-13 + (c_rel * norms[None, :] if c_rel > 0.0 else 0.0)
+        dC = np.abs(Cg - rep["C"])
+        r = dC / ctol
         assert np.all(r <= 1.0), np.max(r)
+        info.update(max_dC=float(np.max(dC)), max_dC_over_tol=float(np.max(r)))
     if "final_err" in gpu:
         df = np.max(np.abs(np.asarray(gpu["final_err"]) - rep["final_err"]))
         assert df <= err_atol, df
-    return dict(max_dq_over_tol=float(np.max(dq / bt)) if k else 0.0,
-                max_err_curve_diff=float(np.max(np.abs(ec_g - ec_r))))
+        info.update(max_final_err_diff=float(df))
+    return info
 
 
 def first_divergence(a, b):
