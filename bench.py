@@ -144,29 +144,57 @@ def cpu_oracle_run(m_sample: int, steps: int = 1, omp: bool = False, want_result
     return by / t_tot / 1e9, t_tot / steps, k
 
 
+def oracle_full_run(S, omp: bool = True):
+    """One full greedy of the FP64 C oracle on the whole host matrix S (the
+    benchmark's workload); returns (GB/s of algorithmic sweep bytes, seconds, k, result)."""
+    from oracle import oracle
+    oracle.build(omp=omp)
+    M, N = S.shape
+    t0 = time.perf_counter()
+    r = oracle.rb_greedy(S, TOL, KMAX, omp=omp)
+    t = time.perf_counter() - t0
+    by = r["k"] * (16.0 * N * M + 16.0 * N + 41.0 * M)
+    return by / t / 1e9, t, r["k"], r
+
+
 def run_reference(args):
+    """The oracle as it stands (its OpenMP build: column loops over all host
+    cores, each column summed sequentially, identical results to one thread)
+    on the benchmark's whole workload, generated on the host."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    m = 4096
+    from paper_1805_06124_gb300 import synth
+    N, M = args.N, args.M
+    S = synth.chirps_blocked(N, M, SEED)
     for _ in range(args.warmup):
-        cpu_oracle_run(m, 1)
-    gbs, t, k = cpu_oracle_run(m, args.steps)
+        oracle_full_run(S)
+    tot, by, k = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        gbs, t, k, _r = oracle_full_run(S)
+        tot += t
+        by += gbs * t
+    gbs = by / tot
+    cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"FP64 CPU oracle, chirps N={N_DEF} x M={m} sample of the N={N_DEF} x "
-                                   f"M={M_DEF} workload, tol {TOL}, kmax {KMAX}", "k": k},
-            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{m} of {M_DEF} columns, N={N_DEF}, one full greedy per step"},
+            "config": {"workload": f"FP64-form RB-greedy on seeded chirps N={N} x M={M} complex128, "
+                                   f"tol {TOL}, kmax {KMAX}", "N": N, "M": M, "tol": TOL, "kmax": KMAX, "k": k,
+                       "impl": "FP64 C oracle, OpenMP build (column loops on all host cores)"},
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"the whole workload ({M} of {M} columns, N={N}), one full greedy per step"},
             "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def split_vs_fp64(torch, rb, synth, dev, stream, N=16384, M=196608, tol=1e-10, reps=3):
+def split_vs_fp64(torch, rb, synth, dev, stream, N=16384, M=196608, tol=1e-10, reps=3, M_big=393216):
     """Time to basis of the FP64 form (complex128 input) and of the split form
-    (hi/lo input) on the same chirps, seed 2; returns the ratio and both curves'
-    agreement."""
+    (hi/lo input) on the same chirps, seed 2, and the two forms' agreement:
+    both take their norms with the same steps, so they start from the same
+    (tied) pivot and their pivots, error curves, bases and final errors are
+    compared directly.  Then the split form alone at M_big columns (hi + lo
+    made in two halves, 103 GB), reported per N*M element."""
     import numpy as np
     c = rb.RB(device=dev, stream=stream)
     q, m = synth.chirp_params(M, 2)
@@ -185,24 +213,59 @@ def split_vs_fp64(torch, rb, synth, dev, stream, N=16384, M=196608, tol=1e-10, r
                 ts.append(r["ms_total"])
         res[name] = dict(ms=float(np.median(ts)), k=r["k"], err_curve=r["err_curve"].cpu().numpy(),
                          pivots=r["pivots"].cpu().numpy(), switch_iter=r["switch_iter"],
-                         final_max=float(r["final_err"].max()))
+                         Q=r["Q"].cpu().numpy(), final_err=r["final_err"].cpu().numpy())
     c.close()
-    del S, hi, lo
-    # unit-norm chirps tie at the first step to the last bit, so the two forms
-    # (norms summed in different arithmetic) may start from different pivots;
-    # the curves are compared over the common pivot prefix
-    pa, pb = res["fp64"]["pivots"], res["split"]["pivots"]
+    del S, hi, lo, r
+    torch.cuda.empty_cache()
+    a, b = res["fp64"], res["split"]
+    pa, pb = a["pivots"], b["pivots"]
     same = next((i for i in range(min(len(pa), len(pb))) if pa[i] != pb[i]), min(len(pa), len(pb)))
-    n = min(len(res["fp64"]["err_curve"]), len(res["split"]["err_curve"]), same + 1)
-    return {"workload": f"chirps N={N} x M={M} seed 2, tol {tol}; FP64 form reads complex128, split form reads "
-                        "complex64 hi+lo (prepared by rb_split, not timed)",
-            "fp64_ms": round(res["fp64"]["ms"], 2), "split_ms": round(res["split"]["ms"], 2),
-            "ratio": round(res["fp64"]["ms"] / res["split"]["ms"], 3),
-            "k_fp64": res["fp64"]["k"], "k_split": res["split"]["k"], "switch_iter": res["split"]["switch_iter"],
-            "common_pivot_prefix": int(same),
-            "max_abs_err_curve_diff_on_prefix": float(np.max(np.abs(res["fp64"]["err_curve"][:n] - res["split"]["err_curve"][:n]))),
-            "fp64_final_max_err": res["fp64"]["final_max"],
-            "split_final_max_err": res["split"]["final_max"]}
+    n = min(len(a["err_curve"]), len(b["err_curve"]), same + 1)
+    out = {"workload": f"chirps N={N} x M={M} seed 2, tol {tol}; FP64 form reads complex128, split form reads "
+                       "complex64 hi+lo (prepared by rb_split, not timed)",
+           "fp64_ms": round(a["ms"], 2), "split_ms": round(b["ms"], 2), "ratio": round(a["ms"] / b["ms"], 3),
+           "k_fp64": a["k"], "k_split": b["k"], "switch_iter": b["switch_iter"],
+           "common_pivot_prefix": int(same),
+           "max_abs_err_curve_diff_on_prefix": float(np.max(np.abs(a["err_curve"][:n] - b["err_curve"][:n]))),
+           "fp64_final_max_err": float(a["final_err"].max()), "split_final_max_err": float(b["final_err"].max())}
+    if same == a["k"] == b["k"]:
+        out["max_abs_final_err_diff"] = float(np.max(np.abs(a["final_err"] - b["final_err"])))
+        out["max_basis_diff"] = float(np.max(np.abs(a["Q"] - b["Q"])))
+        # relative to the per-vector basis tolerance of the parity tests
+        d = np.sqrt(np.maximum(a["err_curve"][:same], 1e-300))
+        bt = np.maximum(1e-12, 64 * 2.0 ** -53 * np.sqrt(same) / d)
+        out["max_basis_diff_over_tol"] = float(np.max(np.max(np.abs(a["Q"] - b["Q"]), axis=1) / bt))
+    del res
+    if M_big:
+        c = rb.RB(device=dev, stream=stream)
+        qb, mb = synth.chirp_params(M_big, 2)
+        ld = N
+        with torch.cuda.stream(stream):
+            hi = torch.empty((M_big, ld), dtype=torch.complex64, device=f"cuda:{dev}")
+            lo = torch.empty((M_big, ld), dtype=torch.complex64, device=f"cuda:{dev}")
+            half = M_big // 2
+            for a0, a1 in ((0, half), (half, M_big)):
+                Sp = c.generate(qb[a0:a1], mb[a0:a1], N)
+                c.split(Sp, out=(hi[a0:a1], lo[a0:a1]))
+                del Sp
+        stream.synchronize()
+        torch.cuda.empty_cache()
+        with torch.cuda.stream(stream):
+            r = c.greedy_split(hi, lo, tol, 800)
+            ts = []
+            for _ in range(2):
+                r = c.greedy_split(hi, lo, tol, 800)
+                ts.append(r["ms_total"])
+        ms = float(np.median(ts))
+        out["split_M393216"] = {"workload": f"split form, chirps N={N} x M={M_big} seed 2 "
+                                            f"({16.0 * N * M_big / 1e9:.1f} GB hi+lo), tol {tol}",
+                                "ms": round(ms, 2), "k": r["k"],
+                                "ps_per_element": round(ms * 1e9 / (N * M_big), 2),
+                                "fp64_form_ps_per_element_at_M196608": round(a["ms"] * 1e9 / (N * M), 2)}
+        c.close()
+        del hi, lo, r
+        torch.cuda.empty_cache()
+    return out
 
 
 def batched_run(torch, rb, synth, dev, stream, nprob=96, seed=3, tol=1e-10, reps=2):
@@ -591,6 +654,7 @@ def run_ours(args):
 
     # end to end through the host-buffer entry point
     e2e = None
+    Sh, piv_gpu = None, []
     if rank == 0 and not args.no_e2e:
         Sh = torch.empty((M, N), dtype=torch.complex128, pin_memory=True)
         Sh.copy_(S)
@@ -601,7 +665,7 @@ def run_ours(args):
         outb = rb.RB.host_outputs(N, M, KMAX)
         rh = ctx_h.greedy_host(Sh, TOL, KMAX, out=outb)
         t0 = time.perf_counter()
-        nst = max(1, min(args.steps, 2))
+        nst = max(1, args.steps)
         byts, h2d, d2h = 0.0, 0, 0
         for _ in range(nst):
             rh = ctx_h.greedy_host(Sh, TOL, KMAX, out=outb)
@@ -629,27 +693,55 @@ def run_ours(args):
                 "host_columns_read_per_iteration": round(sts["chunk_reads"] / max(1, sts["chunks"] * gs["k"]), 4)}
             del gs
         ctx_h.close()
-        del Sh, outb, rh
+        piv_gpu = outb["pivots"][:kh].numpy().copy()
+        del outb, rh
 
-    cpu = cpu_omp = None
+    cpu = cpu_1t = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cores = 1
-        gbs, t_cpu, k_cpu, r1 = cpu_oracle_run(CPU_SAMPLE_M, 1, want_result=True)
-        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
-               "sample": f"one full greedy on {CPU_SAMPLE_M} of {M} columns (N={N}, seed {SEED}, tol {TOL}), "
-                         f"k={k_cpu}, {t_cpu:.1f} s"}
-        # the paper's shared-memory scheme: the same oracle with its column
-        # loops on all host cores (identical results)
+        import numpy as np
+        # the oracle as it stands on the whole workload (the same bytes of S,
+        # from the pinned host copy), its OpenMP build: the paper's
+        # shared-memory scheme, column loops on all host cores
+        Sn = Sh.numpy() if Sh is not None else synth.chirps_blocked(N, M, SEED + rank)
         try:
-            gbs_o, t_o, k_o, r2 = cpu_oracle_run(CPU_SAMPLE_M, 1, omp=True, want_result=True)
-            import numpy as np
-            cpu_omp = {"value": round(gbs_o, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle, OpenMP",
-                       "sample": f"the same {CPU_SAMPLE_M}-column sample, {t_o:.1f} s",
-                       "identical_to_single_thread": bool(k_o == k_cpu and
-                                                          np.array_equal(r1["pivots"], r2["pivots"]) and
-                                                          np.array_equal(r1["err_curve"], r2["err_curve"]))}
+            gbs_o, t_o, k_o, r_o = oracle_full_run(Sn, omp=True)
+            piv_o = np.asarray(r_o["pivots"])
+            common = next((i for i in range(min(len(piv_o), len(piv_gpu))) if piv_o[i] != piv_gpu[i]),
+                          min(len(piv_o), len(piv_gpu))) if Sh is not None else None
+            cpu = {"value": round(gbs_o, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"the whole workload: one full greedy on all {M} columns (N={N}, seed {SEED}, "
+                             f"tol {TOL}), k={k_o}, {t_o:.1f} s, OpenMP build (column loops on all host cores, "
+                             f"results identical to one thread)",
+                   "k": k_o, "pivots_equal_gpu_prefix": common}
+            del r_o
         except Exception as e:  # no OpenMP runtime on this host
-            cpu_omp = {"unavailable": str(e)[:200]}
+            cpu = {"unavailable": str(e)[:200]}
+        # the single-threaded build (the authority) on a column sample
+        gbs, t_cpu, k_cpu, r1 = cpu_oracle_run(CPU_SAMPLE_M, 1, want_result=True)
+        cpu_1t = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                  "sample": f"one full greedy on {CPU_SAMPLE_M} of {M} columns (N={N}, seed {SEED}, tol {TOL}), "
+                            f"k={k_cpu}, {t_cpu:.1f} s"}
+        del Sn
+    Sh = None
+
+    # the plain-FP64 (DFMA) sweep on the same workload, for comparison
+    sweep_fp64 = None
+    if rank == 0 and world == 1 and not args.no_next and args.sweep == "df32":
+        with torch.cuda.stream(stream):
+            if S is None:
+                S = ctx.generate(q, m, N)
+            c64 = rb.RB(device=local, sweep="fp64", stream=stream)
+            r64 = c64.greedy(S, TOL, KMAX)
+            ts = []
+            for _ in range(2):
+                r64 = c64.greedy(S, TOL, KMAX)
+                ts.append(r64["ms_total"])
+        t64 = sorted(ts)[len(ts) // 2]
+        sweep_fp64 = {"sweep": "plain FP64 DFMA products on complex128 (RB_SWEEP_FP64)", "k": r64["k"],
+                      "time_to_basis_ms": round(t64, 2),
+                      "GBps": round(r64["sweep_bytes"] / (t64 * 1e-3) / 1e9, 1)}
+        c64.close()
+        del r64
 
     extra_split = extra_batched = None
     if rank == 0 and world == 1:
@@ -666,7 +758,12 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 (df32 sweep)" if args.sweep == "df32" else "f64",
+                "dtype_note": ("sweep products in double-float on the FP32 pipe over a hi/lo copy of S that equals "
+                               "complex128 to 2^-48 relative (the lo*lo term dropped); bookkeeping, argmax, IMGS "
+                               "and norms in FP64") if args.sweep == "df32" else "plain FP64",
+                "data": "synthetic",
                 "config": {"workload": f"FP64-form RB-greedy on seeded chirps N={N} x M={M} complex128, "
                                        f"tol {TOL}, kmax {KMAX}", "N": N, "M": M, "tol": TOL, "kmax": KMAX,
                            "sweep": args.sweep, "k": k, "time_to_basis_ms": round(ms_max / args.steps, 3),
@@ -679,7 +776,7 @@ def run_ours(args):
                              "traffic": (round(tpb * per_launch) if tpb else None),
                              "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": round(sweep_ms, 4)},
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
-                "cpu_baseline_openmp": cpu_omp,
+                "cpu_baseline_1thread": cpu_1t, "sweep_fp64": sweep_fp64,
                 "split_vs_fp64": extra_split, "batched": extra_batched, "after_greedy": extra_next}
         print(json.dumps(line), flush=True)
     if not (rank == 0 and world == 1):

@@ -191,10 +191,21 @@ class RB:
         self._check(self.lib.rb_generate(self._h, q.data_ptr(), m.data_ptr(), N, M, S.data_ptr(), ld))
         return S
 
-    def split(self, S, ldh: int | None = None):
+    def split(self, S, ldh: int | None = None, out=None):
+        """hi/lo complex64 split of S (rb_split).  out: optional (hi, lo) views
+        of shape (M, N) with a common row stride, written in place."""
         torch = _torch()
         _check2d(S, torch.complex128, "S")
         M, N = S.shape
+        if out is not None:
+            hi, lo = out
+            if (hi.dtype != torch.complex64 or lo.dtype != torch.complex64 or tuple(hi.shape) != (M, N)
+                    or tuple(lo.shape) != (M, N) or hi.stride(1) != 1 or lo.stride(1) != 1
+                    or _ld(hi) != _ld(lo)):
+                raise ValueError("split: out must be two complex64 (M, N) views with one row stride")
+            self._check(self.lib.rb_split(self._h, S.data_ptr(), N, M, _ld(S), hi.data_ptr(), lo.data_ptr(),
+                                          _ld(hi)))
+            return hi, lo
         ldh = N if ldh is None else ldh
         with torch.cuda.stream(self.stream):
             hi = torch.empty((M, ldh), dtype=torch.complex64, device=S.device)

@@ -59,6 +59,24 @@ def chirps(N: int, M: int, seed: int, **kw) -> np.ndarray:
     return chirp_matrix(N, q, m)
 
 
+def chirps_blocked(N: int, M: int, seed: int, block: int = 4096, threads: int | None = None) -> np.ndarray:
+    """The same snapshots as ``chirps`` for large M: the (q, m) draws are made
+    once for all columns, then the rows are filled in blocks on a thread pool
+    (numpy's elementwise loops release the GIL), so the peak memory is the
+    output plus one block of temporaries per thread."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    q, m = chirp_params(M, seed)
+    S = np.empty((M, N), np.complex128)
+
+    def fill(a):
+        S[a:a + block] = chirp_matrix(N, q[a:a + block], m[a:a + block])
+
+    with ThreadPoolExecutor(max_workers=threads or min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(fill, range(0, M, block)))
+    return S
+
+
 def random_complex(M: int, N: int, seed: int, scales=None) -> np.ndarray:
     """Gaussian complex (M, N) matrix; optional per-snapshot scales."""
     rng = np.random.default_rng(seed)
