@@ -303,3 +303,26 @@ def test_openmp_build_gives_identical_results(orc):
     np.testing.assert_array_equal(a["err_curve"], b["err_curve"])
     np.testing.assert_array_equal(a["Q"], b["Q"])
     np.testing.assert_array_equal(a["C"], b["C"])
+
+
+@pytest.mark.parametrize("N,M", [(16384, 1024), (1024, 2048)])
+def test_bookkeeping_noise_within_parity_margin(orc, N, M):
+    """The noise model of the parity protocol: the oracle's final errors from
+    the Eq. (Residual) bookkeeping (sequential FP64 norms and coefficients)
+    deviate from the direct residual norms ||s_j - Q Q^H s_j||^2 (no
+    cancellation: accurate to about 1e-20 here) by less than half of the
+    margin delta(k, N) = 4 (k + sqrt(N)) u max||s||^2 that the GPU replays
+    allow each side.  A bookkeeping mistake (a dropped term, a wrong index)
+    would show here as a deviation of order the errors themselves."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import parity
+    S = synth.chirps(N, M, seed=2)
+    r = orc.rb_greedy(S, 1e-10, 300)
+    Q, k = r["Q"], r["k"]
+    R = S - (Q.conj() @ S.T).T @ Q
+    direct = np.sum(R.real ** 2 + R.imag ** 2, axis=1)
+    dev = np.max(np.abs(r["final_err"] - direct))
+    assert dev <= 0.5 * parity.delta(k, N, r["err_curve"][0]), (dev, parity.delta(k, N, r["err_curve"][0]))
+    assert dev > 0.0  # rounding is there, so the check is not vacuous
