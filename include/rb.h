@@ -189,8 +189,10 @@ rb_status rb_greedy_resume(rb_ctx *ctx, const void *S, long long N, long long M,
  * upper bound, or the exact pivot error, is below tol (or at kmax), and then
  * one tensor-core projection of the basis onto lo completes C and the errors.
  * IMGS, norms, the bookkeeping and the re-check stay FP64(-accurate).  Outputs
- * and returns as rb_greedy; C is accurate to 2^-48 sqrt(N) ||s_j|| beyond the
- * FP64 form's; out->switch_iter is the basis size at the projection onto lo;
+ * and returns as rb_greedy; C is accurate to (2^-48 sqrt(N) + 2^-42) ||s_j||
+ * beyond the FP64 form's (the hi-only sweep's rounding and the FP16 pieces of
+ * the projection onto lo); out->switch_iter is the basis size at the
+ * projection onto lo;
  * opt.switch_err is not used by this form. */
 rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long N, long long M, long long ld,
                           double tol, int kmax, rb_result *out);

@@ -573,8 +573,9 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     size_t o_np = L.add(np * 8), o_be = L.add((size_t)G * 8), o_bi = L.add((size_t)G * 8);
     size_t o_bc = L.add((size_t)G * 4), o_cd = L.add((size_t)M * 8), o_ce = L.add((size_t)M * 8);
     size_t o_pv = L.add((size_t)M * lgcap * 8);
-    // BF16 pieces of the basis for the projection onto lo
+    // FP16 pieces of the basis for the projection onto lo, and their scales
     size_t o_ap = L.add(rbk::lo_pieces_bytes(N, kcap));
+    size_t o_qs = L.add((size_t)kcap * sizeof(int));
     // re-check chunk partials and counters (2048 pairs x 8 chunks x 32 doubles)
     size_t o_rp = L.add((size_t)2048 * 8 * 32 * 8), o_rt = L.add((size_t)2048 * 4);
     size_t o_C = out->C ? 0 : L.add((size_t)kcap * M * sizeof(double2));
@@ -633,6 +634,7 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     p.cand_err = (double *)(w + o_ce);
     p.pv = (double *)(w + o_pv);
     p.apieces = (uint8_t *)(w + o_ap);
+    p.qscale = (int *)(w + o_qs);
     p.rpart = (double *)(w + o_rp);
     p.rtick = (int *)(w + o_rt);
     p.lgcap = lgcap;

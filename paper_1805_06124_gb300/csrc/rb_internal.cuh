@@ -96,7 +96,8 @@ struct Prob {
     long long *cand;   // candidate columns (capacity M)
     double *cand_err;  // their exact errors
     double *pv;        // recheck partials [candidate][group of 8 basis vectors]
-    uint8_t *apieces;  // BF16 pieces of the basis for the projection onto lo
+    uint8_t *apieces;  // FP16 pieces of the basis for the projection onto lo
+    int *qscale;       // their power-of-two scale exponents, one per basis vector
     double *rpart;     // re-check row-chunk partials [pair][chunk][32]
     int *rtick;        // re-check chunk counters per (candidate, group) pair
     int lgcap;         // groups per candidate in pv

@@ -594,176 +594,281 @@ __global__ void __launch_bounds__(kThreads) k_recheck(Prob p) {
 // d = Qh^H lo for the k1 basis vectors on the tensor cores, then C[l, j] += d.
 // As a real GEMM with K = 2N interleaved (re, im): A rows 2l = (a_i, b_i) and
 // 2l+1 = (-b_i, a_i) for q_l = a + ib; B row j = (u_i, v_i) for lo_j = u + iv.
-// Every FP32 value is split exactly into three BF16 pieces (x = x1 + x2 + x3);
-// the six piece products with s + t <= 4 accumulate into one FP32 TMEM
-// accumulator, which leaves a relative error of a few 2^-24 -- what d needs,
-// since |lo| <= 2^-24 |s|.  Blocks loop over (row tile, column tile) pairs.
-constexpr int PT = 128;  // tile rows (A) and columns (B)
-constexpr int PKC = 32;  // K per stage
-constexpr int PSL = 3;   // BF16 pieces per FP32 value
+// Every FP32 value is scaled by a power of two (per basis vector for A, per
+// column for B, so that the largest scaled magnitude is at most 2^14) and
+// split into two FP16 pieces: hi = the value with its low 13 mantissa bits
+// cleared, lo = the exact remainder (|lo| < 2^-10 |x|) rounded to FP16
+// (lp_enc2).  The three products hiA hiB + hiA loB + loA hiB accumulate in
+// one FP32 TMEM accumulator; the dropped loA loB and the rounding of the lo
+// pieces leave a relative error below 2^-19 per product, i.e. below
+// 2^-43 ||s_j|| on d since |lo_j| <= 2^-24 |s_j|.  The epilogue undoes the
+// two scales exactly.  Tiles are LT_M = 128 rows of A by nt <= 128 columns of
+// lo, stages of LKC = 64 K entries; blocks loop over (row tile, column tile)
+// pairs.
+constexpr int LT_M = 128;      // A rows per tile
+constexpr int LT_NMAX = 128;   // lo columns per tile (at most)
+constexpr int LKC = 64;        // K entries per stage (32 complex elements, 256 bytes of lo per column)
+constexpr int LA_PIECE = LT_M * LKC * 2;       // bytes of one FP16 piece of an A stage (16 KB)
+constexpr int LA_STAGE = 2 * LA_PIECE;         // both pieces (32 KB)
+// B pieces in shared memory: the K-major no-swizzle canonical layout with the
+// core matrices (8 rows x 16 bytes) of one 8-row group LB_LBO = 144 bytes
+// apart along K (128 + 16: consecutive K core matrices of a row fall in
+// different banks) and 8-row groups LB_SBO = 4 x 144 bytes apart; the lo
+// piece starts 64 bytes (mod 128) after the hi piece.  A row's 4 hi and 4 lo
+// 16-byte pieces then cover all 8 bank groups (see lp_store).
+constexpr int LB_LBO = 144;
+constexpr int LB_SBO = (LKC / 8) * LB_LBO;       // 1152
+constexpr int LB_PIECE = (LT_NMAX / 8) * LB_SBO;  // one FP16 piece of a B stage (18 KB)
+constexpr int LB_LO = LB_PIECE + 64;              // offset of the lo piece
+constexpr int LSTAGE = LA_STAGE + LB_LO + LB_PIECE;  // one ring buffer (68 KB + 64 B)
+static_assert(LSTAGE % 16 == 0 && LB_LO % 128 == 64, "B layout");
 
-// x rounded to BF16 (nearest, ties to even), as the FP32 bit pattern with the
-// low 16 bits cleared: BF16 is the top half of an FP32, so the rounding is an
-// integer add and mask (finite x; conversion instructions run at a low rate on
-// this GPU).
-__device__ __forceinline__ uint32_t bf16_round_bits(float x) {
-    const uint32_t u = __float_as_uint(x);
-    return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+__device__ __forceinline__ uint32_t lb_off(int r, int k) {
+    return (uint32_t)((r >> 3) * LB_SBO + (k >> 3) * LB_LBO + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// Exact split x = x1 + x2 + x3 into BF16 pieces (each difference is exact in
-// FP32); o[s] = the FP32 bit pattern of piece s (its BF16 value in the top half).
-__device__ __forceinline__ void split3_bits(float x, uint32_t o[PSL]) {
-    o[0] = bf16_round_bits(x);
-    const float r = x - __uint_as_float(o[0]);
-    o[1] = bf16_round_bits(r);
-    o[2] = bf16_round_bits(r - __uint_as_float(o[1]));
+// Power-of-two exponent e with 2^e * x_max <= 2^14 for x_max > 0 (0 for
+// x_max == 0), clamped so that 2^e is a normal FP32 number.
+__device__ __forceinline__ int lp_scale_exp(float xmax) {
+    const uint32_t b = __float_as_uint(xmax) & 0x7FFFFFFFu;
+    if (b == 0u) return 0;
+    int e = (int)(b >> 23) - 127;  // xmax in [2^e, 2^(e+1)) (normal); subnormal -> -127
+    if (b & 0x007FFFFFu) e += 1;   // ceil(log2(xmax))
+    int s = 14 - e;
+    return s > 126 ? 126 : (s < -126 ? -126 : s);
 }
 
-// Stage 8 consecutive K entries (4 complex elements) of one tile row into the
-// three piece tiles: one 16-byte core-matrix row per piece.
-__device__ __forceinline__ void stage_row8(uint8_t *base, int r, int kk, const float v[8]) {
-    uint32_t pc[PSL][8];
+__device__ __forceinline__ float lp_pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// Two FP16 pieces of a pair of values y = x * f (|y| < 2^15): hi = y with
+// its low 13 mantissa bits cleared (on the FP16 grid on the FP16 normal
+// range, so its conversion is exact there), lo = the exact remainder y - hi
+// rounded to FP16; each pair is converted by one packed conversion (element
+// a in the low half).  |y - hi - lo| <= 2^-21 |y| on the FP16 normal range and
+// below 2^-24 absolutely under it.
+__device__ __forceinline__ void lp_enc2(float a, float b, float f, uint32_t &hw, uint32_t &lw) {
+    const float ya = __fmul_rn(a, f), yb = __fmul_rn(b, f);
+    const float ta = __uint_as_float(__float_as_uint(ya) & 0xFFFFE000u);
+    const float tb = __uint_as_float(__float_as_uint(yb) & 0xFFFFE000u);
+    const __half2 h = __floats2half2_rn(ta, tb);
+    const __half2 l = __floats2half2_rn(__fsub_rn(ya, ta), __fsub_rn(yb, tb));
+    hw = *reinterpret_cast<const uint32_t *>(&h);
+    lw = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// Per basis vector l < k1: sa[l] = lp_scale_exp(max_i max(|Re qh_i|, |Im qh_i|)).
+__global__ void __launch_bounds__(kThreads) k_qscale(Prob p) {
+    DevState *st = p.st;
+    if (ld_volatile(&st->stop) || !ld_volatile(&st->switch_pending)) return;
+    const int k1 = st->k;
+    __shared__ float s_m[kThreads / 32];
+    for (int l = blockIdx.x; l < k1; l += gridDim.x) {
+        const float2 *q = p.qh + (long long)l * p.qs_stride;
+        float m = 0.f;
+        for (long long i = threadIdx.x; i < p.N; i += blockDim.x) {
+            const float2 v = q[i];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
 #pragma unroll
-    for (int e = 0; e < 8; e++) {
-        uint32_t o[PSL];
-        split3_bits(v[e], o);
-#pragma unroll
-        for (int s = 0; s < PSL; s++) pc[s][e] = o[s];
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float x = 0.f;
+            for (int w = 0; w < kThreads / 32; w++) x = fmaxf(x, s_m[w]);
+            p.qscale[l] = lp_scale_exp(x);
+        }
+        __syncthreads();
     }
-#pragma unroll
-    for (int s = 0; s < PSL; s++) {
-        // pairs of BF16 values: element 2i in the low half of word i
-        const uint4 w = make_uint4(__byte_perm(pc[s][0], pc[s][1], 0x7632), __byte_perm(pc[s][2], pc[s][3], 0x7632),
-                                   __byte_perm(pc[s][4], pc[s][5], 0x7632), __byte_perm(pc[s][6], pc[s][7], 0x7632));
-        *(uint4 *)(base + s * (PT * PKC * 2) + kmajor_off(r, kk, PKC)) = w;
-    }
 }
 
-// A operand pieces, built once when the loop ends: for row tile rt and K
-// stage st the three BF16 piece tiles lie contiguously (48 KB) in the layout
-// the MMA reads, so a block stages them with plain 16-byte copies.
-constexpr int PTILE = PSL * PT * PKC * 2;  // bytes of one stage's three piece tiles
-
+// A operand pieces, built once when the loop ends: for row tile rt and stage
+// stg the two FP16 piece tiles (K-major canonical layout) lie contiguously
+// (16 KB) at apieces + (rt * nstg + stg) * LA_STAGE, so a block stages them
+// with one bulk copy.  Rows 2 k1 .. and K entries beyond 2N are zero.
 __global__ void __launch_bounds__(kThreads) k_qpieces(Prob p) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop) || !ld_volatile(&st->switch_pending)) return;
     const int k1 = st->k;
-    const int nrt = (2 * k1 + PT - 1) / PT;
-    const long long nstg = (2 * p.N + PKC - 1) / PKC;
-    const long long units = (long long)nrt * nstg * PT * (PKC / 8);
+    const int nrt = (2 * k1 + LT_M - 1) / LT_M;
+    const long long nstg = (2 * p.N + LKC - 1) / LKC;
+    const long long units = (long long)nrt * nstg * LT_M * (LKC / 8);
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
          u += (long long)gridDim.x * blockDim.x) {
-        const long long ts = u / (PT * (PKC / 8));  // (rt, stage) index = rt * nstg + stage
-        const int w = (int)(u % (PT * (PKC / 8)));
-        const int r = w / (PKC / 8), kk = (w % (PKC / 8)) * 8;
+        const long long ts = u / (LT_M * (LKC / 8));  // rt * nstg + stg
+        const int w = (int)(u % (LT_M * (LKC / 8)));
+        const int r = w / (LKC / 8), kk = (w % (LKC / 8)) * 8;
         const int rt = (int)(ts / nstg);
         const long long stg = ts % nstg;
-        const int gr = rt * PT + r;
-        float v[8];
-        const long long i0 = (stg * PKC + kk) >> 1;
+        const int gr = rt * LT_M + r;
+        const int l = gr >> 1;
+        const float f = gr < 2 * k1 ? lp_pow2f(p.qscale[l]) : 0.f;
+        const long long i0 = (stg * LKC + kk) >> 1;
+        uint32_t hp[4], lp[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             const long long i = i0 + e;
-            const float2 q = (gr < 2 * k1 && i < p.N) ? p.qh[(long long)(gr >> 1) * p.qs_stride + i] : make_float2(0.f, 0.f);
-            if ((gr & 1) == 0) { v[2 * e] = q.x; v[2 * e + 1] = q.y; }
-            else { v[2 * e] = -q.y; v[2 * e + 1] = q.x; }
+            const float2 q = (gr < 2 * k1 && i < p.N) ? p.qh[(long long)l * p.qs_stride + i] : make_float2(0.f, 0.f);
+            const float x0 = (gr & 1) == 0 ? q.x : -q.y;
+            const float x1 = (gr & 1) == 0 ? q.y : q.x;
+            lp_enc2(x0, x1, f, hp[e], lp[e]);
         }
-        stage_row8(p.apieces + ts * PTILE, r, kk, v);
+        uint8_t *base = p.apieces + ts * LA_STAGE + kmajor_off(r, kk, LKC);
+        *(uint4 *)base = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+        *(uint4 *)(base + LA_PIECE) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
     }
 }
 
-// One stage of B (lo columns j0..j0+127, K entries [64 stg, +64)) into
-// registers: thread t holds units t + u * kThreads, each 8 K entries.
-constexpr int PBU = PT * (PKC / 8) / kThreads;
+// Producer side of one stage: warp w (of LP_PWARPS) handles the column
+// groups g = w + LP_PWARPS x (x < LP_GROUPS, g < nt / 4) of 4 columns.  Lane
+// L takes column 4 g + (L >> 3) and, per instruction i < LP_CH, the 16-byte
+// chunk q = (L & 7) + 8 i of the column's LKC / 16 chunks (2 complex elements
+// = K entries 4q .. 4q+3): each warp load reads whole 128-byte lines of 4
+// columns.
+constexpr int LP_PWARPS = 16;                       // producer warps
+constexpr int LP_GROUPS = LT_NMAX / 4 / LP_PWARPS;  // column groups per producer warp
+constexpr int LP_CH = LKC / 32;                     // 16-byte chunks per lane, column and stage
+struct LpRegs {
+    float4 v[LP_GROUPS][LP_CH];
+};
 
-// Unit t -> (row r, first K entry kk) such that the 8 threads of each quarter
-// warp store the 8 rows of one core matrix (128 contiguous bytes: no bank
-// conflicts), while each warp still reads whole 128-byte runs of lo.
-__device__ __forceinline__ void proj_unit(int t, int &r, int &kk) {
-    r = (t & 7) + 8 * (t / (8 * (PKC / 8)));
-    kk = ((t >> 3) % (PKC / 8)) * 8;
+// What a producer lane needs per tile, computed once.  A lane's columns are
+// j0 + 4 w + (L >> 3) + 64 x: consecutive groups are 64 columns apart, so
+// the tile state is one base pointer, a validity mask, the scales and one
+// store offset (group x adds 8 row groups, chunk set i adds 4 core columns).
+struct LpTile {
+    const float4 *base;  // chunk (L & 7) of the lane's first column (x = 0)
+    unsigned valid;      // bit x: group x in range
+    float f[LP_GROUPS];
+    uint32_t doff;       // store offset of group 0, chunk set 0
+};
+
+__device__ __forceinline__ void lp_tile(const Prob &p, long long j0, int nt, LpTile &T) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool even = (lane & 1) == 0;
+    const int r0 = 4 * w + (lane >> 3);
+    T.base = reinterpret_cast<const float4 *>(p.lo + (j0 + r0) * p.ldH) + (lane & 7);
+    T.valid = 0u;
+#pragma unroll
+    for (int x = 0; x < LP_GROUPS; x++) {
+        const int g = w + LP_PWARPS * x;
+        const long long j = j0 + 4 * g + (lane >> 3);
+        const bool ok = 4 * g < nt && j < p.M;
+        if (ok) T.valid |= 1u << x;
+        T.f[x] = ok ? lp_pow2f(lp_scale_exp(p.lonrm[j])) : 0.f;
+    }
+    T.doff = (even ? 0u : (uint32_t)LB_LO) + lb_off(r0, 8 * ((lane & 7) >> 1));
 }
 
-__device__ __forceinline__ void proj_load_b(const Prob &p, long long j0, long long stg, float4 bx[PBU], float4 by[PBU]) {
+// Stage stg of this lane's columns: chunks (lane & 7) + 8 i of each, i.e.
+// complex elements (LKC / 2) stg + 2 ((lane & 7) + 8 i) + {0, 1}; stages below
+// nfull (= N / (LKC / 2)) lie wholly inside the columns.
+__device__ __forceinline__ void lp_load(const Prob &p, const LpTile &T, long long stg, long long nfull, LpRegs &R) {
+    const int lane = threadIdx.x & 31;
+    const long long gstride = 64 * (p.ldH >> 1);  // float4 between a lane's groups
 #pragma unroll
-    for (int u = 0; u < PBU; u++) {
-        const int t = threadIdx.x + u * kThreads;
-        int r, kk;
-        proj_unit(t, r, kk);
-        const long long j = j0 + r;
-        const long long i0 = (stg * PKC + kk) >> 1;  // a multiple of 4
-        if (j < p.M && i0 + 3 < p.N) {
-            const float4 *l4 = reinterpret_cast<const float4 *>(p.lo + j * p.ldH + i0);
-            bx[u] = ld_stream(l4);
-            by[u] = ld_stream(l4 + 1);
-        } else {
-            float v[8];
+    for (int x = 0; x < LP_GROUPS; x++) {
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const long long i = i0 + e;
-                const float2 x = (j < p.M && i < p.N) ? p.lo[j * p.ldH + i] : make_float2(0.f, 0.f);
-                v[2 * e] = x.x;
-                v[2 * e + 1] = x.y;
+        for (int i = 0; i < LP_CH; i++) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (T.valid & (1u << x)) {
+                const float4 *src = T.base + x * gstride + stg * (LKC / 4) + 8 * i;
+                if (stg < nfull) {
+                    v = ld_stream(src);
+                } else {
+                    const long long e0 = stg * (LKC / 2) + 2 * ((lane & 7) + 8 * i);
+                    if (e0 + 1 < p.N) {
+                        v = ld_stream(src);
+                    } else if (e0 < p.N) {
+                        const float2 a = *reinterpret_cast<const float2 *>(src);
+                        v = make_float4(a.x, a.y, 0.f, 0.f);
+                    }
+                }
             }
-            bx[u] = make_float4(v[0], v[1], v[2], v[3]);
-            by[u] = make_float4(v[4], v[5], v[6], v[7]);
+            R.v[x][i] = v;
         }
     }
 }
 
-__device__ __forceinline__ void proj_store_b(uint8_t *sB, const float4 bx[PBU], const float4 by[PBU]) {
+// Converts the stage held in R into the two B piece tiles of the buffer at
+// sB: lanes L and L^1 hold the two halves (4 K entries each) of one 16-byte
+// core-matrix row of column 4 g + (L >> 3); the lane with the lower half
+// stores the hi row, its partner the lo row.  The 8 lanes of a quarter warp
+// (one column, four core columns, both pieces) hit 8 different bank groups
+// in the padded layout (lb_off, LB_LO).
+__device__ __forceinline__ void lp_store(int nt, const LpTile &T, const LpRegs &R, uint8_t *sB) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool even = (lane & 1) == 0;
 #pragma unroll
-    for (int u = 0; u < PBU; u++) {
-        const int t = threadIdx.x + u * kThreads;
-        int r, kk;
-        proj_unit(t, r, kk);
-        const float v[8] = {bx[u].x, bx[u].y, bx[u].z, bx[u].w, by[u].x, by[u].y, by[u].z, by[u].w};
-        stage_row8(sB, r, kk, v);
+    for (int x = 0; x < LP_GROUPS; x++) {
+        const int g = w + LP_PWARPS * x;
+        if (4 * g >= nt) continue;  // warp-uniform
+        const float f = T.f[x];
+#pragma unroll
+        for (int i = 0; i < LP_CH; i++) {
+            const float4 v = R.v[x][i];
+            const uint32_t doff = T.doff + (uint32_t)(x * 8 * LB_SBO + i * 4 * LB_LBO);
+            uint32_t ha, la, hb, lb;
+            lp_enc2(v.x, v.y, f, ha, la);
+            lp_enc2(v.z, v.w, f, hb, lb);
+            // the even lane keeps its hi half and receives the odd lane's hi
+            // half; the odd lane keeps its lo half and receives the even lane's
+            const uint32_t sa = even ? la : ha, sb = even ? lb : hb;
+            const uint32_t ra = __shfl_xor_sync(0xffffffffu, sa, 1);
+            const uint32_t rb = __shfl_xor_sync(0xffffffffu, sb, 1);
+            *(uint4 *)(sB + doff) = even ? make_uint4(ha, hb, ra, rb) : make_uint4(ra, rb, la, lb);
+        }
     }
 }
 
 // d = Qh^H lo on the tensor cores, C += d.  One block per SM (persistent over
-// tiles), warp-specialised around a ring of LP_NBUF stage buffers (A pieces,
-// then B pieces):
-//   warps 0-7 (producers) convert the lo values of stage s (loaded into
-//     registers LP_AHEAD stages earlier) into the B pieces of buffer s % LP_NBUF
-//     once the MMAs of stage s - LP_NBUF are done, then arrive on bfull;
-//   warp 8, lane 0 waits for the A bytes (afull) and the B pieces (bfull) of
-//     stage s, issues its MMAs, commits them to done, and bulk-copies the A
-//     pieces of stage s + LP_NBUF - 1 into the buffer of stage s - 1 once the
-//     MMAs of stage s - 1 are done;
-//   warps 0-3 (TMEM lanes 0-127) run the epilogue of each tile.
+// tiles of LT_M rows by nt columns), warp-specialised around a ring of
+// LP_NBUF stage buffers (A pieces, then B pieces), one mbarrier pair per
+// buffer:
+//   warps 0-15 (producers), for stage s: issue the lo loads of stage
+//     s + LP_AHEAD into the register set freed by stage s - 1; wait (one lane
+//     per warp) until the MMAs of stage s - LP_NBUF are done (done); convert
+//     the lo values into the B pieces, fence them for the tensor core and
+//     arrive on bfull (one arrive per warp);
+//   warp 17, lane 0, for stage s: waits for the same done, arrives on bfull
+//     announcing the A bytes (so the phase needs them) and bulk-copies the
+//     A pieces of stage s into the buffer;
+//   warp 16, lane 0 waits for bfull of stage s (17 arrivals and the A bytes),
+//     issues the stage's MMAs and commits them to done;
+//   warps 0-15 run the epilogue of each tile (TMEM lanes 32 (w % 4) .., the
+//     column quarter w / 4).
 // Barrier phases follow a running stage count g over all tiles of the block:
-// buffer g % LP_NBUF, phase (g / LP_NBUF) & 1.  No role can run a full ring
-// ahead of another (each refill waits for the MMAs that emptied the buffer),
-// so no wait can be two phases behind.
-constexpr int LP_NBUF = 4;
-constexpr int LP_AHEAD = 4;                    // stages of lo loaded ahead into registers
-constexpr int LP_PRODUCERS = kThreads;         // 256 converting threads
-constexpr int LP_THREADS = kThreads + 32;      // + the MMA warp
+// buffer g % LP_NBUF, phase (g / LP_NBUF) & 1.  The producers refill a buffer
+// only after its MMAs are done and the MMAs of a stage need its bfull, so no
+// role runs a full ring ahead of the other and no wait is two phases behind.
+// Every wait is bounded (p.wait_cycles); a wait that runs out marks the block
+// bad, which skips the epilogue and the later tiles and sets *err.
+constexpr int LP_NBUF = 3;
+constexpr int LP_SETS = 2;                     // register sets of lo stages per producer lane
+constexpr int LP_AHEAD = LP_SETS - 1;          // stages of lo loaded ahead into registers
+constexpr int LP_PRODUCERS = 32 * LP_PWARPS;   // 512 converting threads
+constexpr int LP_THREADS = LP_PRODUCERS + 64;  // + the MMA warp + the A-copy warp
 
-__global__ void __launch_bounds__(LP_THREADS) k_lo_project_tc(Prob p, int *err) {
+__global__ void __launch_bounds__(LP_THREADS, 1) k_lo_project_tc(Prob p, int nt, int *err) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop) || !ld_volatile(&st->switch_pending)) return;
     const int k1 = st->k;
-    const int nrt = (2 * k1 + PT - 1) / PT;
-    const long long nct = (p.M + PT - 1) / PT;
+    const int nrt = (2 * k1 + LT_M - 1) / LT_M;
+    const long long nct = (p.M + nt - 1) / nt;
     const long long ntiles = (long long)nrt * nct;
     if (k1 <= 0 || (long long)blockIdx.x >= ntiles) return;
     extern __shared__ __align__(1024) uint8_t dsm[];
-    __shared__ __align__(8) uint64_t afull[LP_NBUF], bfull[LP_NBUF], done[LP_NBUF];
+    __shared__ __align__(8) uint64_t bfull[LP_NBUF], done[LP_NBUF];
     __shared__ uint32_t tslot;
     __shared__ int s_bad;
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = threadIdx.x < LP_PRODUCERS;
-    const bool issuer = threadIdx.x == LP_PRODUCERS;  // lane 0 of warp 8
-    if (warp == 0) tmem_alloc(&tslot, PT);
+    const bool issuer = threadIdx.x == LP_PRODUCERS;  // lane 0 of warp 16
+    if (warp == 0) tmem_alloc(&tslot, LT_NMAX);
     if (threadIdx.x == 0) {
         s_bad = 0;
         for (int b = 0; b < LP_NBUF; b++) {
-            mbar_init(&afull[b], 1);
-            mbar_init(&bfull[b], LP_PRODUCERS);  // one arrive per producer thread
+            mbar_init(&bfull[b], LP_PWARPS + 1);  // one arrive per producer warp, one with the A bytes
             mbar_init(&done[b], 1);
         }
     }
@@ -771,100 +876,118 @@ __global__ void __launch_bounds__(LP_THREADS) k_lo_project_tc(Prob p, int *err) 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
-    constexpr uint32_t idesc = idesc_bf16_f32(PT, PT);
-    const long long nstg = (2 * p.N + PKC - 1) / PKC;
+    // kind::f16 with FP16 A and B (format 0), FP32 accumulator, K-major
+    const uint32_t idesc = (1u << 4) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(LT_M >> 4) << 24);
+    const long long nstg = (2 * p.N + LKC - 1) / LKC;
     bool ok = true;
     long long gs = 0;  // stages run by this block so far (all tiles)
-    auto bufA = [&](long long g) { return dsm + (int)(g % LP_NBUF) * 2 * PTILE; };
+    auto buf = [&](long long g) { return dsm + (int)(g % LP_NBUF) * LSTAGE; };
     auto par = [&](long long g) { return (uint32_t)((g / LP_NBUF) & 1); };
-    float4 bx0[PBU], by0[PBU], bx1[PBU], by1[PBU], bx2[PBU], by2[PBU], bx3[PBU], by3[PBU];
+    LpRegs R[LP_SETS];  // (warp 16 does not use them)
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int rt = (int)(tile % nrt);
-        const long long j0 = (tile / nrt) * PT;
-        const uint8_t *ga = p.apieces + (long long)rt * nstg * PTILE;
+        const long long j0 = (tile / nrt) * nt;
+        const uint8_t *ga = p.apieces + (long long)rt * nstg * LA_STAGE;
         const long long g0 = gs;
         if (producer) {
-            // register sets: stage s uses set s % 4
-            proj_load_b(p, j0, 0, bx0, by0);
-            if (nstg > 1) proj_load_b(p, j0, 1, bx1, by1);
-            if (nstg > 2) proj_load_b(p, j0, 2, bx2, by2);
-            if (nstg > 3) proj_load_b(p, j0, 3, bx3, by3);
-            auto produce = [&](long long s, float4 (&BX)[PBU], float4 (&BY)[PBU]) {
+            LpTile T;
+            lp_tile(p, j0, nt, T);
+            const long long nfull = p.N / (LKC / 2);
+#pragma unroll
+            for (int a = 0; a < LP_AHEAD; a++)
+                if (a < nstg) lp_load(p, T, a, nfull, R[a]);
+            auto produce = [&](long long s, const LpRegs &Rc, LpRegs &Rn) {
+                if (s + LP_AHEAD < nstg) lp_load(p, T, s + LP_AHEAD, nfull, Rn);
                 const long long g = g0 + s;
-                if (g >= LP_NBUF) ok = mbar_wait(&done[g % LP_NBUF], par(g - LP_NBUF), p.wait_cycles) && ok;
-                proj_store_b(bufA(g) + PTILE, BX, BY);
-                if (s + LP_AHEAD < nstg) proj_load_b(p, j0, s + LP_AHEAD, BX, BY);
+                uint64_t *fb = &bfull[g % LP_NBUF];
+                if (g >= LP_NBUF) {
+                    // one lane polls; __syncwarp orders the warp's stores after it
+                    bool wok = true;
+                    if (lane == 0) wok = mbar_wait(&done[g % LP_NBUF], par(g - LP_NBUF), p.wait_cycles);
+                    wok = __shfl_sync(0xffffffffu, wok ? 1 : 0, 0) != 0;
+                    __syncwarp();
+                    ok = ok && wok;
+                }
+                lp_store(nt, T, Rc, buf(g) + LA_STAGE);
                 // each thread makes its own stores visible to the tensor core
-                // (async proxy), then arrives
+                // (async proxy); after the warp's, lane 0 arrives for it
                 fence_async_smem();
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[g % LP_NBUF])) : "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(fb)) : "memory");
             };
-            for (long long s = 0; s < nstg; s += 4) {
-                produce(s, bx0, by0);
-                if (s + 1 < nstg) produce(s + 1, bx1, by1);
-                if (s + 2 < nstg) produce(s + 2, bx2, by2);
-                if (s + 3 < nstg) produce(s + 3, bx3, by3);
+            for (long long s = 0; s < nstg; s += LP_SETS) {
+#pragma unroll
+                for (int a = 0; a < LP_SETS; a++)
+                    if (s + a < nstg) produce(s + a, R[a], R[(a + LP_AHEAD) % LP_SETS]);
+            }
+        } else if (threadIdx.x == LP_PRODUCERS + 32) {
+            // lane 0 of warp 17: the A pieces of every stage, into a buffer
+            // whose MMAs are done, announced on its bfull
+            for (long long s = 0; s < nstg; s++) {
+                const long long g = g0 + s;
+                uint64_t *fb = &bfull[g % LP_NBUF];
+                if (g >= LP_NBUF) ok = mbar_wait(&done[g % LP_NBUF], par(g - LP_NBUF), p.wait_cycles) && ok;
+                // arrive and announce the bytes in one step, before the copy:
+                // the phase cannot complete without them
+                mbar_expect_tx(fb, LA_STAGE);
+                bulk_g2s(buf(g), ga + s * LA_STAGE, LA_STAGE, fb);
             }
         } else if (issuer) {
-            auto load_a = [&](long long s) {
-                uint64_t *fb = &afull[(g0 + s) % LP_NBUF];
-                mbar_expect_tx(fb, PTILE);
-                bulk_g2s(bufA(g0 + s), ga + s * PTILE, PTILE, fb);
-            };
-            // the first LP_NBUF - 1 stages: their buffers' MMAs (previous tile)
-            // are complete
-            for (long long s = 0; s < LP_NBUF - 1 && s < nstg; s++) load_a(s);
             for (long long s = 0; s < nstg; s++) {
                 const long long g = g0 + s;
                 const int b = (int)(g % LP_NBUF);
-                ok = mbar_wait(&afull[b], par(g), p.wait_cycles) && ok;
                 ok = mbar_wait(&bfull[b], par(g), p.wait_cycles) && ok;
                 tc_fence_after();
-                const uint64_t ad0 = smem_desc(smem_u32(bufA(g)), 128, (PKC / 8) * 128);
-                const uint64_t bd0 = smem_desc(smem_u32(bufA(g) + PTILE), 128, (PKC / 8) * 128);
-                bool first = true;
+                const uint32_t sa = smem_u32(buf(g)), sb = sa + LA_STAGE;
 #pragma unroll
-                for (int sa = 0; sa < PSL; sa++)
-#pragma unroll
-                    for (int sb = 0; sb < PSL; sb++) {
-                        if (sa + sb > 2) continue;  // pieces s + t <= 4 (0-based sa + sb <= 2)
-#pragma unroll
-                        for (int kk = 0; kk < PKC / 16; kk++) {
-                            const uint64_t ad = ad0 + (uint64_t)((sa * (PT * PKC * 2) + kk * 256) >> 4);
-                            const uint64_t bd = bd0 + (uint64_t)((sb * (PT * PKC * 2) + kk * 256) >> 4);
-                            tc_mma_bf16(tmem, ad, bd, idesc, (s > 0 || !first) ? 1u : 0u);
-                            first = false;
-                        }
-                    }
-                tc_commit(&done[b]);
-                // A of stage s + LP_NBUF - 1 into the buffer of stage s - 1
-                if (s + LP_NBUF - 1 < nstg) {
-                    if (s >= 1) ok = mbar_wait(&done[(g - 1) % LP_NBUF], par(g - 1), p.wait_cycles) && ok;
-                    load_a(s + LP_NBUF - 1);
+                for (int kk = 0; kk < LKC / 16; kk++) {
+                    // K step kk: two core matrices along K
+                    const uint64_t ah = smem_desc(sa + kk * 256, 128, (LKC / 8) * 128);
+                    const uint64_t al = smem_desc(sa + LA_PIECE + kk * 256, 128, (LKC / 8) * 128);
+                    const uint64_t bh = smem_desc(sb + kk * 2 * LB_LBO, LB_LBO, LB_SBO);
+                    const uint64_t bl = smem_desc(sb + LB_LO + kk * 2 * LB_LBO, LB_LBO, LB_SBO);
+                    tc_mma_bf16(tmem, ah, bh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                    tc_mma_bf16(tmem, ah, bl, idesc, 1u);
+                    tc_mma_bf16(tmem, al, bh, idesc, 1u);
                 }
+                tc_commit(&done[b]);
             }
         }
+        // the other lanes of the MMA and A-copy warps wait here, converged,
+        // while their lane 0 works
+        if (warp >= LP_PWARPS) __syncwarp();
         gs = g0 + nstg;
         // every thread: the tile's last MMAs (the latest phase of that barrier)
         ok = mbar_wait(&done[(gs - 1) % LP_NBUF], par(gs - 1), p.wait_cycles) && ok;
+        if (!ok) s_bad = 1;
+        __syncthreads();
         tc_fence_after();
-        // epilogue: thread = A row (TMEM lane); row 2l adds to Re C[l, j], row 2l+1 to Im
-        if (warp < 4) {
-            const int r = rt * PT + threadIdx.x;
-            for (int c0 = 0; c0 < PT; c0 += 16) {
+        // epilogue: thread = A row (TMEM lane); row 2l adds to Re C[l, j], row
+        // 2l+1 to Im; warp w reads TMEM lanes 32 (w % 4) .. for the column
+        // quarter w / 4
+        if (warp < LP_PWARPS && !s_bad) {
+            const int r = rt * LT_M + 32 * (warp & 3) + lane;
+            const int qw = ((nt >> 2) + 15) & ~15;
+            const int c_lo = qw * (warp >> 2);
+            const int c_hi = c_lo + qw < nt ? c_lo + qw : nt;
+            const int sa_l = r < 2 * k1 ? p.qscale[r >> 1] : 0;
+            for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-                if (r < 2 * k1 && ok) {
+                tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, v);
+                if (r < 2 * k1) {
                     double *crow = (double *)(p.C + (long long)(r >> 1) * p.ldC) + (r & 1);
 #pragma unroll
                     for (int e = 0; e < 16; e++) {
                         const long long j = j0 + c0 + e;
-                        if (j < p.M) crow[2 * j] += (double)v[e];
+                        if (c0 + e < c_hi && j < p.M) {
+                            const int sc = sa_l + lp_scale_exp(p.lonrm[j]);
+                            const double f = __longlong_as_double((long long)(1023 - sc) << 52);
+                            crow[2 * j] += (double)v[e] * f;
+                        }
                     }
                 }
             }
         }
-        if (!ok) s_bad = 1;
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
@@ -872,7 +995,7 @@ __global__ void __launch_bounds__(LP_THREADS) k_lo_project_tc(Prob p, int *err) 
     }
     if (s_bad && threadIdx.x == 0) atomicExch(err, 1);
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, PT);
+    if (warp == 0) tmem_dealloc(tmem, LT_NMAX);
 }
 
 // acc_j = sum_l |C[l, j]|^2 after the projection onto lo, the final argmax and
@@ -959,28 +1082,47 @@ cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int 
 // Queued after every iteration; both kernels return at once unless the loop
 // has just ended.
 size_t lo_pieces_bytes(long long N, int kcap) {
-    const long long nrt = (2LL * kcap + PT - 1) / PT, nstg = (2 * N + PKC - 1) / PKC;
-    return (size_t)nrt * (size_t)nstg * PTILE;
+    const long long nrt = (2LL * kcap + LT_M - 1) / LT_M, nstg = (2 * N + LKC - 1) / LKC;
+    return (size_t)nrt * (size_t)nstg * LA_STAGE;
+}
+
+// Column tile width of the projection onto lo: a multiple of 16 in [32, 256]
+// that minimises (waves of tiles over the SMs) x (tile width + a per-tile
+// overhead), so the last wave is not mostly empty.
+static int lp_tile_width(long long M, int sms) {
+    int best = LT_NMAX;
+    double best_cost = 1e300;
+    for (int nt = LT_NMAX; nt >= 32; nt -= 16) {
+        const long long tiles = (M + nt - 1) / nt;
+        const long long waves = (tiles + sms - 1) / sms;
+        const double cost = (double)waves * (nt + 24);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = nt;
+        }
+    }
+    return best;
 }
 
 cudaError_t launch_split_finish(const Prob &p, int grid, cudaStream_t s, int *nlaunch) {
-    const size_t dsmem = (size_t)LP_NBUF * 2 * PTILE;  // 192 KB
-    static int g_proj = 0;
-    if (!g_proj) {
+    const size_t dsmem = (size_t)LP_NBUF * LSTAGE;  // 204 KB (3 x 68 KB)
+    static int sms = 0;
+    if (!sms) {
         cudaFuncSetAttribute(k_lo_project_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
         cudaFuncSetAttribute(k_lo_project_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        // one block per SM (144 KB ring)
-        int dev = 0, sms = 152;
+        // one block per SM
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g_proj = sms;
     }
+    const int nt = lp_tile_width(p.M, sms);
+    k_qscale<<<256, kThreads, 0, s>>>(p);
     k_qpieces<<<grid, kThreads, 0, s>>>(p);
-    k_lo_project_tc<<<g_proj, LP_THREADS, dsmem, s>>>(p, p.tc_err);
+    k_lo_project_tc<<<sms, LP_THREADS, dsmem, s>>>(p, nt, p.tc_err);
     long long rf = (p.M + kThreads - 1) / kThreads;
     if (rf > grid) rf = grid;
     k_rebase_finish<<<(int)rf, kThreads, 0, s>>>(p);
-    if (nlaunch) *nlaunch += 3;
+    if (nlaunch) *nlaunch += 4;
     return cudaGetLastError();
 }
 

@@ -14,7 +14,7 @@ be the GPU pivot wherever the top-two gap is clear, otherwise the GPU pivot's
 exact error lies within the FP64 bookkeeping margin of the max.  Error curve,
 final errors (all M), basis and coefficients (all k x M) are then compared
 with the tolerances of the other parity tests; the split form adds its
-stated C bound 2^-48 sqrt(N) ||s_j||.  The measured deviations are printed
+stated C bound (2^-48 sqrt(N) + 2^-42) ||s_j||.  The measured deviations are printed
 (run pytest with -s to see them).
 
 Host memory: S is held once on the host (34 GB and 51.5 GB).
@@ -174,7 +174,7 @@ def test_config3_split_form_full_size_oracle_replay(orc, rbm, cfg3):
     torch.cuda.empty_cache()
     assert g["status"] == 0 and g["switch_iter"] == g["k"]
     rep = parity.replay_and_check(orc, cfg3["S"], g, tol, kmax, omp=True)
-    info = parity.compare(g, rep, cfg3["S"], c_rel=2.0 ** -48 * np.sqrt(N), norms=cfg3["norms"])
+    info = parity.compare(g, rep, cfg3["S"], c_rel=2.0 ** -48 * np.sqrt(N) + 2.0 ** -42, norms=cfg3["norms"])
     k = rep["k"]
     info["max_dC_over_norm"] = float(np.max(np.abs(g["C"][:k] - rep["C"]) / cfg3["norms"][None, :]))
     own = _cfg3_unforced(orc, cfg3)

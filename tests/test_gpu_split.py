@@ -27,8 +27,10 @@ def npy(d):
 def c_rel(N):
     """The split form's stated C tolerance relative to ||s_j||: a quarter of
     the sweep bound eta = 2^-46 sqrt(N) (measured errors stay below 2^-42.4
-    at N = 16384, i.e. about eta / 10)."""
-    return 2.0 ** -48 * np.sqrt(N)
+    at N = 16384, i.e. about eta / 10), plus 2^-42 for the FP16 pieces of the
+    projection onto lo (at most 2^-18.4 relative per product of |q| |lo|,
+    |lo| <= 2^-24 |s|)."""
+    return 2.0 ** -48 * np.sqrt(N) + 2.0 ** -42
 
 
 def split_upload(orc, S, ld=None):
