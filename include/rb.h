@@ -332,6 +332,50 @@ rb_status rb_greedy_streamed(rb_ctx *ctx, const void *S, long long N, long long 
  * pointer may be NULL.  Errors: RB_EINVAL. */
 rb_status rb_streamed_stats(const rb_ctx *ctx, long long *counts, double *host_bytes, double *ms_init);
 
+/* ---------------------------------------------------------------------------
+ * One rank's part of the column-sharded greedy: the paper's parallel scheme
+ * (Sec. 6.1.4, Sec. 6.2).  Rank r owns columns col0 .. col0 + M - 1 of the
+ * global snapshot matrix; per iteration the ranks reduce their local
+ * candidates (error, global index) to the global pivot with a max-loc (ties
+ * to the lowest global index), the owner sends the pivot column, and every
+ * rank orthogonalises it against its own copy of the basis with the same
+ * deterministic kernels, so all ranks hold bit-identical bases.  The
+ * exchange and the stopping rule (max error < tol, k = kmax, k = min(N, M_total))
+ * belong to the caller (paper_1805_06124_gb300/sharded.py drives them over
+ * torch.distributed).  Arithmetic as rb_greedy with RB_SWEEP_DF32: the
+ * ranks' local sweeps are the in-core sweep on their columns.
+ * ------------------------------------------------------------------------- */
+typedef struct rb_shard rb_shard;
+
+/* S: this rank's columns (device complex128, N x M column-major, ldS >= N),
+ * global indices col0 ..; out: Q (N x kmax, every rank), pivots (kmax,
+ * global indices), optional C (kmax x M, this rank's columns; needed for the
+ * periodic recompute, off without it) and rdiag; err_curve is the caller's.
+ * The shard keeps pointers to S and *out's arrays.  Errors: RB_EINVAL,
+ * RB_ENOMEM. */
+rb_status rb_shard_create(rb_ctx *ctx, const void *S, long long N, long long M, long long ldS, long long col0,
+                          int kmax, rb_result *out, rb_shard **sh);
+void rb_shard_destroy(rb_shard *sh);
+/* Norms (Alg. 3 before the loop) and the local candidate: *best_err = the
+ * largest ||s_j||^2 of the rank's columns, *best_idx its global index (-1:
+ * none).  Returns RB_ENONFINITE for NaN/Inf in S. */
+rb_status rb_shard_init(rb_shard *sh, double *best_err, long long *best_idx);
+/* The owner's side of the send: column j (global index, owned by this rank)
+ * copied to dst (device, N complex128, 16-byte aligned) and its stored norm
+ * ||s_j||^2 to *norm2 (host).  Synchronises the stream. */
+rb_status rb_shard_column(rb_shard *sh, long long j, void *dst, double *norm2);
+/* Every rank: IMGS of the received pivot column v (device, N complex128) with
+ * norm2 from its owner against the current basis (MGSCI, Sec. 6.1.2), the new
+ * basis vector appended (pivots[k] = j), then the sweep of this rank's
+ * columns; returns the next local candidate.  *appended = 0 when v lay in the
+ * span of the basis (exact rank: the caller stops).  Errors: RB_EORTHO,
+ * RB_EINVAL (kmax vectors built, bad arguments), RB_ECUDA. */
+rb_status rb_shard_append(rb_shard *sh, const void *v, double norm2, long long j, double *best_err,
+                          long long *best_idx, int *appended);
+/* final_err (device, M doubles, optional): err_j of this rank's columns; *k:
+ * vectors built. */
+rb_status rb_shard_finish(rb_shard *sh, double *final_err, int *k);
+
 /* Projection onto a basis: C[l*ldC + j] = q_l^H x_j for l < k, j < Mx
  * (Sec. 2: a column is represented by its orthogonal projection onto the
  * span of the basis).  Q: complex128 N x k (ldQ >= N); X: complex128 N x Mx

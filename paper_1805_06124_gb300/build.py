@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "librb_gb300.so")
-SOURCES = ["rb_init.cu", "rb_sweep.cu", "rb_imgs.cu", "rb_project.cu", "rb_api.cu", "rb_noalloc.cu", "rb_split_form.cu", "rb_mlp.cu", "rb_batched.cu", "rb_ozaki.cu", "rb_recon.cu", "rb_eim.cu", "rb_stream.cu"]
+SOURCES = ["rb_init.cu", "rb_sweep.cu", "rb_imgs.cu", "rb_project.cu", "rb_api.cu", "rb_noalloc.cu", "rb_split_form.cu", "rb_mlp.cu", "rb_batched.cu", "rb_ozaki.cu", "rb_recon.cu", "rb_eim.cu", "rb_stream.cu", "rb_shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

@@ -119,6 +119,9 @@ int ctx_device(rb_ctx *ctx) { return ctx->device; }
 unsigned long long ctx_wait_cycles(const rb_ctx *ctx) {
     return ctx->opt.timeout_cycles ? ctx->opt.timeout_cycles : kWaitCyclesDefault;
 }
+const rb_options &ctx_options(const rb_ctx *ctx) { return ctx->opt; }
+int ctx_sweep_grid(rb_ctx *ctx, int variant) { return grid_for_variant(ctx, variant); }
+rb_status ctx_fail(rb_ctx *ctx, rb_status s, const char *msg) { return fail(ctx, s, "%s", msg); }
 }  // namespace rbk
 
 extern "C" {

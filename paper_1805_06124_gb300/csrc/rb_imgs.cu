@@ -198,6 +198,18 @@ cudaError_t launch_imgs(const Prob &p, int grid, bool from_split, cudaStream_t s
     return cudaGetLastError();
 }
 
+// The (dot, update) pass pairs alone, for a caller that prepares p.v and the
+// state itself (the column-sharded greedy).
+cudaError_t launch_imgs_passes(const Prob &p, int grid, cudaStream_t s, int *nlaunch) {
+    const int gN = (int)((p.N + kThreads - 1) / kThreads);
+    for (int pass = 0; pass < p.max_passes; pass++) {
+        k_imgs_dot<<<grid, kThreads, 0, s>>>(p);
+        k_imgs_update<<<gN, kThreads, 0, s>>>(p);
+    }
+    if (nlaunch) *nlaunch += 2 * p.max_passes;
+    return cudaGetLastError();
+}
+
 // The same steps for nprob problems at once (complex128 input): grid.y is the
 // problem, grid.x is sized for the largest N (smaller problems leave the extra
 // blocks idle; every problem's npart must hold gridDim.x entries).

@@ -539,4 +539,8 @@ cudaError_t launch_breduce(const BProb *P, int nprob, const long long *chunk0, c
 cudaStream_t ctx_stream(rb_ctx *ctx);
 int ctx_device(rb_ctx *ctx);
 unsigned long long ctx_wait_cycles(const rb_ctx *ctx);  // rb_options.timeout_cycles, 0 -> the default
+const rb_options &ctx_options(const rb_ctx *ctx);
+int ctx_sweep_grid(rb_ctx *ctx, int variant);             // cached grid of the FP64-form sweep
+rb_status ctx_fail(rb_ctx *ctx, rb_status s, const char *msg);  // records msg for rb_last_error
+cudaError_t launch_imgs_passes(const Prob &p, int grid, cudaStream_t s, int *nlaunch);
 }  // namespace rbk

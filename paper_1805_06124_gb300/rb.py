@@ -102,8 +102,18 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.rb_greedy_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(Problem), c_double, c_int,
                                       ctypes.POINTER(Result)]
     lib.rb_greedy_batched.restype = c_int
+    lib.rb_shard_create.argtypes = [c_void_p, c_void_p, c_ll, c_ll, c_ll, c_ll, c_int, ctypes.POINTER(Result),
+                                    ctypes.POINTER(c_void_p)]
+    lib.rb_shard_destroy.argtypes = [c_void_p]
+    lib.rb_shard_destroy.restype = None
+    lib.rb_shard_init.argtypes = [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_ll)]
+    lib.rb_shard_column.argtypes = [c_void_p, c_ll, c_void_p, ctypes.POINTER(c_double)]
+    lib.rb_shard_append.argtypes = [c_void_p, c_void_p, c_double, c_ll, ctypes.POINTER(c_double),
+                                    ctypes.POINTER(c_ll), ctypes.POINTER(c_int)]
+    lib.rb_shard_finish.argtypes = [c_void_p, c_void_p, ctypes.POINTER(c_int)]
     for f in ("rb_generate", "rb_split", "rb_greedy", "rb_greedy_host", "rb_greedy_split", "rb_project",
-              "rb_reconstruct", "rb_reconstruct_stats", "rb_eim", "rb_validate", "rb_greedy_resume", "rb_trace"):
+              "rb_reconstruct", "rb_reconstruct_stats", "rb_eim", "rb_validate", "rb_greedy_resume", "rb_trace",
+              "rb_shard_create", "rb_shard_init", "rb_shard_column", "rb_shard_append", "rb_shard_finish"):
         getattr(lib, f).restype = c_int
     _LIB = lib
     return lib
@@ -518,6 +528,74 @@ class RB:
         cnt = (c_int * 4)()
         self._check(self.lib.rb_reconstruct_stats(self._h, ms, cnt))
         return dict(ms=dict(zip(self.RECON_PHASES, list(ms))), sweeps=(cnt[0], cnt[2]), rotations=(cnt[1], cnt[3]))
+
+
+class Shard:
+    """One rank's columns of the column-sharded greedy (rb_shard_*): the
+    engine that paper_1805_06124_gb300.sharded drives.  S: this rank's
+    snapshots, a CUDA complex128 (M, N) tensor; col0: the global index of its
+    first column.  The buffers exchanged between ranks are (N + 1,) complex128
+    CUDA tensors: the pivot column, then its stored norm in the real part of
+    the last entry."""
+
+    def __init__(self, ctx: "RB", S, col0: int, kmax: int, want_C: bool = True):
+        torch = _torch()
+        _check2d(S, torch.complex128, "S")
+        self.ctx, self.lib, self.S = ctx, ctx.lib, S
+        self.M, self.N = S.shape
+        self.col0, self.kmax = int(col0), int(kmax)
+        with torch.cuda.stream(ctx.stream):
+            self._r, self._bufs = ctx._alloc_result(self.N, self.M, kmax, S.device, want_C, True)
+        h = c_void_p()
+        ctx._check(self.lib.rb_shard_create(ctx._h, S.data_ptr(), self.N, self.M, _ld(S), self.col0, self.kmax,
+                                            ctypes.byref(self._r), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.rb_shard_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_buffer(self):
+        torch = _torch()
+        return torch.zeros((self.N + 1,), dtype=torch.complex128, device=self.S.device)
+
+    def init(self):
+        e, j = c_double(), c_ll()
+        self.ctx._check(self.lib.rb_shard_init(self._h, ctypes.byref(e), ctypes.byref(j)))
+        return e.value, j.value
+
+    def column(self, j: int, buf):
+        """Column j (owned here) into buf[:N], its norm into buf[N]."""
+        n2 = c_double()
+        self.ctx._check(self.lib.rb_shard_column(self._h, int(j), buf.data_ptr(), ctypes.byref(n2)))
+        buf[self.N] = complex(n2.value, 0.0)
+        return n2.value
+
+    def append(self, buf, j: int):
+        """IMGS of the received pivot column (buf from the owner) and the sweep
+        of this rank's columns; returns (best_err, best_idx, appended)."""
+        n2 = float(buf[self.N].real.item())
+        e, jj, app = c_double(), c_ll(), c_int()
+        self.ctx._check(self.lib.rb_shard_append(self._h, buf.data_ptr(), n2, int(j), ctypes.byref(e),
+                                                 ctypes.byref(jj), ctypes.byref(app)))
+        return e.value, jj.value, bool(app.value)
+
+    def finish(self):
+        k = c_int()
+        st = self.lib.rb_shard_finish(self._h, self._bufs["final_err"].data_ptr(), ctypes.byref(k))
+        k = k.value
+        out = dict(status=st, k=k, Q=self._bufs["Q"][:k], pivots=self._bufs["pivots"][:k], rdiag=self._bufs["rdiag"][:k],
+                   final_err=self._bufs["final_err"])
+        if "C" in self._bufs:
+            out["C"] = self._bufs["C"][:k]
+        return out
 
 
 class MLP:
