@@ -298,10 +298,11 @@ def batched_run(torch, rb, synth, dev, stream, nprob=96, seed=3, tol=1e-10, reps
             "k_min": min(ks), "k_max": max(ks), "gpu_launches": outs[0]["n_launches"]}
 
 
-def run_surrogate(args):
-    """Learned surrogate: greedy on N=8192 x M=131072 chirps (seed 4, tol 1e-10),
-    MLP on its C, 16384 held-out (seed 5) judged by exact projection."""
-    import numpy as np
+def surrogate_run(epochs=400, lr=3e-3, mode="fourier-split"):
+    """Learned surrogate (config 5): greedy on N=8192 x M=131072 chirps (seed 4,
+    tol 1e-10), MLP on its C, 16384 held-out (seed 5) judged by exact
+    projection Q^H s; the non-learned baseline is the coefficient vector of
+    the training snapshot nearest in omega."""
     import torch
     from paper_1805_06124_gb300 import rb, surrogate, synth
     N, M, Mt = 8192, 131072, 16384
@@ -312,12 +313,14 @@ def run_surrogate(args):
     with torch.cuda.stream(stream):
         S = c.generate(q, m, N)
         g = c.greedy(S, 1e-10, 800)
-        St = c.generate(qt, mt, N)
     stream.synchronize()
     k = g["k"]
     del S
-    net, curve, t_train = surrogate.train(c, q, m, g["C"], epochs=args.epochs, batch=1024, lr=1e-3, seed=4)
-    Xt = surrogate.scale_inputs(qt, mt).cuda()
+    fourier = surrogate.chirp_tau_band(N) if mode in ("fourier", "fourier-split") else None
+    split = mode in ("split", "fourier-split")
+    net, curve, t_train = surrogate.train(c, q, m, g["C"], epochs=epochs, batch=1024, lr=lr, seed=4,
+                                          fourier=fourier, split=split)
+    Xt = surrogate.inputs(net, qt, mt).cuda()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         Y = net.infer(Xt)
@@ -336,28 +339,30 @@ def run_surrogate(args):
     t_exact = ev0.elapsed_time(ev1)
     Tt = surrogate.targets_from_C(Ct)
     rel_e, abs_e = surrogate.relative_errors(Y, Tt)
-    # non-learned baseline: coefficients of the training snapshot nearest in omega
-    om = torch.as_tensor(synth.chirp_omega(q, m), device="cuda")
-    omt = torch.as_tensor(synth.chirp_omega(qt, mt), device="cuda")
-    order = torch.argsort(om)
-    pos = torch.searchsorted(om[order], omt).clamp(1, M - 1)
-    left, right = order[pos - 1], order[pos]
-    nn = torch.where((omt - om[left]).abs() <= (om[right] - omt).abs(), left, right)
+    nn = surrogate.nearest_in_omega(q, m, qt, mt)
     Ttrain = surrogate.targets_from_C(g["C"])
     rel_nn, _ = surrogate.relative_errors(Ttrain[nn], Tt)
-    line = {"impl": "ours", "metric": "surrogate coefficient relative error vs exact projection (median)",
-            "value": round(surrogate.summarize(rel_e)["median"], 5), "unit": "relative L2",
-            "higher_is_better": False, "data": "synthetic", "dtype": "bf16/f32",
-            "config": {"workload": f"MLP 2-256-256-256-{2 * k}, {M} training pairs from greedy on N={N} x M={M} "
-                                   f"chirps (seed 4, tol 1e-10, k={k}), {Mt} held-out (seed 5)",
-                       "epochs": args.epochs, "batch": 1024, "lr": 1e-3},
-            "mlp": surrogate.summarize(rel_e), "mlp_abs_waveform_err": surrogate.summarize(abs_e),
-            "nearest_training_column": surrogate.summarize(rel_nn), "zero_prediction": 1.0,
-            "final_train_loss": float(curve[-1]), "train_s": round(t_train, 2),
-            "infer_ms_per_16384": round(t_mlp, 3), "generate_plus_project_ms_per_16384": round(t_exact, 3)}
-    print(json.dumps(line), flush=True)
+    out = {"workload": f"MLP 2-256-256-256-{2 * k}, {M} training pairs from greedy on N={N} x M={M} chirps "
+                       f"(seed 4, tol 1e-10, k={k}), {Mt} held-out (seed 5), judged by exact projection",
+           "mode": mode, "epochs": epochs, "batch": 1024, "lr": lr,
+           "mlp": surrogate.summarize(rel_e), "mlp_abs_waveform_err": surrogate.summarize(abs_e),
+           "nearest_training_column": surrogate.summarize(rel_nn), "zero_prediction": 1.0,
+           "final_train_loss": float(curve[-1]), "train_s": round(t_train, 2),
+           "infer_ms_per_16384": round(t_mlp, 3), "generate_plus_project_ms_per_16384": round(t_exact, 3)}
     net.close()
     c.close()
+    return out
+
+
+def run_surrogate(args):
+    r = surrogate_run(args.epochs, args.lr, args.mlp_mode)
+    line = {"impl": "ours", "metric": "surrogate coefficient relative error vs exact projection (median)",
+            "value": round(r["mlp"]["median"], 7), "unit": "relative L2", "higher_is_better": False,
+            "data": "synthetic", "dtype": "bf16 (split forward) / f32",
+            "config": {"workload": r["workload"], "epochs": r["epochs"], "batch": r["batch"], "lr": r["lr"],
+                       "mode": r["mode"]}}
+    line.update({k: v for k, v in r.items() if k not in ("workload", "epochs", "batch", "lr", "mode")})
+    print(json.dumps(line), flush=True)
 
 
 def run_split_once(args):
@@ -820,7 +825,7 @@ def run_ours(args):
         c64.close()
         del r64
 
-    extra_split = extra_batched = None
+    extra_split = extra_batched = extra_surrogate = None
     if rank == 0 and world == 1:
         ctx.close()
         S = None
@@ -830,6 +835,9 @@ def run_ours(args):
             torch.cuda.empty_cache()
         if not args.no_batched:
             extra_batched = batched_run(torch, rb, synth, local, stream)
+            torch.cuda.empty_cache()
+        if not args.no_surrogate:
+            extra_surrogate = surrogate_run()
             torch.cuda.empty_cache()
 
     if rank == 0:
@@ -854,7 +862,8 @@ def run_ours(args):
                              "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": round(sweep_ms, 4)},
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
                 "cpu_baseline_1thread": cpu_1t, "sweep_fp64": sweep_fp64,
-                "split_vs_fp64": extra_split, "batched": extra_batched, "after_greedy": extra_next}
+                "split_vs_fp64": extra_split, "batched": extra_batched, "surrogate": extra_surrogate,
+                "after_greedy": extra_next}
         print(json.dumps(line), flush=True)
     if not (rank == 0 and world == 1):
         ctx.close()
@@ -875,12 +884,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-next", action="store_true")
     ap.add_argument("--sharded", action="store_true",
                     help="the column-sharded greedy (default when launched on more than one rank)")
     ap.add_argument("--workload", default="greedy", choices=["greedy", "surrogate", "split", "project", "batched",
                                                                 "recon", "eim", "resume", "streamed"])
-    ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--mlp-mode", default="fourier-split", choices=["plain", "split", "fourier", "fourier-split"])
     ap.add_argument("--k", type=int, default=53)
     ap.add_argument("--project-fp64", action="store_true")
     args = ap.parse_args()

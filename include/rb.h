@@ -405,6 +405,22 @@ typedef struct rb_mlp rb_mlp;
  * splitmix64(seed); batch_cap bounds
  * the rows of one rb_mlp_grad call and the chunk of rb_mlp_infer. */
 rb_status rb_mlp_create(rb_ctx *ctx, int n_out, int batch_cap, unsigned long long seed, rb_mlp **out);
+
+/* rb_mlp_create_ex flags */
+#define RB_MLP_FOURIER 1u  /* input rows are the physical (q, m); the first layer is the fixed encoding
+                              h1 = (cos(omega tau_f), sin(omega tau_f)), f < 128, tau_f uniform on
+                              [tau_lo, tau_hi], omega = 200 eta^(-3/8) m^(-5/8), eta = q/(1+q)^2 (the
+                              snapshot family's phase rate; a coefficient c_l = q_l^H s(omega) is a sum of
+                              exp(-i omega tau_i) over the samples, tau_i = (t_c - t_i)^(5/8)); W1 and b1
+                              are unused and their gradient is zero */
+#define RB_MLP_SPLIT 2u    /* forward GEMMs on FP32 activations and master weights, each as BF16
+                              hi + lo pieces, hi*hi + hi*lo + lo*hi accumulated in FP32 (about 16-bit
+                              operands instead of 8-bit); the backward pass stays single BF16 */
+/* As rb_mlp_create with the flags above (tau_lo, tau_hi used with
+ * RB_MLP_FOURIER: 0 <= tau_lo < tau_hi).  Errors: RB_EINVAL, RB_ENOMEM,
+ * RB_ECUDA. */
+rb_status rb_mlp_create_ex(rb_ctx *ctx, int n_out, int batch_cap, unsigned long long seed, unsigned flags,
+                           double tau_lo, double tau_hi, rb_mlp **out);
 void rb_mlp_destroy(rb_mlp *mlp);
 long long rb_mlp_num_params(const rb_mlp *mlp);
 /* dst / src: device FP32, rb_mlp_num_params entries.  set_params also resets

@@ -40,6 +40,9 @@ struct GemmArgs {
     long long ldb;
     const float *zin;    // pre-activation for EPI_GELU_BWD, (m, n) at zin[m*ldz + n]
     long long ldz;
+    float *outh;         // FP32 gelu(z) (EPI_BIAS_GELU) at outh[m*ldo + n], or null
+    const float *Af;     // split form: FP32 A and B (same strides as A, B)
+    const float *Bf;
     int *err;
     unsigned long long wait;  // budget of each mbarrier wait, SM clock cycles
 };
@@ -49,66 +52,100 @@ __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-// Stage rows [r0, r0+GT) x k [k0, k0+GKC) of a strided BF16 matrix into the
+// Stage rows [r0, r0+GT) x k [k0, k0+KC) of a strided BF16 matrix into the
 // K-major tile, zero outside [0, R) x [0, K).
+template <int KC>
 __device__ __forceinline__ void stage_tile(uint8_t *s, const bf16 *X, long long sr, long long sk, int R, int K, int r0,
                                            int k0) {
     const bf16 zero = __float2bfloat16(0.f);
-    if (sr == 1) {  // rows contiguous: consecutive threads take consecutive rows
-        for (int t = threadIdx.x; t < GT * GKC; t += blockDim.x) {
-            int k = t / GT, r = t % GT;
-            int gr = r0 + r, gk = k0 + k;
-            bf16 v = (gr < R && gk < K) ? X[(long long)gr * sr + (long long)gk * sk] : zero;
-            *(bf16 *)(s + kmajor_off(r, k, GKC)) = v;
-        }
-    } else {
-        for (int t = threadIdx.x; t < GT * GKC; t += blockDim.x) {
-            int r = t / GKC, k = t % GKC;
-            int gr = r0 + r, gk = k0 + k;
-            bf16 v = (gr < R && gk < K) ? X[(long long)gr * sr + (long long)gk * sk] : zero;
-            *(bf16 *)(s + kmajor_off(r, k, GKC)) = v;
-        }
+    const bool rows_fast = sr == 1;  // rows contiguous: consecutive threads take consecutive rows
+    for (int t = threadIdx.x; t < GT * KC; t += blockDim.x) {
+        const int r = rows_fast ? t % GT : t / KC, k = rows_fast ? t / GT : t % KC;
+        const int gr = r0 + r, gk = k0 + k;
+        bf16 v = (gr < R && gk < K) ? X[(long long)gr * sr + (long long)gk * sk] : zero;
+        *(bf16 *)(s + kmajor_off(r, k, KC)) = v;
     }
 }
 
-// C[M x N] = A[M x K] * B[N x K]^T on tcgen05, one 128 x 128 tile per block.
+// The same tile from an FP32 matrix as two BF16 pieces: hi = bf16(x) into s,
+// lo = bf16(x - hi) into s + lo_off (x = hi + lo to about 2^-16 |x|).
+template <int KC>
+__device__ __forceinline__ void stage_tile_split(uint8_t *s, int lo_off, const float *X, long long sr, long long sk,
+                                                 int R, int K, int r0, int k0) {
+    const bool rows_fast = sr == 1;
+    for (int t = threadIdx.x; t < GT * KC; t += blockDim.x) {
+        const int r = rows_fast ? t % GT : t / KC, k = rows_fast ? t / GT : t % KC;
+        const int gr = r0 + r, gk = k0 + k;
+        const float x = (gr < R && gk < K) ? X[(long long)gr * sr + (long long)gk * sk] : 0.f;
+        const bf16 hi = __float2bfloat16(x);
+        const bf16 lo = __float2bfloat16(x - __bfloat162float(hi));
+        *(bf16 *)(s + kmajor_off(r, k, KC)) = hi;
+        *(bf16 *)(s + lo_off + kmajor_off(r, k, KC)) = lo;
+    }
+}
+
+// C[M x N] = A[M x K] * B[N x K]^T on tcgen05, one 128 x 128 tile per block,
+// K in stages over a ring of two buffers: the tiles of stage c + 1 are
+// staged while the MMAs of stage c run.  SPLIT: A and B are FP32, each staged
+// as BF16 hi + lo pieces, and hi*hi + hi*lo + lo*hi accumulate (products of
+// about 16-bit operands; the dropped lo*lo is 2^-16 relative).
+template <bool SPLIT>
 __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
-    __shared__ __align__(1024) uint8_t sA[GT * GKC * 2];
-    __shared__ __align__(1024) uint8_t sB[GT * GKC * 2];
-    __shared__ __align__(8) uint64_t mbar;
+    constexpr int KC = SPLIT ? 32 : GKC;     // K per stage
+    constexpr int TILE = GT * KC * 2;         // bytes of one BF16 tile
+    constexpr int STAGE = (SPLIT ? 4 : 2) * TILE;  // A, B (then A lo, B lo)
+    extern __shared__ __align__(1024) uint8_t dsm[];
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5;
     const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
     if (warp == 0) tmem_alloc(&tslot, GT);
-    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
     constexpr uint32_t idesc = idesc_bf16_f32(GT, GT);
-    uint32_t phase = 0;
     bool ok = true;
-    const int nk = (g.K + GKC - 1) / GKC;
+    const int nk = (g.K + KC - 1) / KC;
     for (int c = 0; c < nk; c++) {
-        stage_tile(sA, g.A, g.sam, g.sak, g.M, g.K, m0, c * GKC);
-        stage_tile(sB, g.B, g.sbn, g.sbk, g.N, g.K, n0, c * GKC);
+        const int b = c & 1;
+        uint8_t *sA = dsm + b * STAGE, *sB = sA + TILE;
+        // the MMAs of stage c - 2 (same buffer) must be done before it is refilled
+        if (c >= 2) ok = mbar_wait(&mbar[b], (uint32_t)(((c - 2) >> 1) & 1), g.wait) && ok;
+        if (SPLIT) {
+            stage_tile_split<KC>(sA, 2 * TILE, g.Af, g.sam, g.sak, g.M, g.K, m0, c * KC);
+            stage_tile_split<KC>(sB, 2 * TILE, g.Bf, g.sbn, g.sbk, g.N, g.K, n0, c * KC);
+        } else {
+            stage_tile<KC>(sA, g.A, g.sam, g.sak, g.M, g.K, m0, c * KC);
+            stage_tile<KC>(sB, g.B, g.sbn, g.sbk, g.N, g.K, n0, c * KC);
+        }
         fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
             tc_fence_after();
 #pragma unroll
-            for (int kk = 0; kk < GKC / 16; kk++) {
-                uint64_t ad = smem_desc(smem_u32(sA) + kk * 256, 128, (GKC / 8) * 128);
-                uint64_t bd = smem_desc(smem_u32(sB) + kk * 256, 128, (GKC / 8) * 128);
+            for (int kk = 0; kk < KC / 16; kk++) {
+                const uint64_t ad = smem_desc(smem_u32(sA) + kk * 256, 128, (KC / 8) * 128);
+                const uint64_t bd = smem_desc(smem_u32(sB) + kk * 256, 128, (KC / 8) * 128);
                 tc_mma_bf16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                if (SPLIT) {
+                    const uint64_t adl = smem_desc(smem_u32(sA) + 2 * TILE + kk * 256, 128, (KC / 8) * 128);
+                    const uint64_t bdl = smem_desc(smem_u32(sB) + 2 * TILE + kk * 256, 128, (KC / 8) * 128);
+                    tc_mma_bf16(tmem, ad, bdl, idesc, 1u);
+                    tc_mma_bf16(tmem, adl, bd, idesc, 1u);
+                }
             }
-            tc_commit(&mbar);
+            tc_commit(&mbar[b]);
         }
-        ok = mbar_wait(&mbar, phase, g.wait) && ok;
-        phase ^= 1;
-        tc_fence_after();
-        __syncthreads();
     }
+    // the last commit completes when every MMA of the tile has
+    if (nk > 0) ok = mbar_wait(&mbar[(nk - 1) & 1], (uint32_t)(((nk - 1) >> 1) & 1), g.wait) && ok;
+    tc_fence_after();
+    __syncthreads();
     if (!ok && g.err) atomicExch(g.err, 1);
     // epilogue: thread = one row of the tile (TMEM lane)
     const int m = m0 + threadIdx.x;
@@ -123,8 +160,10 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
                 float x = v[j];
                 if (g.bias) x += g.bias[n];
                 if (g.epi == EPI_BIAS_GELU) {
+                    const float h = gelu(x);
                     g.out[(long long)m * g.ldo + n] = x;
-                    g.outb[(long long)m * g.ldb + n] = __float2bfloat16(gelu(x));
+                    g.outb[(long long)m * g.ldb + n] = __float2bfloat16(h);
+                    if (g.outh) g.outh[(long long)m * g.ldo + n] = h;
                 } else if (g.epi == EPI_GELU_BWD) {
                     float d = x * gelu_grad(g.zin[(long long)m * g.ldz + n]);
                     g.out[(long long)m * g.ldo + n] = d;
@@ -141,10 +180,21 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
     if (warp == 0) tmem_dealloc(tmem, GT);
 }
 
-static cudaError_t gemm(GemmArgs g, unsigned long long wait, cudaStream_t s) {
+// split: FP32 operands in two BF16 pieces (g.Af, g.Bf), three products
+static cudaError_t gemm(GemmArgs g, unsigned long long wait, cudaStream_t s, bool split = false) {
     g.wait = wait;
     dim3 grid((g.M + GT - 1) / GT, (g.N + GT - 1) / GT);
-    k_gemm_bf16<<<grid, 128, 0, s>>>(g);
+    const int smem = split ? 2 * 4 * GT * 32 * 2 : 2 * 2 * GT * GKC * 2;  // 128 KB / 64 KB
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gemm_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4 * GT * 32 * 2);
+        cudaFuncSetAttribute(k_gemm_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 2 * GT * GKC * 2);
+        attr = true;
+    }
+    if (split)
+        k_gemm_bf16<true><<<grid, 128, smem, s>>>(g);
+    else
+        k_gemm_bf16<false><<<grid, 128, smem, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -229,7 +279,8 @@ __global__ void k_gather(const float *X, const float *T, long long n, int O, int
 }
 
 // z1 = x W1^T + b1, h1 = gelu(z1) (W1 rounded to BF16 like the other weights)
-__global__ void k_l1_fwd(const float *X, int B, const bf16 *pb, const float *p, int O, float *z1, bf16 *h1) {
+__global__ void k_l1_fwd(const float *X, int B, const bf16 *pb, const float *p, int O, float *z1, bf16 *h1,
+                         float *h1f) {
     MlpLayout L = mlp_layout(O);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)B * MW;
          t += (long long)gridDim.x * blockDim.x) {
@@ -238,7 +289,37 @@ __global__ void k_l1_fwd(const float *X, int B, const bf16 *pb, const float *p, 
         float w0 = __bfloat162float(pb[L.w1 + i * 2]), w1 = __bfloat162float(pb[L.w1 + i * 2 + 1]);
         float z = fmaf(w0, X[r * 2], fmaf(w1, X[r * 2 + 1], p[L.b1 + i]));
         z1[t] = z;
-        h1[t] = __float2bfloat16(gelu(z));
+        const float h = gelu(z);
+        h1[t] = __float2bfloat16(h);
+        if (h1f) h1f[t] = h;
+    }
+}
+
+// Fourier input layer (RB_MLP_FOURIER): a row is a snapshot's parameters
+// (q, m); omega = 200 eta^(-3/8) m^(-5/8), eta = q / (1 + q)^2 (the chirp
+// family's phase rate) in FP64, and h1[f] = cos(omega tau_f),
+// h1[128 + f] = sin(omega tau_f) for tau_f = tau_lo + f dtau, f < 128.  The
+// phase is reduced modulo 2 pi in FP64, the sine and cosine taken in FP32.
+// The layer has no trained parameters (W1, b1 are unused).
+__global__ void k_l1_fourier(const float *X, int B, double tau_lo, double dtau, bf16 *h1, float *h1f) {
+    constexpr int NF = MW / 2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)B * NF;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / NF;
+        const int f = (int)(t % NF);
+        const double q = X[r * 2], m = X[r * 2 + 1];
+        const double eta = q / ((1.0 + q) * (1.0 + q));
+        const double omega = 200.0 * pow(eta, -0.375) * pow(m, -0.625);
+        const double ph = omega * (tau_lo + dtau * f);
+        const double red = ph - 6.283185307179586 * rint(ph * 0.15915494309189535);
+        float sn, cs;
+        sincosf((float)red, &sn, &cs);
+        h1[r * MW + f] = __float2bfloat16(cs);
+        h1[r * MW + NF + f] = __float2bfloat16(sn);
+        if (h1f) {
+            h1f[r * MW + f] = cs;
+            h1f[r * MW + NF + f] = sn;
+        }
     }
 }
 
@@ -337,6 +418,9 @@ struct rb_mlp {
     StepState *ss = nullptr;
     int *err = nullptr;
     void *block = nullptr;
+    unsigned flags = 0;                    // RB_MLP_FOURIER, RB_MLP_SPLIT
+    double tau_lo = 0.0, dtau = 0.0;       // Fourier input layer
+    float *h1f = nullptr, *h2f = nullptr, *h3f = nullptr;  // FP32 activations (split forward)
     char msg[256] = {0};
 };
 
@@ -345,25 +429,37 @@ namespace {
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
-// forward on rows [0, B) of (X, z/h buffers); y gets B x O
+// forward on rows [0, B) of (X, z/h buffers); y gets B x O.  With
+// RB_MLP_SPLIT the three tensor-core layers take FP32 activations and master
+// weights as BF16 hi + lo pieces (three products per K step).
 cudaError_t forward(rb_mlp *n, const float *X, int B, float *y, cudaStream_t s) {
     const int O = n->O;
     const MlpLayout &L = n->L;
-    int g1 = (int)((B * (long long)MW + 255) / 256);
-    if (g1 > 4096) g1 = 4096;
-    k_l1_fwd<<<g1, 256, 0, s>>>(X, B, n->pb, n->p, O, n->z1, n->h1);
+    const bool split = (n->flags & RB_MLP_SPLIT) != 0;
+    if (n->flags & RB_MLP_FOURIER) {
+        int gf = (int)((B * (long long)(MW / 2) + 255) / 256);
+        if (gf > 4096) gf = 4096;
+        k_l1_fourier<<<gf, 256, 0, s>>>(X, B, n->tau_lo, n->dtau, n->h1, split ? n->h1f : nullptr);
+    } else {
+        int g1 = (int)((B * (long long)MW + 255) / 256);
+        if (g1 > 4096) g1 = 4096;
+        k_l1_fwd<<<g1, 256, 0, s>>>(X, B, n->pb, n->p, O, n->z1, n->h1, split ? n->h1f : nullptr);
+    }
     GemmArgs a{};
     a.M = B; a.N = MW; a.K = MW; a.A = n->h1; a.sam = MW; a.sak = 1; a.B = n->pb + L.w2; a.sbn = MW; a.sbk = 1;
     a.epi = EPI_BIAS_GELU; a.bias = n->p + L.b2; a.out = n->z2; a.ldo = MW; a.outb = n->h2; a.ldb = MW; a.err = n->err;
-    cudaError_t e = gemm(a, n->wait, s);
+    a.Af = n->h1f; a.Bf = n->p + L.w2; a.outh = split ? n->h2f : nullptr;
+    cudaError_t e = gemm(a, n->wait, s, split);
     if (e != cudaSuccess) return e;
     a.A = n->h2; a.B = n->pb + L.w3; a.bias = n->p + L.b3; a.out = n->z3; a.outb = n->h3;
-    e = gemm(a, n->wait, s);
+    a.Af = n->h2f; a.Bf = n->p + L.w3; a.outh = split ? n->h3f : nullptr;
+    e = gemm(a, n->wait, s, split);
     if (e != cudaSuccess) return e;
     GemmArgs c{};
     c.M = B; c.N = O; c.K = MW; c.A = n->h3; c.sam = MW; c.sak = 1; c.B = n->pb + L.w4; c.sbn = MW; c.sbk = 1;
     c.epi = EPI_STORE; c.bias = n->p + L.b4; c.out = y; c.ldo = O; c.outb = nullptr; c.err = n->err;
-    return gemm(c, n->wait, s);
+    c.Af = n->h3f; c.Bf = n->p + L.w4;
+    return gemm(c, n->wait, s, split);
 }
 
 // backward of the batch held in the buffers; gradients into n->g
@@ -391,10 +487,12 @@ cudaError_t backward(rb_mlp *n, const float *X, int B, cudaStream_t s) {
     // dW2 = dz2^T h1
     a.A = n->dz2b; a.B = n->h1; a.out = n->g + L.w2;
     if ((e = gemm(a, n->wait, s)) != cudaSuccess) return e;
-    // dz1 = (dz2 W2) * gelu'(z1)
-    b.A = n->dz2b; b.B = n->pb + L.w2; b.out = n->dz1; b.outb = nullptr; b.zin = n->z1;
-    if ((e = gemm(b, n->wait, s)) != cudaSuccess) return e;
-    k_l1_bwd<<<MW, 256, 0, s>>>(n->dz1, X, B, n->g, O);
+    if (!(n->flags & RB_MLP_FOURIER)) {  // the Fourier input layer has no parameters (their gradient stays 0)
+        // dz1 = (dz2 W2) * gelu'(z1)
+        b.A = n->dz2b; b.B = n->pb + L.w2; b.out = n->dz1; b.outb = nullptr; b.zin = n->z1;
+        if ((e = gemm(b, n->wait, s)) != cudaSuccess) return e;
+        k_l1_bwd<<<MW, 256, 0, s>>>(n->dz1, X, B, n->g, O);
+    }
     k_colsum<<<MW, 256, 0, s>>>(n->dz2, B, MW, n->g + L.b2);
     k_colsum<<<MW, 256, 0, s>>>(n->dz3, B, MW, n->g + L.b3);
     k_colsum<<<O, 256, 0, s>>>(n->dyf, B, O, n->g + L.b4);
@@ -406,10 +504,21 @@ cudaError_t backward(rb_mlp *n, const float *X, int B, cudaStream_t s) {
 extern "C" {
 
 rb_status rb_mlp_create(rb_ctx *ctx, int n_out, int batch_cap, unsigned long long seed, rb_mlp **out) {
+    return rb_mlp_create_ex(ctx, n_out, batch_cap, seed, 0u, 0.0, 0.0, out);
+}
+
+rb_status rb_mlp_create_ex(rb_ctx *ctx, int n_out, int batch_cap, unsigned long long seed, unsigned flags,
+                           double tau_lo, double tau_hi, rb_mlp **out) {
     if (!ctx || !out || n_out < 1 || n_out > 4096 || batch_cap < 1 || batch_cap > (1 << 20)) return RB_EINVAL;
+    if ((flags & ~(unsigned)(RB_MLP_FOURIER | RB_MLP_SPLIT)) ||
+        ((flags & RB_MLP_FOURIER) && !(tau_lo >= 0.0 && tau_hi > tau_lo && std::isfinite(tau_hi))))
+        return RB_EINVAL;
     *out = nullptr;
     rb_mlp *n = new (std::nothrow) rb_mlp();
     if (!n) return RB_ENOMEM;
+    n->flags = flags;
+    n->tau_lo = tau_lo;
+    n->dtau = (flags & RB_MLP_FOURIER) ? (tau_hi - tau_lo) / (double)(MW / 2 - 1) : 0.0;
     n->ctx = ctx;
     n->wait = rbk::ctx_wait_cycles(ctx);
     n->stream = rbk::ctx_stream(ctx);
@@ -427,6 +536,9 @@ rb_status rb_mlp_create(rb_ctx *ctx, int n_out, int batch_cap, unsigned long lon
     size_t o_h1 = take(B * MW * 2), o_h2 = take(B * MW * 2), o_h3 = take(B * MW * 2), o_dyb = take(B * O * 2),
            o_dz2b = take(B * MW * 2), o_dz3b = take(B * MW * 2);
     size_t o_ss = take(sizeof(StepState)), o_err = take(4);
+    const bool split = (flags & RB_MLP_SPLIT) != 0;
+    size_t o_h1f = split ? take(B * MW * 4) : 0, o_h2f = split ? take(B * MW * 4) : 0,
+           o_h3f = split ? take(B * MW * 4) : 0;
     cudaSetDevice(n->device);
     if (cudaMalloc(&n->block, off) != cudaSuccess) {
         cudaGetLastError();
@@ -443,6 +555,11 @@ rb_status rb_mlp_create(rb_ctx *ctx, int n_out, int batch_cap, unsigned long lon
     n->dz2b = (bf16 *)(w + o_dz2b); n->dz3b = (bf16 *)(w + o_dz3b);
     n->ss = (StepState *)(w + o_ss);
     n->err = (int *)(w + o_err);
+    if (split) {
+        n->h1f = (float *)(w + o_h1f);
+        n->h2f = (float *)(w + o_h2f);
+        n->h3f = (float *)(w + o_h3f);
+    }
     cudaStream_t s = n->stream;
     cudaMemsetAsync(n->block, 0, off, s);
     k_mlp_init<<<256, 256, 0, s>>>(n->p, n_out, seed);

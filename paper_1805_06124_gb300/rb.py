@@ -26,6 +26,7 @@ EINVAL, ENOMEM, ECUDA, ENONFINITE, EORTHO, ETIMEOUT, ESTATE = -1, -2, -3, -4, -5
 SWEEP = {"df32": 0, "fp64": 1}
 FLAG_TIMING = 1
 FLAG_PROJECT_FP64 = 2
+MLP_FOURIER, MLP_SPLIT = 1, 2
 
 
 class Options(ctypes.Structure):
@@ -604,11 +605,18 @@ class MLP:
     Inputs X are (rows, 2) float32, targets T (rows, n_out) float32, all CUDA
     tensors; the caller scales the inputs (e.g. to [-1, 1])."""
 
-    def __init__(self, ctx: "RB", n_out: int, batch_cap: int = 4096, seed: int = 0):
+    def __init__(self, ctx: "RB", n_out: int, batch_cap: int = 4096, seed: int = 0, fourier=None,
+                 split: bool = False):
+        """fourier: (tau_lo, tau_hi) for the fixed Fourier input layer of
+        RB_MLP_FOURIER (inputs are then the physical (q, m)); split: the
+        RB_MLP_SPLIT forward (BF16 hi + lo pieces)."""
         lib = ctx.lib
         if not hasattr(lib.rb_mlp_create, "_rb_typed"):
             lib.rb_mlp_create.argtypes = [c_void_p, c_int, c_int, ctypes.c_ulonglong, ctypes.POINTER(c_void_p)]
             lib.rb_mlp_create.restype = c_int
+            lib.rb_mlp_create_ex.argtypes = [c_void_p, c_int, c_int, ctypes.c_ulonglong, c_uint, c_double, c_double,
+                                             ctypes.POINTER(c_void_p)]
+            lib.rb_mlp_create_ex.restype = c_int
             lib.rb_mlp_destroy.argtypes = [c_void_p]
             lib.rb_mlp_destroy.restype = None
             lib.rb_mlp_num_params.argtypes = [c_void_p]
@@ -625,8 +633,11 @@ class MLP:
             lib.rb_mlp_train.restype = c_int
             lib.rb_mlp_create._rb_typed = True
         self.ctx, self.lib, self.n_out = ctx, lib, n_out
+        self.fourier, self.split = fourier, split
+        flags = (MLP_FOURIER if fourier is not None else 0) | (MLP_SPLIT if split else 0)
+        tl, th = (float(fourier[0]), float(fourier[1])) if fourier is not None else (0.0, 0.0)
         h = c_void_p()
-        st = lib.rb_mlp_create(ctx._h, n_out, batch_cap, seed, ctypes.byref(h))
+        st = lib.rb_mlp_create_ex(ctx._h, n_out, batch_cap, seed, flags, tl, th, ctypes.byref(h))
         if st != OK:
             raise RBError(st, "rb_mlp_create failed")
         self._h = h

@@ -50,10 +50,42 @@ def summarize(e):
     return {"median": float(e.median()), "p95": float(torch.quantile(e, 0.95)), "max": float(e.max())}
 
 
-def train(ctx: rb.RB, q, m, C, epochs=200, batch=1024, lr=1e-3, seed=4):
-    X = scale_inputs(q, m).cuda(ctx.device)
+def chirp_tau_band(N: int, t_c: float = 1.05):
+    """[tau_lo, tau_hi] of the chirp family's phase variable tau_i =
+    (t_c - t_i)^(5/8), t_i = i / N: a snapshot is sum_i a_i exp(-i omega tau_i),
+    so each basis coefficient is a sum of exp(-i omega tau_i) over this band."""
+    return (t_c - (N - 1) / N) ** 0.625, t_c ** 0.625
+
+
+def inputs(net: "rb.MLP", q, m):
+    """The network's input rows: (q, m) themselves for the Fourier input
+    layer, else their affine scaling."""
+    import torch
+    if net.fourier is not None:
+        return torch.stack([torch.as_tensor(q, dtype=torch.float64), torch.as_tensor(m, dtype=torch.float64)],
+                           1).to(torch.float32).contiguous()
+    return scale_inputs(q, m)
+
+
+def nearest_in_omega(q, m, qt, mt, device="cuda"):
+    """The non-learned baseline: for each held-out (qt, mt), the index of the
+    training snapshot nearest in omega (the family depends on (q, m) only
+    through omega)."""
+    import torch
+    from . import synth
+    om = torch.as_tensor(synth.chirp_omega(q, m), device=device)
+    omt = torch.as_tensor(synth.chirp_omega(qt, mt), device=device)
+    order = torch.argsort(om)
+    pos = torch.searchsorted(om[order], omt).clamp(1, om.numel() - 1)
+    left, right = order[pos - 1], order[pos]
+    return torch.where((omt - om[left]).abs() <= (om[right] - omt).abs(), left, right)
+
+
+def train(ctx: rb.RB, q, m, C, epochs=200, batch=1024, lr=1e-3, seed=4, fourier=None, split=False):
+    """fourier: (tau_lo, tau_hi) for the Fourier input layer (chirp_tau_band(N))."""
     T = targets_from_C(C).cuda(ctx.device)
-    net = rb.MLP(ctx, T.shape[1], batch_cap=max(batch, 4096), seed=seed)
+    net = rb.MLP(ctx, T.shape[1], batch_cap=max(batch, 4096), seed=seed, fourier=fourier, split=split)
+    X = inputs(net, q, m).cuda(ctx.device)
     t0 = time.perf_counter()
     curve = net.train(X, T, epochs, batch, lr, seed)
     ctx.stream.synchronize()
