@@ -23,23 +23,30 @@ def _greedy(orc, S, tol=1e-30, kmax=None, **kw):
 
 # ---------------------------------------------------------------- closed forms
 
+def _cplx(a):
+    a = np.asarray(a, np.float64)
+    return a[..., 0] + 1j * a[..., 1]
+
+
 def test_hand_worked_2x2(orc):
-    """Alg. 3 by hand on s_0 = (1, 0), s_1 = (1, 1):
-    ||s||^2 = (1, 2) -> pivot 1; q_1 = (1,1)/sqrt2; c(s_0) = 1/sqrt2 so
-    err_0 = 1 - 1/2 = 1/2 -> pivot 0; q_2 = (1,-1)/sqrt2; nothing left."""
-    S = np.array([[1, 0], [1, 1]], np.complex128)
-    r = _greedy(orc, S, tol=1e-30, kmax=2)
-    assert r["status"] == orc.OK and r["k"] == 2
-    assert list(r["pivots"]) == [1, 0]
-    np.testing.assert_allclose(r["err_curve"], [2.0, 0.5, 0.0], atol=1e-15)
-    h = 1 / np.sqrt(2)
-    np.testing.assert_allclose(r["Q"], [[h, h], [h, -h]], atol=1e-15)
-    np.testing.assert_allclose(r["C"], [[h, np.sqrt(2)], [h, 0]], atol=1e-15)
-    np.testing.assert_allclose(r["rdiag"], [np.sqrt(2), h], atol=1e-15)
-    # stopping rule: with tol = 1 the second error (0.5) is below tol -> k = 1
-    r1 = _greedy(orc, S, tol=1.0, kmax=2)
-    assert r1["k"] == 1 and list(r1["pivots"]) == [1]
-    np.testing.assert_allclose(r1["err_curve"], [2.0, 0.5], atol=1e-15)
+    """Alg. 3 by hand (tests/golden/alg3_hand_worked_2x2.json, with its
+    derivation): s_0 = (1, 0), s_1 = (1, 1) -> pivots (1, 0), errors
+    (2, 1/2, 0), and the stopping rule on squared errors."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "alg3_hand_worked_2x2.json")) as f:
+        fx = json.load(f)
+    S = _cplx(fx["S_columns"])
+    r = _greedy(orc, S, tol=fx["tol"], kmax=fx["kmax"])
+    assert r["status"] == orc.OK and r["k"] == len(fx["pivots"])
+    assert list(r["pivots"]) == fx["pivots"]
+    np.testing.assert_allclose(r["err_curve"], fx["err_curve"], atol=1e-15)
+    np.testing.assert_allclose(r["Q"], _cplx(fx["Q_rows"]), atol=1e-15)
+    np.testing.assert_allclose(r["C"], _cplx(fx["C"]), atol=1e-15)
+    np.testing.assert_allclose(r["rdiag"], fx["rdiag"], atol=1e-15)
+    r1 = _greedy(orc, S, tol=fx["tol_loose"], kmax=fx["kmax"])
+    assert r1["k"] == 1 and list(r1["pivots"]) == fx["pivots_loose"]
+    np.testing.assert_allclose(r1["err_curve"], fx["err_curve_loose"], atol=1e-15)
 
 
 def test_exact_ties_lowest_index(orc):
