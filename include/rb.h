@@ -69,13 +69,17 @@ enum {
 /* rb_options.flags */
 #define RB_FLAG_TIMING 1u        /* time every sweep launch with CUDA events (fills rb_result.ms_sweep) */
 #define RB_FLAG_PROJECT_FP64 2u  /* rb_project on the plain-FP64 CUDA-core kernel instead of the tensor cores */
+#define RB_FLAG_SPLIT_NO_SWITCH 4u /* rb_greedy_split never switches to hi + lo sweeps on the candidate count
+                                      (it re-checks however many candidates the bounds admit) */
 
 typedef struct rb_options {
     int device;            /* CUDA device ordinal */
     int sweep;             /* RB_SWEEP_DF32 (default) or RB_SWEEP_FP64 */
     double imgs_kappa;     /* MGSCI kappa, > 1 (default 2.0) */
     int imgs_max_passes;   /* cap on IMGS passes per vector, >= 1 (default 4) */
-    double switch_err;     /* reserved (must be > 0; default 1e-6); the split form does not switch sweeps */
+    double switch_err;     /* rb_greedy_split: switch to hi + lo sweeps once every error is certified below
+                              switch_err * max_j ||s_j||^2 (the largest upper bound of the hi-only phase);
+                              0 (default) = switch on the candidate count only.  Finite, >= 0 */
     int iters_per_sync;    /* iterations queued between host checks of the stop flag (default 8) */
     void *stream;          /* cudaStream_t; NULL = the context creates its own stream */
     unsigned flags;        /* RB_FLAG_* */
@@ -179,21 +183,28 @@ rb_status rb_greedy_resume(rb_ctx *ctx, const void *S, long long N, long long M,
 
 /* Split-precision RB-greedy on S stored as complex64 hi + lo (see rb_split;
  * column j at hi + j*ld and lo + j*ld, ld even, both 16-byte aligned; N <= 2^22).
- * Every sweep reads hi only: c~ = q^H hi with FP32 FMAs summed against a
- * fixed power-of-two offset per lane chain (rounding about 2^-42 ||hi_j|| at
- * N = 16384), FP64 bookkeeping of the error of hi_j, and the certified bounds
+ * Two phases.  Hi-only phase: every sweep reads hi only: c~ = q^H hi with
+ * FP32 FMAs summed against a fixed power-of-two offset per lane chain
+ * (rounding about 2^-42 ||hi_j|| at N = 16384), FP64 bookkeeping of the error
+ * of hi_j, and the certified bounds
  * |err(hi_j) - bookkeeping| <= 2 eta ||hi_j|| sum_l |c~_lj| (eta = 2^-46 sqrt(N))
  * and |sqrt(err_j) - sqrt(err(hi_j))| <= ||lo_j||.  The columns whose upper
  * bound reaches the best lower bound are re-checked exactly (hi and lo,
- * compensated) and the exact argmax is the pivot; the loop ends when every
- * upper bound, or the exact pivot error, is below tol (or at kmax), and then
- * one tensor-core projection of the basis onto lo completes C and the errors.
- * IMGS, norms, the bookkeeping and the re-check stay FP64(-accurate).  Outputs
- * and returns as rb_greedy; C is accurate to (2^-48 sqrt(N) + 2^-42) ||s_j||
- * beyond the FP64 form's (the hi-only sweep's rounding and the FP16 pieces of
- * the projection onto lo); out->switch_iter is the basis size at the
- * projection onto lo;
- * opt.switch_err is not used by this form. */
+ * compensated) and the exact argmax is the pivot.  The switch: once more
+ * than max(M/8, 256) columns are candidates (unless opt.flags has
+ * RB_FLAG_SPLIT_NO_SWITCH), or once every upper bound is below
+ * opt.switch_err * max_j ||s_j||^2, the basis so far is projected onto lo on
+ * the tensor cores (C becomes exact), the errors are rebuilt from C, and every
+ * later sweep reads hi + lo with double-float products (the FP64 form's
+ * sweep, 16 bytes per element).  The loop ends when every upper bound, or
+ * the exact pivot error, is below tol (or at kmax); if that happens in the
+ * hi-only phase, one projection of the basis onto lo then completes C and the
+ * errors.  IMGS, norms, the bookkeeping and the re-check stay FP64(-accurate).
+ * Outputs and returns as rb_greedy; the rows of C before the switch are
+ * accurate to (2^-48 sqrt(N) + 2^-42) ||s_j|| beyond the FP64 form's (the
+ * hi-only sweep's rounding and the FP16 pieces of the projection onto lo),
+ * later rows as the FP64 form's; out->switch_iter is the basis size at the
+ * switch (-1: the loop ended in the hi-only phase). */
 rb_status rb_greedy_split(rb_ctx *ctx, const void *hi, const void *lo, long long N, long long M, long long ld,
                           double tol, int kmax, rb_result *out);
 

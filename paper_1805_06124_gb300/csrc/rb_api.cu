@@ -6,6 +6,7 @@
 // 100-byte device state once.  Kernels queued after the stop flag was set
 // return immediately.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -133,7 +134,7 @@ void rb_default_options(rb_options *opt) {
     opt->sweep = RB_SWEEP_DF32;
     opt->imgs_kappa = 2.0;
     opt->imgs_max_passes = 4;
-    opt->switch_err = 1e-6;
+    opt->switch_err = 0.0;
     opt->iters_per_sync = 8;
     opt->recompute_period = 16;
     opt->stream = nullptr;
@@ -151,7 +152,7 @@ rb_status rb_create(const rb_options *opt, rb_ctx **out) {
     else
         rb_default_options(&o);
     if (!(o.imgs_kappa > 1.0) || o.imgs_max_passes < 1 || o.iters_per_sync < 1 || o.recompute_period < 0 ||
-        (o.sweep != RB_SWEEP_DF32 && o.sweep != RB_SWEEP_FP64) || !(o.switch_err > 0.0) ||
+        (o.sweep != RB_SWEEP_DF32 && o.sweep != RB_SWEEP_FP64) || !(o.switch_err >= 0.0) || !std::isfinite(o.switch_err) ||
         o.batched_variant < -1 || o.batched_variant > 23 || (o.timeout_cycles && o.timeout_cycles < (1ull << 20)))
         return RB_EINVAL;
     rb_ctx *ctx = new (std::nothrow) rb_ctx();
@@ -643,6 +644,9 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     p.lgcap = lgcap;
     p.tc_err = (int *)(w + o_te);
     p.wait_cycles = rbk::ctx_wait_cycles(ctx);
+    p.switch_err = o.switch_err;
+    // re-checking more than this many candidates costs more than sweeping hi + lo
+    p.switch_cand = (o.flags & RB_FLAG_SPLIT_NO_SWITCH) ? INT_MAX : (int)std::max<long long>(M / 8, 256);
 
     cudaStream_t sm = ctx->stream;
     int nlaunch = 0;
@@ -660,7 +664,12 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     while (!stopped) {
         for (int t = 0; t < o.iters_per_sync && it <= kcap; t++, it++) {
             RB_CK(rbk::launch_imgs(p, G, true, sm, &nlaunch), "imgs");
+            // hi-only phase (these return at once after the switch) ...
             RB_CK(rbk::launch_split_iteration(p, G, sm, &nlaunch), "split iteration");
+            // ... or the hi + lo sweep after it (returns at once before it)
+            RB_CK(rbk::launch_sweep(p, RB_SWEEP_DF32, G, sm), "hi+lo sweep");
+            nlaunch += 1;
+            // the projection onto lo, queued at the switch or when the loop ends
             RB_CK(rbk::launch_split_finish(p, G, sm, &nlaunch), "split finish");
         }
         RB_CK(cudaMemcpyAsync(ctx->st_host, p.st, sizeof(rbk::DevState), cudaMemcpyDeviceToHost, sm), "state copy");
@@ -689,8 +698,10 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     RB_CK(cudaMemcpy(&tc_err, p.tc_err, sizeof(int), cudaMemcpyDeviceToHost), "tc flag");
     if (tc_err) return fail(ctx, RB_ETIMEOUT, "rb_greedy_split: a tensor-core wait ran out");
     // per hi-only sweep: hi (8 N M), chain norms (256 M), q (16 N), the column
-    // scalars read and written (acc, sabs, C row, norm2, norm2_hi, lonrm, picked)
-    out->sweep_bytes = (double)hs.n_sweeps * (8.0 * N * M + 256.0 * M + 16.0 * N + 69.0 * M);
+    // scalars read and written (acc, sabs, C row, norm2, norm2_hi, lonrm, picked);
+    // per hi + lo sweep after the switch, the FP64 form's sweep bytes
+    out->sweep_bytes = (double)(hs.n_sweeps - hs.n_sweeps_hl) * (8.0 * N * M + 256.0 * M + 16.0 * N + 69.0 * M) +
+                       (double)hs.n_sweeps_hl * (16.0 * N * M + 16.0 * N + 41.0 * M);
     if (hs.status < 0) {
         const char *why = hs.status == RB_ENONFINITE ? "NaN or Inf in hi/lo"
                           : hs.status == RB_EORTHO   ? "IMGS did not pass the kappa test within imgs_max_passes"

@@ -29,12 +29,13 @@ struct DevState {
     int passes;        // IMGS passes in the current iteration
     int total_passes;  // IMGS passes over the whole call
     int nonfinite;     // a column norm was NaN/Inf
-    int phase;         // split form: 1 once C has been completed by the projection onto lo
-    int switch_iter;   // split form: basis size at that projection (-1 = none)
+    int phase;         // split form: 1 once the sweeps read hi + lo (after the switch)
+    int switch_iter;   // split form: basis size at the switch
     int n_sweeps;      // sweep launches that did work
     int ncand;         // split form: candidates in the last recheck
-    int switch_pending;  // split form: the loop has ended; the projection onto lo is queued
-    int pad0;
+    int switch_pending;  // split form: the projection onto lo is queued; 1: the loop has ended,
+                         // 2: the switch to hi + lo sweeps (the loop goes on)
+    int n_sweeps_hl;     // split form: hi + lo sweeps after the switch
     int max_cand;        // split form: largest candidate list seen
     int force_stop;      // split form: exact rank reached (IMGS found a zero vector)
     int cand_total;      // split form: candidates counted in this iteration
@@ -105,6 +106,8 @@ struct Prob {
     int nblk_cand;     // blocks of the candidate kernels
     int *tc_err;       // set when a tensor-core wait ran out
     unsigned long long wait_cycles;  // budget of each tensor-core wait, SM clock cycles
+    double switch_err; // split form: switch once every error is certified below switch_err * max ||s_j||^2 (0: off)
+    int switch_cand;   // split form: switch once more than switch_cand columns are candidates
     double *dacc;      // D_j = sum_l (|c_lj|^2 - |c~_lj|^2) over the rows re-checked so far
     int *dcnt;         // rows covered by D_j
     int *passes_out;   // IMGS passes of iteration k at [k] (may be null)

@@ -213,8 +213,9 @@ __device__ __forceinline__ double2 col_dot_sig(const float2 *__restrict__ hcol, 
     return make_double2((double)rh + (double)rl, (double)ih + (double)il);
 }
 
+// The hi-only phase is running (no projection onto lo queued, no switch yet).
 __device__ __forceinline__ bool loop_active(const DevState *st) {
-    return !ld_volatile(&st->stop) && !ld_volatile(&st->switch_pending);
+    return !ld_volatile(&st->stop) && !ld_volatile(&st->switch_pending) && !ld_volatile(&st->phase);
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_sweep_hi(Prob p) {
@@ -320,6 +321,10 @@ __global__ void __launch_bounds__(kThreads) k_bounds(Prob p) {
             // the loop ends: complete C on lo first (gu < tol certifies every error below tol)
             st->switch_pending = 1;
             st->ncand = 0;
+        } else if (gu < p.switch_err * p.err_curve[0]) {
+            // every error is certified below switch_err * max ||s_j||^2: switch to hi + lo sweeps
+            st->switch_pending = 2;
+            st->ncand = 0;
         } else {
             st->ncand = -1;  // re-check needed
         }
@@ -367,6 +372,12 @@ __global__ void __launch_bounds__(kThreads) k_cand_count(Prob p) {
         }
         st->cand_total = run;
         st->ticket_aux = 0;
+        if (run > p.switch_cand) {
+            // the bounds no longer separate the columns: re-checking this many
+            // would cost more than sweeping hi + lo, so switch instead
+            st->switch_pending = 2;
+            st->ncand = 0;
+        }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < G; b += blockDim.x) p.bcount[b] = sc[b];
@@ -998,8 +1009,12 @@ __global__ void __launch_bounds__(LP_THREADS, 1) k_lo_project_tc(Prob p, int nt,
     if (warp == 0) tmem_dealloc(tmem, LT_NMAX);
 }
 
-// acc_j = sum_l |C[l, j]|^2 after the projection onto lo, the final argmax and
-// the stopping status.
+// After the projection onto lo: acc_j = sum_l |C[l, j]|^2 from the now exact
+// coefficients (error-free squares, compensated sum) and the exact argmax.
+// switch_pending 1 (the loop has ended): the stopping status.  switch_pending
+// 2 (the switch): the sweeps read hi + lo from here on (phase 1, the FP64
+// form's double-float sweep on the same hi/lo storage), err_curve[k] and the
+// next pivot become exact, and the stopping rule is applied to them.
 __global__ void __launch_bounds__(kThreads) k_rebase_finish(Prob p) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop) || !ld_volatile(&st->switch_pending)) return;
@@ -1007,11 +1022,7 @@ __global__ void __launch_bounds__(kThreads) k_rebase_finish(Prob p) {
     double be = -INFINITY;
     long long bi = kNoIdx;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < p.M; j += (long long)gridDim.x * blockDim.x) {
-        double a = 0.0;
-        for (int l = 0; l < k1; l++) {
-            double2 c = p.C[(long long)l * p.ldC + j];
-            a += c.x * c.x + c.y * c.y;
-        }
+        const double a = acc_recompute(p.C, p.ldC, j, k1);
         p.acc[j] = a;
         double e = p.norm2[j] - a;
         if (!p.picked[j] && better(e, j, be, bi)) { be = e; bi = j; }
@@ -1032,17 +1043,31 @@ __global__ void __launch_bounds__(kThreads) k_rebase_finish(Prob p) {
     block_best(be, bi);
     if (threadIdx.x == 0) {
         st->ticket_aux = 0;
+        const bool ending = st->switch_pending == 1;
         st->switch_pending = 0;
-        st->phase = 1;
-        st->switch_iter = k1;
         double emax = bi == kNoIdx ? 0.0 : be;
         p.err_curve[k1] = emax;
         st->J = bi;
         st->errJ = emax;
-        st->status = (bi != kNoIdx && !(emax < p.tol) && !st->force_stop && k1 >= p.kmax && k1 < p.minNM)
-                         ? RB_KMAX_REACHED
-                         : RB_OK;
-        st->stop = 1;
+        if (ending) {
+            st->status = (bi != kNoIdx && !(emax < p.tol) && !st->force_stop && k1 >= p.kmax && k1 < p.minNM)
+                             ? RB_KMAX_REACHED
+                             : RB_OK;
+            st->stop = 1;
+        } else {
+            st->phase = 1;
+            st->switch_iter = k1;
+            if (bi == kNoIdx || emax < p.tol) {
+                st->status = RB_OK;
+                st->stop = 1;
+            } else if (k1 >= p.kmax) {
+                st->status = RB_KMAX_REACHED;
+                st->stop = 1;
+            } else if (k1 >= p.minNM) {
+                st->status = RB_OK;
+                st->stop = 1;
+            }
+        }
     }
 }
 

@@ -46,7 +46,7 @@ template <int VARIANT>
 __global__ void __launch_bounds__(kThreads) k_sweep(Prob p) {
     DevState *st = p.st;
     if (ld_volatile(&st->stop)) return;
-    if (p.qs_stride && (ld_volatile(&st->phase) == 0 || ld_volatile(&st->switch_pending))) return;  // split form, hi-only phase
+    if (p.qs_stride && (ld_volatile(&st->phase) == 0 || ld_volatile(&st->switch_pending))) return;  // split form before the switch
     const int k = st->k;  // row of C written by this sweep; q_k is the newest vector
     const int lane = threadIdx.x & 31;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(Prob p) {
     block_best(be, bi);
     if (threadIdx.x == 0) {
         st->ticket_sweep = 0;
+        if (p.qs_stride) st->n_sweeps_hl += 1;
         sweep_publish(p, st, k, be, bi);
     }
 }

@@ -26,6 +26,7 @@ EINVAL, ENOMEM, ECUDA, ENONFINITE, EORTHO, ETIMEOUT, ESTATE = -1, -2, -3, -4, -5
 SWEEP = {"df32": 0, "fp64": 1}
 FLAG_TIMING = 1
 FLAG_PROJECT_FP64 = 2
+FLAG_SPLIT_NO_SWITCH = 4
 MLP_FOURIER, MLP_SPLIT = 1, 2
 
 
@@ -142,9 +143,9 @@ class RB:
     """One rb_ctx.  ``stream`` defaults to torch's current stream on ``device``."""
 
     def __init__(self, device: int = 0, sweep: str = "df32", kappa: float = 2.0, max_passes: int = 4,
-                 switch_err: float = 1e-6, iters_per_sync: int = 8, stream=None, timing: bool = False,
+                 switch_err: float = 0.0, iters_per_sync: int = 8, stream=None, timing: bool = False,
                  project_fp64: bool = False, recompute_period: int = 16, batched_variant: int = -1,
-                 timeout_cycles: int = 0):
+                 timeout_cycles: int = 0, split_switch: bool = True):
         torch = _torch()
         self.lib = load()
         self.device = device
@@ -166,7 +167,8 @@ class RB:
         # (0x1) so the library orders its work with torch instead of
         # creating a private stream.
         opt.stream = c_void_p(stream.cuda_stream or 1)
-        opt.flags = (FLAG_TIMING if timing else 0) | (FLAG_PROJECT_FP64 if project_fp64 else 0)
+        opt.flags = ((FLAG_TIMING if timing else 0) | (FLAG_PROJECT_FP64 if project_fp64 else 0) |
+                     (0 if split_switch else FLAG_SPLIT_NO_SWITCH))
         h = c_void_p()
         st = self.lib.rb_create(ctypes.byref(opt), ctypes.byref(h))
         if st != OK:

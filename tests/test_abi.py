@@ -57,7 +57,7 @@ def test_default_options(lib):
     o = rb.Options()
     L.rb_default_options(ctypes.byref(o))
     assert o.sweep == rb.SWEEP["df32"] and o.imgs_kappa == 2.0 and o.imgs_max_passes == 4
-    assert o.switch_err == 1e-6 and o.iters_per_sync >= 1
+    assert o.switch_err == 0.0 and o.iters_per_sync >= 1
     assert o.batched_variant == -1 and o.timeout_cycles == 0
 
 
@@ -70,6 +70,12 @@ def test_bad_options_rejected_before_any_device_call(lib):
     assert L.rb_create(ctypes.byref(o), ctypes.byref(h)) == rb.EINVAL
     L.rb_default_options(ctypes.byref(o))
     o.batched_variant = 24
+    assert L.rb_create(ctypes.byref(o), ctypes.byref(h)) == rb.EINVAL
+    L.rb_default_options(ctypes.byref(o))
+    o.switch_err = -1e-6
+    assert L.rb_create(ctypes.byref(o), ctypes.byref(h)) == rb.EINVAL
+    L.rb_default_options(ctypes.byref(o))
+    o.switch_err = float("nan")
     assert L.rb_create(ctypes.byref(o), ctypes.byref(h)) == rb.EINVAL
     L.rb_default_options(ctypes.byref(o))
     o.timeout_cycles = 1000

@@ -172,7 +172,7 @@ def test_config3_split_form_full_size_oracle_replay(orc, rbm, cfg3):
     c.close()
     del hi, lo
     torch.cuda.empty_cache()
-    assert g["status"] == 0 and g["switch_iter"] == g["k"]
+    assert g["status"] == 0 and g["switch_iter"] == -1  # few candidates: no switch
     rep = parity.replay_and_check(orc, cfg3["S"], g, tol, kmax, omp=True)
     info = parity.compare(g, rep, cfg3["S"], c_rel=2.0 ** -48 * np.sqrt(N) + 2.0 ** -42, norms=cfg3["norms"])
     k = rep["k"]

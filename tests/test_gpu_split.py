@@ -52,9 +52,9 @@ def test_split_config1_parity(orc, rbm):
     assert g["status"] == 0
     rep = parity.replay_and_check(orc, S, g, 1e-10, 300)
     info = parity.compare(g, rep, S, c_rel=c_rel(S.shape[1]))
-    print("split k", g["k"], "projection at", g["switch_iter"], info)
-    # C is completed on lo once, when the loop ends
-    assert g["switch_iter"] == g["k"]
+    print("split k", g["k"], "switch at", g["switch_iter"], info)
+    # the candidates stay few: no switch, C is completed on lo once, when the loop ends
+    assert g["switch_iter"] == -1
     assert np.max(g["final_err"]) < 1e-10 + 1e-12
     c.close()
 
@@ -172,3 +172,72 @@ def test_split_several_row_tiles(orc, rbm, kmax):
     rep = parity.replay_and_check(orc, S, g, 0.0, kmax)
     parity.compare(g, rep, S, err_atol=1e-12 * rep["err_curve"][0], c_rel=c_rel(S.shape[1]))
     c.close()
+
+
+def _rows_after_switch_fp64_tol(g, rep, ks):
+    """Rows of C from the switch on come from the hi + lo (double-float)
+    sweep: the FP64 form's C tolerance, without the split form's c_rel."""
+    k = rep["k"]
+    bt = parity.basis_tol(rep["err_curve"], k)
+    dC = np.abs(np.asarray(g["C"])[ks:k] - rep["C"][ks:k])
+    r = dC / (bt[ks:k, None] + 1e-13)
+    assert np.all(r <= 1.0), np.max(r)
+    return float(np.max(dC)) if k > ks else 0.0
+
+
+def test_split_switch_on_error_threshold(orc, rbm):
+    """opt.switch_err: once every error is certified below
+    switch_err * max ||s_j||^2 the basis so far is projected onto lo and the
+    later sweeps read hi + lo.  The pivots, curve, basis and errors meet the
+    FP64 protocol; the rows of C before the switch the split form's C
+    tolerance, the later rows the FP64 form's."""
+    S = synth.chirps(1024, 2048, seed=0)
+    tol, kmax = 1e-10, 300
+    c = rbm.RB(device=0, switch_err=1e-6)
+    H, L = split_upload(orc, S)
+    g = npy(c.greedy_split(H, L, tol, kmax))
+    assert g["status"] == 0
+    ks = g["switch_iter"]
+    assert 0 < ks < g["k"], (ks, g["k"])
+    ec = np.asarray(g["err_curve"])
+    assert ec[ks] < 1e-6 * ec[0]           # the rule that fired
+    rep = parity.replay_and_check(orc, S, g, tol, kmax)
+    info = parity.compare(g, rep, S, c_rel=c_rel(S.shape[1]))
+    info["max_dC_after_switch"] = _rows_after_switch_fp64_tol(g, rep, ks)
+    # the same pivots as the run without the switch
+    c2 = rbm.RB(device=0)
+    g2 = npy(c2.greedy_split(H, L, tol, kmax))
+    assert list(g2["pivots"]) == list(g["pivots"]) and g2["switch_iter"] == -1
+    print("switch at", ks, "of", g["k"], info)
+    c.close()
+    c2.close()
+
+
+def test_split_switch_on_candidate_count_large_m(orc, rbm):
+    """tol far below the hi-only bound widths on a large M: in the last
+    iterations the bounds admit most columns as candidates, the count passes
+    M/8 and the form switches to hi + lo sweeps.  The same run with the
+    switch disabled (RB_FLAG_SPLIT_NO_SWITCH) re-checks every candidate.
+    Both meet the protocol against the oracle."""
+    N, M = 2048, 65536
+    S = synth.chirps(N, M, seed=7)
+    # below the bound widths (about 2 eta sum_l |c~_lj| ~ 3e-12 here), well above
+    # the bookkeeping noise, so the stop is not a near-tie with tol
+    tol, kmax = 3e-12, 400
+    H, L = split_upload(orc, S)
+    res = {}
+    for sw in (True, False):
+        c = rbm.RB(device=0, split_switch=sw)
+        g = npy(c.greedy_split(H, L, tol, kmax))
+        c.close()
+        assert g["status"] == 0
+        rep = parity.replay_and_check(orc, S, g, tol, kmax, omp=True)
+        info = parity.compare(g, rep, S, c_rel=c_rel(N))
+        if sw:
+            assert 0 < g["switch_iter"] <= g["k"]
+            info["max_dC_after_switch"] = _rows_after_switch_fp64_tol(g, rep, g["switch_iter"])
+        else:
+            assert g["switch_iter"] == -1
+        info.update(switch_iter=int(g["switch_iter"]), ms=round(float(g["ms_total"]), 3))
+        res[sw] = info
+    print("switch", res[True], "no switch", res[False])
