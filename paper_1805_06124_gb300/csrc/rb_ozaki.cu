@@ -184,23 +184,81 @@ __device__ __forceinline__ void tmem_ld4_levels(uint32_t taddr, float (&v)[OZ_LV
         for (int e = 0; e < 4; e++) v[L][e] = __uint_as_float(r[L][e]);
 }
 
-// The GEMM with the snapshot slicing inside it.  Warps 0-7 (256 producer
+// Snapshot (B) slices inside the GEMM.  X = round(v 2^(49-E)) is formed as
+// the magnitude |X| (one right shift of the 53-bit significand, at least 5
+// bits since |v| < 2^(E-1)) and a sign.  The balanced digits of |X| < 2^48
+// come from the unsigned 7-bit fields gamma_s of
+// Y = |X| + 64 sum_s 2^(49-7s) > 0: |X| = sum_s (gamma_s - 64) 2^(49-7s), the
+// top field taking every bit from 2^42 up (gamma_1 <= 128), so |alpha_s| <= 64
+// as for digits7.  A signed digit becomes an FP32 value as
+// sign * (2^23 + gamma) - sign * (2^23 + 64) in one FMA (both terms exact, the
+// result an integer), and two FP32 digits (at most 8 significant bits) become
+// one BF16x2 word by keeping their upper halves: no conversion instructions.
+constexpr unsigned long long OZ_OFF =
+    64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
+
+__device__ __forceinline__ void digits7f(double v, int E, float (&f)[OZ_S]) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const unsigned hw = (unsigned)(bits >> 32);
+    const int e = (int)((hw >> 20) & 0x7FFu);
+    const int sh = 1026 + E - e;
+    unsigned long long mag = 0;
+    if (e != 0 && sh < 64) {  // round half up: (m / 2^(sh-1) + 1) / 2
+        const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+        mag = ((m >> (sh - 1)) + 1ull) >> 1;
+    }
+    const unsigned long long Y = mag + OZ_OFF;
+    const unsigned lo = (unsigned)Y, hi = (unsigned)(Y >> 32);
+    const unsigned g[OZ_S] = {hi >> 10, (hi >> 3) & 127u, (unsigned)(Y >> 28) & 127u, (lo >> 21) & 127u,
+                              (lo >> 14) & 127u, (lo >> 7) & 127u, lo & 127u};
+    const float sg = (hw >> 31) ? -1.0f : 1.0f;
+#pragma unroll
+    for (int t = 0; t < OZ_S; t++) f[t] = fmaf(sg, __uint_as_float(0x4B000000u | g[t]), sg * -8388672.0f);
+}
+
+// The seven BF16x2 (re, im) slice words of one complex value.
+__device__ __forceinline__ void slice7_words(double re, double im, int E, uint32_t (&w)[OZ_S]) {
+    float a[OZ_S], c[OZ_S];
+    digits7f(re, E, a);
+    digits7f(im, E, c);
+#pragma unroll
+    for (int t = 0; t < OZ_S; t++) w[t] = __byte_perm(__float_as_uint(a[t]), __float_as_uint(c[t]), 0x7632);
+}
+
+// The GEMM with the snapshot slicing inside it.  Warps 0-15 (512 producer
 // threads) read X and write the seven B slice planes of each K stage straight
-// into the stage's shared-memory buffer (thread t: column 64 ct + t / 4,
-// complex elements 2 (t % 4) and 2 (t % 4) + 1 of the stage, X read
-// OZ_AHEAD stages ahead into registers); lane 0 of warp 8 fills the A half of
-// the buffer with one bulk copy of the pre-sliced basis (28 KB, L2-resident)
-// and issues the stage's 28 MMAs.  Barriers per buffer: "afull" counts the
-// A bytes, "bfull" the 256 producer arrivals, "done" receives the MMA
-// commit; the n-th phase of buffer b belongs to stage b + OZ_NBUF n.  At the
-// end of each exact chunk (OZ_DRAIN K values) the producer threads drain the
-// TMEM levels into double-float running sums held in registers: thread
-// (warp w, lane l) owns row 32 (w % 4) + l and columns 32 (w / 4) .. + 31.
-constexpr int OZ_NBUF = 5;
-constexpr int OZ_PRODUCERS = 256;
-constexpr int OZ_THREADS = OZ_PRODUCERS + 32;
-constexpr int OZ_AHEAD = 2;  // equals the number of register sets in k_oz_gemm
-static_assert((OZ_DRAIN / OZ_KS) % OZ_AHEAD == 0, "chunks hold whole register-set rounds");
+// into the stage's shared-memory buffer: thread t owns column 64 ct + t / 8
+// and complex element t % 8 of every stage, and reads X in groups of OZ_FG
+// stages (512 contiguous bytes per column per group), two groups ahead of
+// the slicing.  Lane 0 of warp 16 fills the A half of each buffer with one
+// bulk copy of the pre-sliced basis (28 KB, L2-resident) and issues the
+// stage's MMAs: slice sa of A against the consecutive B planes sb .. sb+g-1
+// as one operand of 64 g rows (the planes are 64 rows apart in the K-major
+// layout), whose product lands on the TMEM levels sa+sb .. sa+sb+g-1 (the
+// levels are 64 columns apart) -- 10 MMAs of N = 64 .. 256 per stage.
+// Barriers per buffer: "afull" counts the A bytes, "bfull" one arrival per
+// producer warp, "done" receives the MMA commit; the n-th phase of buffer b
+// belongs to stage b + OZ_NBUF n (buffer and phase parity are carried along
+// with the stage).  At the end of each exact chunk (OZ_DRAIN K values) the
+// producers drain the TMEM levels into double-float running sums kept in
+// shared memory (column-major, so a warp's 32 rows are 32 consecutive
+// words): thread (warp w, lane l) owns row 32 (w % 4) + l and columns
+// 16 (w / 4) .. + 15.
+constexpr int OZ_NBUF = 3;
+constexpr int OZ_PWARPS = 16;
+constexpr int OZ_PRODUCERS = 32 * OZ_PWARPS;
+constexpr int OZ_THREADS = OZ_PRODUCERS + 32;      // 17 warps
+constexpr int OZ_FG = 4;                           // stages per X read group
+constexpr int OZ_DC = OZ_N / (OZ_PWARPS / 4);      // columns drained per thread (16)
+constexpr int OZ_SA = OZ_S * OZ_M * OZ_KS * 2;     // A half of a stage buffer (28 KB)
+constexpr int OZ_SB = OZ_S * OZ_N * OZ_KS * 2;     // B half (14 KB)
+constexpr int OZ_ACC = 2 * OZ_M * OZ_N * 4;        // running sums, hi and lo (64 KB)
+static_assert((OZ_DRAIN / OZ_KS) % (2 * OZ_FG) == 0 && OZ_FG % 2 == 0, "chunks hold whole pairs of read groups");
+static_assert(OZ_PRODUCERS == OZ_N * (OZ_KS / 2), "one complex element per producer and stage");
+// the grouped MMAs: plane sb + 1 of a B stage starts where row OZ_N of plane sb
+// would (8-row groups (OZ_KS / 8) * 128 bytes apart), and the levels fit TMEM
+static_assert((OZ_N / 8) * ((OZ_KS / 8) * 128) == OZ_N * OZ_KS * 2, "B planes contiguous as rows");
+static_assert(OZ_LV * OZ_N <= OZ_TCOLS && 4 * OZ_N <= 256, "level columns");
 
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *__restrict__ As,
                                                         const double2 *__restrict__ X, long long N, long long ldX,
@@ -209,23 +267,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                                                         long long ldC, long long col_off, int *err,
                                                         unsigned long long wait) {
     extern __shared__ __align__(1024) uint8_t dsm[];
-    constexpr int SA = OZ_S * OZ_M * OZ_KS * 2, SB = OZ_S * OZ_N * OZ_KS * 2;  // 28 KB, 14 KB per buffer
     __shared__ __align__(8) uint64_t afull[OZ_NBUF], bfull[OZ_NBUF], done[OZ_NBUF], cdone;
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool producer = threadIdx.x < OZ_PRODUCERS;
+    const bool producer = warp < OZ_PWARPS;
     const bool issuer = threadIdx.x == OZ_PRODUCERS;
-    const int row = 32 * (warp & 3) + lane, cbase = 32 * ((warp >> 2) & 1);
+    const int row = 32 * (warp & 3) + lane, cbase = OZ_DC * ((warp >> 2) & 3);
     const long long ct = blockIdx.x, rt = blockIdx.y;
     const long long j0 = ct * OZ_N, r0 = rt * OZ_M;
-    float acc_h[32], acc_l[32];
+    float *acc_hs = (float *)(dsm + OZ_NBUF * (OZ_SA + OZ_SB));  // [column][row]
+    float *acc_ls = acc_hs + OZ_M * OZ_N;
+    if (producer)
 #pragma unroll
-    for (int c = 0; c < 32; c++) acc_h[c] = acc_l[c] = 0.f;
+        for (int c = 0; c < OZ_DC; c++) acc_hs[(cbase + c) * OZ_M + row] = acc_ls[(cbase + c) * OZ_M + row] = 0.f;
     if (warp == 0) tmem_alloc(&tslot, OZ_TCOLS);
     if (threadIdx.x == 0) {
         for (int b = 0; b < OZ_NBUF; b++) {
             mbar_init(&afull[b], 1);
-            mbar_init(&bfull[b], OZ_PRODUCERS);
+            mbar_init(&bfull[b], OZ_PWARPS);
             mbar_init(&done[b], 1);
         }
         mbar_init(&cdone, 1);
@@ -234,112 +293,129 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
-    constexpr uint32_t idesc = idesc_bf16_f32(OZ_M, OZ_N);
     bool ok = true;
-    const long long nst = Kp / OZ_KS;
+    const int nst = (int)(Kp / OZ_KS);  // Kp <= 2^23
     constexpr int per_drain = OZ_DRAIN / OZ_KS;
-    auto bufA = [&](long long st) { return dsm + (int)(st % OZ_NBUF) * (SA + SB); };
-    auto bufB = [&](long long st) { return dsm + (int)(st % OZ_NBUF) * (SA + SB) + SA; };
-    auto par = [&](long long st) { return (uint32_t)((st / OZ_NBUF) & 1); };
-    // producer: this thread's column and the two complex elements of a stage
-    const int jj = threadIdx.x >> 2, p0 = (threadIdx.x & 3) * 2;
+    const uint32_t dsm0 = smem_u32(dsm);
+    // producer: this thread's column and complex element of a stage
+    const int jj = (threadIdx.x >> 3) & (OZ_N - 1), p0 = threadIdx.x & 7;
     const long long j = j0 + jj;
     const bool live = producer && j < Mb;
     const int E = live ? Eb[j] : 0;
-    const double2 *x = X + (live ? j : 0) * ldX;
-    constexpr long long pstride2 = OZ_N * OZ_KS / 2;
-    const uint32_t off0 = kmajor_off(jj & (OZ_N - 1), 2 * p0, OZ_KS) >> 1,
-                   off1 = kmajor_off(jj & (OZ_N - 1), 2 * p0 + 2, OZ_KS) >> 1;
-    // two register sets: stage st uses set st % 2 (X read OZ_AHEAD = 2 stages ahead)
-    double2 xa0, xa1, xb0, xb1;
-    auto fetch = [&](long long st, double2 &v0, double2 &v1) {
-        const long long i0 = st * (OZ_KS / 2) + p0;
-        v0 = (live && i0 < N) ? x[i0] : make_double2(0.0, 0.0);
-        v1 = (live && i0 + 1 < N) ? x[i0 + 1] : make_double2(0.0, 0.0);
+    const double2 *x = X + (live ? j : 0) * ldX + p0;
+    const int nlim = live ? (int)((N - p0 + (OZ_KS / 2) - 1) / (OZ_KS / 2)) : 0;  // stages holding this element
+    constexpr int pstride = OZ_N * OZ_KS / 2;  // plane stride in 32-bit words
+    const uint32_t woff = kmajor_off(jj, 2 * p0, OZ_KS) >> 2;
+    // two register sets of OZ_FG stages: read group q (stages OZ_FG q ..) uses set q % 2
+    double2 xa[OZ_FG], xb[OZ_FG];
+    auto fetch = [&](int q, double2 (&v)[OZ_FG]) {
+#pragma unroll
+        for (int u = 0; u < OZ_FG; u++) {
+            const int st = q * OZ_FG + u;
+            v[u] = st < nlim ? x[(long long)st * (OZ_KS / 2)] : make_double2(0.0, 0.0);
+        }
     };
+    const int ngr = (nst + OZ_FG - 1) / OZ_FG;
     if (producer) {
-        fetch(0, xa0, xa1);
-        if (nst > 1) fetch(1, xb0, xb1);
+        fetch(0, xa);
+        if (ngr > 1) fetch(1, xb);
     }
-    auto produce = [&](long long st, double2 &v0, double2 &v1) {
-        if (st >= OZ_NBUF) ok = mbar_wait(&done[st % OZ_NBUF], par(st - OZ_NBUF), wait) && ok;
-        __nv_bfloat16 *blk = (__nv_bfloat16 *)bufB(st);
-        const long long i0 = st * (OZ_KS / 2) + p0;
-        __nv_bfloat162 *o0 = (__nv_bfloat162 *)(blk + off0), *o1 = (__nv_bfloat162 *)(blk + off1);
-        const __nv_bfloat162 z2 = __floats2bfloat162_rn(0.f, 0.f);
-        if (live && i0 < N) slice7_pair(v0.x, v0.y, E, o0, pstride2);
-        else
+    auto load_a = [&](int st, int bb) {  // issuer
+        uint64_t *fb = &afull[bb];
+        mbar_expect_tx(fb, OZ_SA);
+        bulk_g2s(dsm + bb * (OZ_SA + OZ_SB), As + (rt * nst + st) * (long long)(OZ_S * OZ_M * OZ_KS), OZ_SA, fb);
+    };
+    // stage st: buffer b, phase parity ph (of this use of the buffer)
+    int b = 0;
+    uint32_t ph = 0;
+    auto advance = [&]() {
+        if (++b == OZ_NBUF) {
+            b = 0;
+            ph ^= 1u;
+        }
+    };
+    // store the slice words of stage st (zeros past the column's end) once
+    // its buffer is free; the warp's stores become visible to the tensor
+    // core, then one lane arrives
+    auto put = [&](int st, const uint32_t (&w)[OZ_S]) {
+        if (st >= OZ_NBUF) ok = mbar_wait(&done[b], ph ^ 1u, wait) && ok;  // the MMAs of stage st - OZ_NBUF
+        uint32_t *o = (uint32_t *)(dsm + b * (OZ_SA + OZ_SB) + OZ_SA) + woff;
+        const bool in = st < nlim;
 #pragma unroll
-            for (int sl = 0; sl < OZ_S; sl++) o0[sl * pstride2] = z2;
-        if (live && i0 + 1 < N) slice7_pair(v1.x, v1.y, E, o1, pstride2);
-        else
-#pragma unroll
-            for (int sl = 0; sl < OZ_S; sl++) o1[sl * pstride2] = z2;
-        if (st + OZ_AHEAD < nst) fetch(st + OZ_AHEAD, v0, v1);
-        // this thread's stores become visible to the tensor core, then it arrives
+        for (int t = 0; t < OZ_S; t++) o[t * pstride] = in ? w[t] : 0u;
         fence_async_smem();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[st % OZ_NBUF])) : "memory");
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[b])) : "memory");
+        advance();
     };
-    auto load_a = [&](long long st) {  // issuer only
-        uint64_t *fb = &afull[st % OZ_NBUF];
-        mbar_expect_tx(fb, SA);
-        bulk_g2s(bufA(st), As + (rt * nst + st) * (long long)(OZ_S * OZ_M * OZ_KS), SA, fb);
+    // a read group in pairs of stages: both stages' values are sliced first
+    // (independent work), then stored in order
+    auto group = [&](int q, int ce, double2 (&v)[OZ_FG]) {
+#pragma unroll
+        for (int u = 0; u < OZ_FG; u += 2) {
+            const int st = q * OZ_FG + u;
+            uint32_t w0[OZ_S], w1[OZ_S];
+            slice7_words(v[u].x, v[u].y, E, w0);
+            slice7_words(v[u + 1].x, v[u + 1].y, E, w1);
+            if (st < ce) put(st, w0);
+            if (st + 1 < ce) put(st + 1, w1);
+        }
+        if (q + 2 < ngr) fetch(q + 2, v);
     };
-    if (issuer)
-        for (long long st = 0; st < OZ_NBUF - 1 && st < nst; st++) load_a(st);
-    for (long long cs = 0; cs < nst; cs += per_drain) {
-        const long long ce = cs + per_drain < nst ? cs + per_drain : nst;
-        if (producer) {
-            // per_drain is even, so stage st always meets set st % 2
-            for (long long st = cs; st < ce; st += 2) {
-                produce(st, xa0, xa1);
-                if (st + 1 < ce) produce(st + 1, xb0, xb1);
-            }
-        } else if (issuer) {
-            for (long long st = cs; st < ce; st++) {
-                const int b = (int)(st % OZ_NBUF);
-                ok = mbar_wait(&afull[b], par(st), wait) && ok;
-                ok = mbar_wait(&bfull[b], par(st), wait) && ok;
-                tc_fence_after();
-                // one descriptor per operand and stage; slices and K steps are
-                // constant offsets of its 16-byte address field
-                const uint64_t ad0 = smem_desc(smem_u32(bufA(st)), 128, (OZ_KS / 8) * 128);
-                const uint64_t bd0 = smem_desc(smem_u32(bufB(st)), 128, (OZ_KS / 8) * 128);
-                const uint32_t acc0 = st == cs ? 0u : 1u;  // a chunk's first stage overwrites the levels
+    auto issue = [&](int st, int cs) {
+        ok = mbar_wait(&afull[b], ph, wait) && ok;
+        ok = mbar_wait(&bfull[b], ph, wait) && ok;
+        tc_fence_after();
+        // one descriptor per operand and stage; slices and K steps are
+        // constant offsets of its 16-byte address field
+        const uint32_t base = dsm0 + (uint32_t)(b * (OZ_SA + OZ_SB));
+        const uint64_t ad0 = smem_desc(base, 128, (OZ_KS / 8) * 128);
+        const uint64_t bd0 = smem_desc(base + OZ_SA, 128, (OZ_KS / 8) * 128);
+        const uint32_t acc0 = st == cs ? 0u : 1u;  // a chunk's first stage overwrites the levels
 #pragma unroll
-                for (int sa = 0; sa < OZ_S; sa++)
+        for (int sa = 0; sa < OZ_S; sa++)
 #pragma unroll
-                    for (int sb = 0; sb < OZ_S; sb++) {
-                        const int L = sa + sb;  // level - 2
-                        if (L >= OZ_LV) continue;
+            for (int sb = 0; sb < OZ_S - sa; sb += 4) {
+                const int g = OZ_S - sa - sb < 4 ? OZ_S - sa - sb : 4;
+                const int L = sa + sb;  // first level - 2
 #pragma unroll
-                        for (int kk = 0; kk < OZ_KS / 16; kk++) {
-                            const uint64_t ad = ad0 + (uint64_t)((sa * (OZ_M * OZ_KS * 2) + kk * 256) >> 4);
-                            const uint64_t bd = bd0 + (uint64_t)((sb * (OZ_N * OZ_KS * 2) + kk * 256) >> 4);
-                            // level L is first reached at sa = 0 (sb = L <= 6)
-                            const uint32_t ac = (sa == 0 && kk == 0) ? acc0 : 1u;
-                            tc_mma_bf16(tmem + (uint32_t)(L * OZ_N), ad, bd, idesc, ac);
-                        }
-                    }
-                tc_commit(&done[b]);
-                // A of stage st + OZ_NBUF - 1 into the buffer of stage st - 1
-                if (st + OZ_NBUF - 1 < nst) {
-                    if (st >= 1) ok = mbar_wait(&done[(st - 1) % OZ_NBUF], par(st - 1), wait) && ok;
-                    load_a(st + OZ_NBUF - 1);
+                for (int kk = 0; kk < OZ_KS / 16; kk++) {
+                    const uint64_t ad = ad0 + (uint64_t)((sa * (OZ_M * OZ_KS * 2) + kk * 256) >> 4);
+                    const uint64_t bd = bd0 + (uint64_t)((sb * (OZ_N * OZ_KS * 2) + kk * 256) >> 4);
+                    // every level is first reached at sa = 0 (sb = L <= 6)
+                    const uint32_t ac = (sa == 0 && kk == 0) ? acc0 : 1u;
+                    tc_mma_bf16(tmem + (uint32_t)(L * OZ_N), ad, bd, idesc_bf16_f32(OZ_M, g * OZ_N), ac);
                 }
             }
-            tc_commit(&cdone);
+        tc_commit(&done[b]);
+        // A of stage st + OZ_NBUF - 1 into the buffer of stage st - 1, once
+        // the MMAs of stage st - 1 are complete
+        if (st + OZ_NBUF - 1 < nst) {
+            const int bp = b == 0 ? OZ_NBUF - 1 : b - 1;
+            if (st >= 1) ok = mbar_wait(&done[bp], b == 0 ? ph ^ 1u : ph, wait) && ok;
+            load_a(st + OZ_NBUF - 1, bp);
         }
-        // drain (producer threads): wait for the chunk's MMAs (cdone completes
-        // once per chunk and no thread runs more than one chunk behind), then
-        // read this thread's TMEM lane; levels combined smallest first, in
-        // double-float
+        advance();
+    };
+    if (issuer)
+        for (int st = 0; st < OZ_NBUF - 1 && st < nst; st++) load_a(st, st);
+    for (int cs = 0; cs < nst; cs += per_drain) {
+        const int ce = cs + per_drain < nst ? cs + per_drain : nst;
         if (producer) {
+            // a chunk holds an even number of read groups, so group q meets set q % 2
+            for (int q = cs / OZ_FG; q * OZ_FG < ce; q += 2) {
+                group(q, ce, xa);
+                if ((q + 1) * OZ_FG < ce) group(q + 1, ce, xb);
+            }
+            // drain: wait for the chunk's MMAs (cdone completes once per chunk
+            // and no thread runs more than one chunk behind), then read this
+            // thread's TMEM lane; levels combined smallest first, in double-float
             ok = mbar_wait(&cdone, (uint32_t)((cs / per_drain) & 1), wait) && ok;
             tc_fence_after();
             const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
 #pragma unroll
-            for (int h = 0; h < 8; h++) {
+            for (int h = 0; h < OZ_DC / 4; h++) {
                 float v[OZ_LV][4];
                 tmem_ld4_levels(tmem + lane_off + (uint32_t)(cbase + 4 * h), v);
 #pragma unroll
@@ -351,9 +427,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                         float xl = v[L][e] * __int_as_float((127 - OZ_BITS * (L + 2)) << 23);
                         dfs_add(th, tl, xl, 0.f);
                     }
-                    dfs_add(acc_h[4 * h + e], acc_l[4 * h + e], th, tl);
+                    const int a = (cbase + 4 * h + e) * OZ_M + row;
+                    float ah = acc_hs[a], al = acc_ls[a];
+                    dfs_add(ah, al, th, tl);
+                    acc_hs[a] = ah;
+                    acc_ls[a] = al;
                 }
             }
+        } else if (issuer) {
+            for (int st = cs; st < ce; st++) issue(st, cs);
+            tc_commit(&cdone);
         }
         tc_fence_before();
         __syncthreads();
@@ -367,9 +450,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         const int Ex = Ea[l];
         double *crow = (double *)(C + (long long)l * ldC) + (R & 1);
 #pragma unroll
-        for (int c = 0; c < 32; c++) {
+        for (int c = 0; c < OZ_DC; c++) {
             const long long jc = j0 + cbase + c;
-            if (jc < Mb) crow[2 * (col_off + jc)] = ldexp((double)acc_h[c] + (double)acc_l[c], Ex + Eb[jc]);
+            const int a = (cbase + c) * OZ_M + row;
+            if (jc < Mb) crow[2 * (col_off + jc)] = ldexp((double)acc_hs[a] + (double)acc_ls[a], Ex + Eb[jc]);
         }
     }
     tc_fence_before();
@@ -421,7 +505,7 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
     k_oz_slice_A<<<k, 256, 0, s>>>(Q, N, k, ldQ, Kp, Rp, As, Ea);
     const long long ge = (Mb * 32 + 255) / 256;
     k_oz_exp_B<<<(unsigned)(ge < 4096 ? ge : 4096), 256, 0, s>>>(X, N, Mb, ldX, Eb);
-    const size_t dsm = (size_t)OZ_NBUF * OZ_S * (OZ_M + OZ_N) * OZ_KS * 2;  // 210 KB ring
+    const size_t dsm = (size_t)OZ_NBUF * (OZ_SA + OZ_SB) + OZ_ACC;  // 126 KB ring + 64 KB running sums
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
