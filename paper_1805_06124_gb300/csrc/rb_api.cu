@@ -575,7 +575,7 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     size_t o_hp = L.add((size_t)kcap * nchunk * sizeof(double2));
     size_t np = (size_t)(G > gN ? G : gN);
     size_t o_np = L.add(np * 8), o_be = L.add((size_t)G * 8), o_bi = L.add((size_t)G * 8);
-    size_t o_bc = L.add((size_t)G * 4), o_cd = L.add((size_t)M * 8), o_ce = L.add((size_t)M * 8);
+    size_t o_cd = L.add((size_t)M * 8), o_ce = L.add((size_t)M * 8);
     size_t o_pv = L.add((size_t)M * lgcap * 8);
     // FP16 pieces of the basis for the projection onto lo, and their scales
     size_t o_ap = L.add(rbk::lo_pieces_bytes(N, kcap));
@@ -632,7 +632,6 @@ static rb_status greedy_split_device(rb_ctx *ctx, const void *hi, const void *lo
     p.eta = std::ldexp(1.0, -46) * std::sqrt((double)N);
     p.dacc = (double *)(w + o_da);
     p.dcnt = (int *)(w + o_dc);
-    p.bcount = (int *)(w + o_bc);
     p.nblk_cand = G;
     p.cand = (long long *)(w + o_cd);
     p.cand_err = (double *)(w + o_ce);

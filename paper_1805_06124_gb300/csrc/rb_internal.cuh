@@ -102,8 +102,7 @@ struct Prob {
     double *rpart;     // re-check row-chunk partials [pair][chunk][32]
     int *rtick;        // re-check chunk counters per (candidate, group) pair
     int lgcap;         // groups per candidate in pv
-    int *bcount;       // per-block candidate counts
-    int nblk_cand;     // blocks of the candidate kernels
+    int nblk_cand;     // blocks of the candidate kernel
     int *tc_err;       // set when a tensor-core wait ran out
     unsigned long long wait_cycles;  // budget of each tensor-core wait, SM clock cycles
     double switch_err; // split form: switch once every error is certified below switch_err * max ||s_j||^2 (0: off)

@@ -42,6 +42,17 @@ namespace rbk {
 // Rounding allowance of the FP32 chain norms (sums of at most 2^16 squares).
 constexpr float kNormUp = 1.001f;
 
+// An upper bound of sqrt(x) for x >= 0 from the FP32 square root: x rounded
+// up to FP32, the correctly rounded sqrtf (within half an ulp), and a factor
+// 1 + 2^-22 that covers that half ulp and the rounding of the product.  It
+// only scales the small terms of the bounds, so FP32 accuracy is ample, and
+// it keeps the FP64 square roots (long sequences on this GPU's FP64 pipe) out
+// of the per-column work.  x beyond the FP32 range gives +inf (a looser,
+// still valid bound).
+__device__ __forceinline__ double sqrt_up(double x) {
+    return (double)(sqrtf(__double2float_ru(x)) * 1.0000002384185791f);
+}
+
 // Certified bounds of the true error from the hi-only bookkeeping.
 //   e   = ||hi_j||^2 - acc~_j          ln  = ||lo_j|| (rounded up)
 //   Ec  = bound on |err(hi_j) - e|     n2  = ||s_j||^2 (FP64 bookkeeping slack)
@@ -49,15 +60,18 @@ __device__ __forceinline__ void split_bounds(double e, double Ec, float lonrm, d
                                              double &L) {
     const double ln = (double)lonrm;
     const double ehi_up = e + Ec > 0.0 ? e + Ec : 0.0;
-    const double r = sqrt(ehi_up) * (1.0 + 1e-15);
+    const double r = sqrt_up(ehi_up);
     const double slack = 8.0 * (k + 16) * 1.1102230246251565e-16 * n2;
     U = ehi_up + 2.0 * r * ln + ln * ln + slack;
     L = e - Ec - 2.0 * r * ln - slack;
 }
 
+__device__ __forceinline__ double ec_of(double eta, double nh2, double sabs, int k1) {
+    return 2.0 * eta * sqrt_up(nh2) * sabs + 3.0 * k1 * eta * eta * nh2;
+}
+
 __device__ __forceinline__ double col_ec(const Prob &p, long long j, int k1) {
-    const double nh2 = p.norm2_hi[j];
-    return 2.0 * p.eta * sqrt(nh2) * p.sabs[j] + 3.0 * k1 * p.eta * p.eta * nh2;
+    return ec_of(p.eta, p.norm2_hi[j], p.sabs[j], k1);
 }
 
 // ---------------------------------------------------------------- init
@@ -77,8 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_split_init(Prob p) {
         const float4 *l4 = reinterpret_cast<const float4 *>(l);
         Norm2Acc a{0.f, 0.f, 0.f};
         float bh = 0.f, bl = 0.f, c0 = 0.f, c1 = 0.f;
-        for (long long t = lane; t < n2; t += 32) {
-            float4 x = h4[t], y = l4[t];
+        auto slot = [&](const float4 &x, const float4 &y) {
             norm2_acc4(a, x, y);
             df_mac(bh, bl, x.x, 0.f, x.x, 0.f);
             df_mac(bh, bl, x.y, 0.f, x.y, 0.f);
@@ -86,7 +99,22 @@ __global__ void __launch_bounds__(kThreads) k_split_init(Prob p) {
             df_mac(bh, bl, x.w, 0.f, x.w, 0.f);
             c0 = fmaf(x.x, x.x, fmaf(x.y, x.y, c0));
             c1 = fmaf(x.z, x.z, fmaf(x.w, x.w, c1));
+        };
+        // U slots of hi and lo in flight per lane; each lane still takes its
+        // slots in increasing order
+        constexpr int U = 4;
+        long long t = lane;
+        for (; t + 32 * (U - 1) < n2; t += 32 * U) {
+            float4 x[U], y[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                x[u] = ld_stream(h4 + t + 32 * u);
+                y[u] = ld_stream(l4 + t + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) slot(x[u], y[u]);
         }
+        for (; t < n2; t += 32) slot(ld_stream(h4 + t), ld_stream(l4 + t));
         if ((p.N & 1) && lane == 0) {
             float2 x = h[p.N - 1], y = l[p.N - 1];
             norm2_acc2(a, x, y);
@@ -327,6 +355,7 @@ __global__ void __launch_bounds__(kThreads) k_bounds(Prob p) {
             st->ncand = 0;
         } else {
             st->ncand = -1;  // re-check needed
+            st->cand_total = 0;
         }
     }
 }
@@ -343,72 +372,38 @@ __device__ __forceinline__ bool recheck_active(const DevState *st) {
     return loop_active(st) && ld_volatile(&st->ncand) == -1;
 }
 
-// Deterministic gathering: block b owns the contiguous column range
-// [b*chunk, (b+1)*chunk); counts first, then writes at its exclusive prefix.
-__global__ void __launch_bounds__(kThreads) k_cand_count(Prob p) {
+// The candidate list: every unpicked column whose upper bound reaches the
+// largest lower bound, gathered with one atomic per warp.  The order of the
+// list does not matter: each candidate's re-check is its own and the exact
+// argmax breaks ties by column index.  The last block applies the switch rule
+// on the count.
+__global__ void __launch_bounds__(kThreads) k_cand(Prob p) {
     DevState *st = p.st;
     if (!recheck_active(st)) return;
     const int k1 = st->k;
     const double Lmax = st->Lmax;
-    const long long per = (p.M + gridDim.x - 1) / gridDim.x;
-    const long long j0 = blockIdx.x * per, j1 = j0 + per < p.M ? j0 + per : p.M;
-    int c = 0;
-    for (long long j = j0 + threadIdx.x; j < j1; j += blockDim.x) c += is_candidate(p, j, k1, Lmax);
-    c = (int)block_sum((double)c);
-    if (threadIdx.x == 0) p.bcount[blockIdx.x] = c;
-    // the last block turns the counts into exclusive prefixes (bases of the
-    // write pass) and publishes the total, once, through shared memory
-    if (!last_block(&st->ticket_aux)) return;
-    __shared__ int sc[4096];
-    const int G = gridDim.x;
-    for (int b = threadIdx.x; b < G; b += blockDim.x) sc[b] = __ldcg(p.bcount + b);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int b = 0; b < G; b++) {
-            int x = sc[b];
-            sc[b] = run;
-            run += x;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j0 = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; j0 < p.M; j0 += stride) {
+        const long long j = j0 + lane;
+        const bool c = j < p.M && is_candidate(p, j, k1, Lmax);
+        const unsigned m = __ballot_sync(0xffffffffu, c);
+        if (m) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&st->cand_total, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (c) p.cand[base + __popc(m & ((1u << lane) - 1u))] = j;
         }
-        st->cand_total = run;
+    }
+    if (!last_block(&st->ticket_aux)) return;
+    if (threadIdx.x == 0) {
         st->ticket_aux = 0;
-        if (run > p.switch_cand) {
+        if (ld_volatile(&st->cand_total) > p.switch_cand) {
             // the bounds no longer separate the columns: re-checking this many
             // would cost more than sweeping hi + lo, so switch instead
             st->switch_pending = 2;
             st->ncand = 0;
         }
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < G; b += blockDim.x) p.bcount[b] = sc[b];
-}
-
-__global__ void __launch_bounds__(kThreads) k_cand_write(Prob p) {
-    DevState *st = p.st;
-    if (!recheck_active(st)) return;
-    const int k1 = st->k;
-    const double Lmax = st->Lmax;
-    __shared__ int wcount[kThreads / 32];
-    const int base = p.bcount[blockIdx.x];  // exclusive prefix from k_cand_count
-    const long long per = (p.M + gridDim.x - 1) / gridDim.x;
-    const long long j0 = blockIdx.x * per, j1 = j0 + per < p.M ? j0 + per : p.M;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int off = base;
-    // process the range in rounds of blockDim.x columns, in index order
-    for (long long r = j0; r < j1; r += blockDim.x) {
-        long long j = r + threadIdx.x;
-        bool c = j < j1 && is_candidate(p, j, k1, Lmax);
-        unsigned m = __ballot_sync(0xffffffffu, c);
-        if (lane == 0) wcount[w] = __popc(m);
-        __syncthreads();
-        int before = 0, round = 0;
-        for (int x = 0; x < (int)(blockDim.x >> 5); x++) {
-            if (x < w) before += wcount[x];
-            round += wcount[x];
-        }
-        if (c) p.cand[off + before + __popc(m & ((1u << lane) - 1u))] = j;
-        off += round;
-        __syncthreads();
     }
 }
 
@@ -1097,10 +1092,9 @@ cudaError_t launch_split_iteration(const Prob &p, int grid, cudaStream_t s, int 
     (void)grid;
     k_sweep_hi<<<g_sweep, kThreads, 0, s>>>(p);
     k_bounds<<<p.nblk_cand, kThreads, 0, s>>>(p);
-    k_cand_count<<<p.nblk_cand, kThreads, 0, s>>>(p);
-    k_cand_write<<<p.nblk_cand, kThreads, 0, s>>>(p);
+    k_cand<<<p.nblk_cand, kThreads, 0, s>>>(p);
     k_recheck<<<g_re, kThreads, 0, s>>>(p);
-    if (nlaunch) *nlaunch += 5;
+    if (nlaunch) *nlaunch += 4;
     return cudaGetLastError();
 }
 
