@@ -796,6 +796,24 @@ __device__ __forceinline__ void lp_load(const Prob &p, const LpTile &T, long lon
     }
 }
 
+// L2 prefetch of this lane's lines of stage stg, by the lanes that start a
+// 128-byte line ((lane & 7) == 0), for stages wholly inside the columns: the
+// loads into registers (one stage ahead) then find their lines in L2, so the
+// DRAM reads in flight do not depend on registers.
+constexpr int LP_PF = 4;  // stages of lo prefetched into L2 ahead
+__device__ __forceinline__ void lp_prefetch(const Prob &p, const LpTile &T, long long stg, long long nfull) {
+    const int lane = threadIdx.x & 31;
+    if ((lane & 7) != 0 || stg >= nfull) return;
+    const long long gstride = 64 * (p.ldH >> 1);
+#pragma unroll
+    for (int x = 0; x < LP_GROUPS; x++) {
+        if (!(T.valid & (1u << x))) continue;
+#pragma unroll
+        for (int i = 0; i < LP_CH; i++)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(T.base + x * gstride + stg * (LKC / 4) + 8 * i));
+    }
+}
+
 // Converts the stage held in R into the two B piece tiles of the buffer at
 // sB: lanes L and L^1 hold the two halves (4 K entries each) of one 16-byte
 // core-matrix row of column 4 g + (L >> 3); the lane with the lower half
@@ -902,8 +920,10 @@ __global__ void __launch_bounds__(LP_THREADS, 1) k_lo_project_tc(Prob p, int nt,
 #pragma unroll
             for (int a = 0; a < LP_AHEAD; a++)
                 if (a < nstg) lp_load(p, T, a, nfull, R[a]);
+            for (int a = LP_AHEAD; a < LP_PF; a++) lp_prefetch(p, T, a, nfull);
             auto produce = [&](long long s, const LpRegs &Rc, LpRegs &Rn) {
                 if (s + LP_AHEAD < nstg) lp_load(p, T, s + LP_AHEAD, nfull, Rn);
+                lp_prefetch(p, T, s + LP_PF, nfull);
                 const long long g = g0 + s;
                 uint64_t *fb = &bfull[g % LP_NBUF];
                 if (g >= LP_NBUF) {
