@@ -572,9 +572,58 @@ def run_streamed_once(args):
                       "in_core_ms": round(ms_ref, 3), "k": k, "runs": runs, "clocks": clk.summary()}), flush=True)
 
 
+def _host_available_bytes():
+    """MemAvailable of this node in bytes (0 when unknown)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return float(line.split()[1]) * 1024.0
+    except OSError:
+        pass
+    return 0.0
+
+
+def _sharded_e2e(args, torch, dist, world, S, r, step, per):
+    """The sharded greedy end to end: every step copies this rank's columns
+    from pinned host memory into the buffer its shard reads, runs the
+    sharded greedy and copies the basis and this rank's coefficient rows
+    back to pinned memory."""
+    S_host = torch.empty(S.shape, dtype=S.dtype, pin_memory=True)
+    S_host.copy_(S)
+    out = r["shards"][0]
+    Q_host = torch.empty(out["Q"].shape, dtype=out["Q"].dtype, pin_memory=True)
+    C_host = torch.empty(out["C"].shape, dtype=out["C"].dtype, pin_memory=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ks_e = []
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev2.record()
+    for _ in range(args.steps):
+        S.copy_(S_host, non_blocking=True)
+        re = step()
+        o = re["shards"][0]
+        Q_host[:o["Q"].shape[0]].copy_(o["Q"], non_blocking=True)
+        C_host[:o["C"].shape[0]].copy_(o["C"], non_blocking=True)
+        ks_e.append(re["k"])
+    ev3.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_e_max, nbytes_e = reduce_across_ranks(dist, ev2.elapsed_time(ev3), sum(ks_e) * per)
+    e2e = {"value": round(nbytes_e / (ms_e_max * 1e-3) / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": int(S.numel() * 16 * world),
+           "d2h_bytes_per_step": int((Q_host.numel() + C_host.numel()) * 16 * world),
+           "ms_per_step": round(ms_e_max / max(args.steps, 1), 3),
+           "path": "each rank's columns copied from pinned host memory into the device buffer its shard reads, "
+                   "then the sharded greedy; basis and coefficient rows copied back to pinned memory"}
+    return e2e
+
+
 def run_sharded(args):
-    """The column-sharded greedy (the paper's parallel scheme, Sec. 6.1.4 /
-    6.2) over torch.distributed: rank r owns columns r M .. (r+1) M - 1 of one
+    """The column-sharded greedy (the paper's parallel scheme, Sec. 6.1.3)
+    over torch.distributed: rank r owns columns r M .. (r+1) M - 1 of one
     N x (world M) chirp matrix (q, m drawn once for all columns, seed 1), so
     per-GPU work is fixed as the job grows (weak scaling, as in the paper's
     experiments).  Per iteration: one max-loc all-gather and one broadcast of
@@ -624,6 +673,22 @@ def run_sharded(args):
     value = nbytes / (ms_max * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     k = ks[-1]
+    # end to end, when the pinned copies of every rank's columns on this node
+    # fit well inside its available host memory (every rank decides alike)
+    local_world = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+    need = float(S.numel() * 16 * local_world)
+    fits = need < 0.6 * _host_available_bytes()
+    if dist:
+        t = torch.tensor([1.0 if fits else 0.0], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        fits = t.item() > 0.5
+    if fits:
+        e2e = _sharded_e2e(args, torch, dist, world, S, r, step, per)
+    else:
+        e2e = {"value": None, "unit": "GB/s", "h2d_bytes_per_step": int(S.numel() * 16 * world),
+               "d2h_bytes_per_step": 0,
+               "skipped": f"pinned copies of every rank's columns would take {need / 1e9:.0f} GB of this "
+                          f"node's {_host_available_bytes() / 1e9:.0f} GB of available host memory"}
     launches = args.steps and int(sum(2 + kk * (3 + 2 * 4 + 1) for kk in ks) * world)
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -637,8 +702,7 @@ def run_sharded(args):
                            "l2": "inputs larger than L2 (S is 34 GB per GPU; no flush needed)",
                            "parallelism": f"column-sharded over {world} GPU(s): max-loc all-gather + pivot-column "
                                           f"broadcast per iteration ({'NCCL' if dist else 'one process'})"},
-                "clocks": clk.summary(), "gpu_launches": launches,
-                "e2e": None, "e2e_note": "the sharded path is timed on device-resident columns only"}
+                "clocks": clk.summary(), "gpu_launches": launches, "e2e": e2e}
         print(json.dumps(line), flush=True)
     shard.close()
     ctx.close()

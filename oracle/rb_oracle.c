@@ -180,7 +180,7 @@ int orc_rb_greedy(const double *S, i64 N, i64 M, i64 ldS, double tol, int kmax,
     int status = ORC_OK, bad = 0;
     /* Alg. 3 steps "Define sigma_0(s_i) = ||s_i||" and "j(0) = arg sup".
      * Columns are independent; built with -fopenmp (the paper's shared-memory
-     * scheme, Sec. 6.2) they are split over threads, each column still summed
+     * scheme, Sec. 6.1.3) they are split over threads, each column still summed
      * sequentially, so the results do not depend on the thread count. */
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (i64 j = 0; j < M; j++) {

@@ -1,10 +1,14 @@
 """Column-sharded RB-greedy: the exchange of the paper's parallel scheme.
 
-Sec. 6.1.4 and Sec. 6.2 of the paper distribute the snapshot columns over MPI
-processes: each process searches its own columns for the next pivot, the
-processes agree on the global pivot with a max-loc reduction, the owner sends
-that column, and every process orthogonalises it against its own copy of the
-basis.  This module is that exchange, around per-rank engines that do the
+The paper's parallel code (Sec. 6.1.3) distributes the snapshot columns over
+MPI processes: each process updates its columns' errors and finds its local
+maximum, the processes agree on the global pivot with a max-loc all-reduce,
+and the owner sends that column to a master process, which orthogonalises it
+and broadcasts the new basis vector.  Here the owner broadcasts the pivot
+column instead and every process orthogonalises it against its own copy of
+the basis (the same deterministic kernels on identical inputs give identical
+vectors), so one collective carries the column and no process waits for a
+master.  This module is that exchange, around per-rank engines that do the
 arithmetic:
 
   * ``rb.Shard`` -- one GPU's columns through the C ABI (``rb_shard_*``); the

@@ -1,5 +1,5 @@
 """The exchange of the column-sharded greedy (paper_1805_06124_gb300.sharded,
-the paper's parallel scheme of Sec. 6.1.4 / 6.2) on two gloo ranks on the CPU.
+the paper's parallel scheme of Sec. 6.1.3) on two gloo ranks on the CPU.
 
 Each rank's arithmetic is a small numpy engine written here (test code: norms,
 CGS-form IMGS passes with Hoffmann's kappa test, the Eq. (Residual)
