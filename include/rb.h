@@ -474,7 +474,7 @@ rb_status rb_mlp_train(rb_mlp *mlp, const float *X, const float *T, long long ro
  *     before it, on every return path.
  *   - errbuf (may be NULL, errlen bytes) receives a message on failure.
  *   - The first call for a device looks up the array's device address with
- *     that device current; make it before any stream capture.
+ *     that device current (one runtime call per device and process).
  *   - Every call shares the array; calls whose work overlaps on the GPU
  *     (other streams, other host threads) race and must be serialised by the
  *     caller.

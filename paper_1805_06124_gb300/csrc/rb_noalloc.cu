@@ -14,8 +14,7 @@
 //
 // In host code the symbol g_noalloc_scratch is only a host-side stand-in:
 // its device address is obtained with cudaGetSymbolAddress, once per device,
-// with that device current, on the first call made for that device.  Make
-// that first call before any stream capture.
+// with that device current, on the first call made for that device.
 //
 // Every call shares the array and the array keeps the previous call's
 // contents; the call clears what has to start at zero (the loop state) and
