@@ -225,45 +225,69 @@ __device__ __forceinline__ void slice7_words(double re, double im, int E, uint32
     for (int t = 0; t < OZ_S; t++) w[t] = __byte_perm(__float_as_uint(a[t]), __float_as_uint(c[t]), 0x7632);
 }
 
-// The GEMM with the snapshot slicing inside it.  Warps 0-15 (512 producer
-// threads) read X and write the seven B slice planes of each K stage straight
-// into the stage's shared-memory buffer: thread t owns column 64 ct + t / 8
-// and complex element t % 8 of every stage, and reads X in groups of OZ_FG
-// stages (512 contiguous bytes per column per group), two groups ahead of
-// the slicing.  Lane 0 of warp 16 fills the A half of each buffer with one
-// bulk copy of the pre-sliced basis (28 KB, L2-resident) and issues the
-// stage's MMAs: slice sa of A against the consecutive B planes sb .. sb+g-1
-// as one operand of 64 g rows (the planes are 64 rows apart in the K-major
-// layout), whose product lands on the TMEM levels sa+sb .. sa+sb+g-1 (the
-// levels are 64 columns apart) -- 10 MMAs of N = 64 .. 256 per stage.
-// Barriers per buffer: "afull" counts the A bytes, "bfull" one arrival per
-// producer warp, "done" receives the MMA commit; the n-th phase of buffer b
-// belongs to stage b + OZ_NBUF n (buffer and phase parity are carried along
-// with the stage).  At the end of each exact chunk (OZ_DRAIN K values) the
-// producers drain the TMEM levels into double-float running sums kept in
-// shared memory (column-major, so a warp's 32 rows are 32 consecutive
-// words): thread (warp w, lane l) owns row 32 (w % 4) + l and columns
-// 16 (w / 4) .. + 15.
+// The GEMM with the snapshot slicing inside it, persistent and stream-K.
+// A work unit is one exact chunk (OZ_DRAIN K values = OZ_CHUNK stages) of one
+// tile of 128 basis rows by 64 snapshot columns (K is padded to whole chunks
+// with zero basis planes); tile t is row tile t % nrt, column tile t / nrt.
+// Block i of G takes the contiguous units [i U / G, (i+1) U / G), so every
+// block does the same work whatever the tile count.  A tile whose chunks all
+// fall to one block is written to C by it; a tile shared by blocks leaves
+// each block's part (unscaled double sums) in that block's slot -- 2i when
+// the tile is the block's first, 2i + 1 when it is its last -- and
+// k_oz_fixup adds the parts in chunk order.
+//
+// Roles.  Warps 0-15 (512 producer threads) read X and write the seven B
+// slice planes of each stage straight into the stage's shared-memory buffer:
+// thread t owns column 64 ct + t / 8 and complex element t % 8 of every
+// stage, and reads X in groups of OZ_FG stages (512 contiguous bytes per
+// column per group), two groups ahead of the slicing.  Lane 0 of warp 16
+// fills the A half of each buffer with one bulk copy of the pre-sliced basis
+// (28 KB, L2-resident) and issues the stage's MMAs: slice sa of A against the
+// consecutive B planes sb .. sb+g-1 as one operand of 64 g rows (the planes
+// are 64 rows apart in the K-major layout), whose product lands on the TMEM
+// levels sa+sb .. sa+sb+g-1 (the levels are 64 columns apart) -- 10 MMAs of
+// N = 64 .. 256 per stage.  Barriers per buffer: "afull" counts the A bytes,
+// "bfull" one arrival per producer warp, "done" receives the MMA commit; the
+// n-th phase of buffer b belongs to the block's stage b + OZ_NBUF n (buffer
+// and phase parity are carried along with the stage count).  At the end of
+// each unit the producers drain the TMEM levels into double-float running
+// sums kept in shared memory (column-major, so a warp's 32 rows are 32
+// consecutive words): thread (warp w, lane l) owns row 32 (w % 4) + l and
+// columns 16 (w / 4) .. + 15.
 constexpr int OZ_NBUF = 3;
 constexpr int OZ_PWARPS = 16;
 constexpr int OZ_PRODUCERS = 32 * OZ_PWARPS;
 constexpr int OZ_THREADS = OZ_PRODUCERS + 32;      // 17 warps
 constexpr int OZ_FG = 4;                           // stages per X read group
+constexpr int OZ_CHUNK = OZ_DRAIN / OZ_KS;         // stages per work unit (32)
 constexpr int OZ_DC = OZ_N / (OZ_PWARPS / 4);      // columns drained per thread (16)
 constexpr int OZ_SA = OZ_S * OZ_M * OZ_KS * 2;     // A half of a stage buffer (28 KB)
 constexpr int OZ_SB = OZ_S * OZ_N * OZ_KS * 2;     // B half (14 KB)
 constexpr int OZ_ACC = 2 * OZ_M * OZ_N * 4;        // running sums, hi and lo (64 KB)
-static_assert((OZ_DRAIN / OZ_KS) % (2 * OZ_FG) == 0 && OZ_FG % 2 == 0, "chunks hold whole pairs of read groups");
+constexpr int OZ_MAX_BLOCKS = 256;                 // blocks of the persistent launch (at most)
+static_assert(OZ_CHUNK % (2 * OZ_FG) == 0 && OZ_FG % 2 == 0, "units hold whole pairs of read groups");
 static_assert(OZ_PRODUCERS == OZ_N * (OZ_KS / 2), "one complex element per producer and stage");
 // the grouped MMAs: plane sb + 1 of a B stage starts where row OZ_N of plane sb
 // would (8-row groups (OZ_KS / 8) * 128 bytes apart), and the levels fit TMEM
 static_assert((OZ_N / 8) * ((OZ_KS / 8) * 128) == OZ_N * OZ_KS * 2, "B planes contiguous as rows");
 static_assert(OZ_LV * OZ_N <= OZ_TCOLS && 4 * OZ_N <= 256, "level columns");
 
+// First unit of block i of G over U units.
+__host__ __device__ __forceinline__ long long oz_u0(long long i, long long U, long long G) { return i * U / G; }
+
+// The block whose range holds unit x.
+__device__ __forceinline__ int oz_block_of(long long x, long long U, int G) {
+    int i = (int)(x * G / U);
+    while (i + 1 < G && oz_u0(i + 1, U, G) <= x) i++;
+    while (i > 0 && oz_u0(i, U, G) > x) i--;
+    return i;
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *__restrict__ As,
                                                         const double2 *__restrict__ X, long long N, long long ldX,
                                                         const int *__restrict__ Ea, const int *__restrict__ Eb, int k,
-                                                        long long Mb, long long Kp, double2 *__restrict__ C,
+                                                        long long Mb, long long Kp, int nrt, long long U,
+                                                        double *__restrict__ part, double2 *__restrict__ C,
                                                         long long ldC, long long col_off, int *err,
                                                         unsigned long long wait) {
     extern __shared__ __align__(1024) uint8_t dsm[];
@@ -273,8 +297,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     const bool producer = warp < OZ_PWARPS;
     const bool issuer = threadIdx.x == OZ_PRODUCERS;
     const int row = 32 * (warp & 3) + lane, cbase = OZ_DC * ((warp >> 2) & 3);
-    const long long ct = blockIdx.x, rt = blockIdx.y;
-    const long long j0 = ct * OZ_N, r0 = rt * OZ_M;
     float *acc_hs = (float *)(dsm + OZ_NBUF * (OZ_SA + OZ_SB));  // [column][row]
     float *acc_ls = acc_hs + OZ_M * OZ_N;
     if (producer)
@@ -294,20 +316,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     tc_fence_after();
     const uint32_t tmem = tslot;
     bool ok = true;
-    const int nst = (int)(Kp / OZ_KS);  // Kp <= 2^23
-    constexpr int per_drain = OZ_DRAIN / OZ_KS;
+    const int nst = (int)(Kp / OZ_KS);  // whole units, Kp <= 2^23
+    const int nch = nst / OZ_CHUNK;
+    const int G = (int)gridDim.x;
+    const long long u0 = oz_u0(blockIdx.x, U, G), u1 = oz_u0(blockIdx.x + 1, U, G);
+    const long long t_first = u0 / nch;
     const uint32_t dsm0 = smem_u32(dsm);
-    // producer: this thread's column and complex element of a stage
+    // producer: this thread's column of a tile and its complex element of a stage
     const int jj = (threadIdx.x >> 3) & (OZ_N - 1), p0 = threadIdx.x & 7;
-    const long long j = j0 + jj;
-    const bool live = producer && j < Mb;
-    const int E = live ? Eb[j] : 0;
-    const double2 *x = X + (live ? j : 0) * ldX + p0;
-    const int nlim = live ? (int)((N - p0 + (OZ_KS / 2) - 1) / (OZ_KS / 2)) : 0;  // stages holding this element
     constexpr int pstride = OZ_N * OZ_KS / 2;  // plane stride in 32-bit words
     const uint32_t woff = kmajor_off(jj, 2 * p0, OZ_KS) >> 2;
+    int E = 0, nlim = 0;                       // of the current tile's column
+    const double2 *x = X;
     // two register sets of OZ_FG stages: read group q (stages OZ_FG q ..) uses set q % 2
     double2 xa[OZ_FG], xb[OZ_FG];
+    const int ngr = nst / OZ_FG;
     auto fetch = [&](int q, double2 (&v)[OZ_FG]) {
 #pragma unroll
         for (int u = 0; u < OZ_FG; u++) {
@@ -315,30 +338,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
             v[u] = st < nlim ? x[(long long)st * (OZ_KS / 2)] : make_double2(0.0, 0.0);
         }
     };
-    const int ngr = (nst + OZ_FG - 1) / OZ_FG;
-    if (producer) {
-        fetch(0, xa);
-        if (ngr > 1) fetch(1, xb);
-    }
-    auto load_a = [&](int st, int bb) {  // issuer
-        uint64_t *fb = &afull[bb];
-        mbar_expect_tx(fb, OZ_SA);
-        bulk_g2s(dsm + bb * (OZ_SA + OZ_SB), As + (rt * nst + st) * (long long)(OZ_S * OZ_M * OZ_KS), OZ_SA, fb);
-    };
-    // stage st: buffer b, phase parity ph (of this use of the buffer)
+    const long long gtot = (u1 - u0) * OZ_CHUNK;  // stages of this block
+    // the block's stage g: buffer b, phase parity ph (of this use of the buffer)
     int b = 0;
     uint32_t ph = 0;
+    long long g = 0;
     auto advance = [&]() {
+        g++;
         if (++b == OZ_NBUF) {
             b = 0;
             ph ^= 1u;
         }
     };
-    // store the slice words of stage st (zeros past the column's end) once
-    // its buffer is free; the warp's stores become visible to the tensor
+    // store the slice words of tile stage st (zeros past the column's end)
+    // once its buffer is free; the warp's stores become visible to the tensor
     // core, then one lane arrives
     auto put = [&](int st, const uint32_t (&w)[OZ_S]) {
-        if (st >= OZ_NBUF) ok = mbar_wait(&done[b], ph ^ 1u, wait) && ok;  // the MMAs of stage st - OZ_NBUF
+        if (g >= OZ_NBUF) ok = mbar_wait(&done[b], ph ^ 1u, wait) && ok;  // the MMAs of stage g - OZ_NBUF
         uint32_t *o = (uint32_t *)(dsm + b * (OZ_SA + OZ_SB) + OZ_SA) + woff;
         const bool in = st < nlim;
 #pragma unroll
@@ -351,67 +367,48 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     };
     // a read group in pairs of stages: both stages' values are sliced first
     // (independent work), then stored in order
-    auto group = [&](int q, int ce, double2 (&v)[OZ_FG]) {
+    auto group = [&](int q, double2 (&v)[OZ_FG]) {
 #pragma unroll
         for (int u = 0; u < OZ_FG; u += 2) {
             const int st = q * OZ_FG + u;
             uint32_t w0[OZ_S], w1[OZ_S];
             slice7_words(v[u].x, v[u].y, E, w0);
             slice7_words(v[u + 1].x, v[u + 1].y, E, w1);
-            if (st < ce) put(st, w0);
-            if (st + 1 < ce) put(st + 1, w1);
+            put(st, w0);
+            put(st + 1, w1);
         }
         if (q + 2 < ngr) fetch(q + 2, v);
     };
-    auto issue = [&](int st, int cs) {
-        ok = mbar_wait(&afull[b], ph, wait) && ok;
-        ok = mbar_wait(&bfull[b], ph, wait) && ok;
-        tc_fence_after();
-        // one descriptor per operand and stage; slices and K steps are
-        // constant offsets of its 16-byte address field
-        const uint32_t base = dsm0 + (uint32_t)(b * (OZ_SA + OZ_SB));
-        const uint64_t ad0 = smem_desc(base, 128, (OZ_KS / 8) * 128);
-        const uint64_t bd0 = smem_desc(base + OZ_SA, 128, (OZ_KS / 8) * 128);
-        const uint32_t acc0 = st == cs ? 0u : 1u;  // a chunk's first stage overwrites the levels
-#pragma unroll
-        for (int sa = 0; sa < OZ_S; sa++)
-#pragma unroll
-            for (int sb = 0; sb < OZ_S - sa; sb += 4) {
-                const int g = OZ_S - sa - sb < 4 ? OZ_S - sa - sb : 4;
-                const int L = sa + sb;  // first level - 2
-#pragma unroll
-                for (int kk = 0; kk < OZ_KS / 16; kk++) {
-                    const uint64_t ad = ad0 + (uint64_t)((sa * (OZ_M * OZ_KS * 2) + kk * 256) >> 4);
-                    const uint64_t bd = bd0 + (uint64_t)((sb * (OZ_N * OZ_KS * 2) + kk * 256) >> 4);
-                    // every level is first reached at sa = 0 (sb = L <= 6)
-                    const uint32_t ac = (sa == 0 && kk == 0) ? acc0 : 1u;
-                    tc_mma_bf16(tmem + (uint32_t)(L * OZ_N), ad, bd, idesc_bf16_f32(OZ_M, g * OZ_N), ac);
-                }
+    int seg_c0 = 0;  // first chunk of the current tile segment
+    if (producer) {
+    for (long long u = u0; u < u1; u++) {
+        const long long t = u / nch;
+        const int c = (int)(u % nch);
+        const int rt = (int)(t % nrt);
+        const long long ct = t / nrt;
+        if (u == u0 || c == 0) {  // a new tile: this thread's column, its scale and first reads
+            seg_c0 = c;
+            if (producer) {
+                const long long j = ct * OZ_N + jj;
+                const bool live = j < Mb;
+                E = live ? Eb[j] : 0;
+                x = X + (live ? j : 0) * ldX + p0;
+                nlim = live ? (int)((N - p0 + (OZ_KS / 2) - 1) / (OZ_KS / 2)) : 0;  // stages holding the element
+                fetch(c * (OZ_CHUNK / OZ_FG), xa);
+                fetch(c * (OZ_CHUNK / OZ_FG) + 1, xb);
             }
-        tc_commit(&done[b]);
-        // A of stage st + OZ_NBUF - 1 into the buffer of stage st - 1, once
-        // the MMAs of stage st - 1 are complete
-        if (st + OZ_NBUF - 1 < nst) {
-            const int bp = b == 0 ? OZ_NBUF - 1 : b - 1;
-            if (st >= 1) ok = mbar_wait(&done[bp], b == 0 ? ph ^ 1u : ph, wait) && ok;
-            load_a(st + OZ_NBUF - 1, bp);
         }
-        advance();
-    };
-    if (issuer)
-        for (int st = 0; st < OZ_NBUF - 1 && st < nst; st++) load_a(st, st);
-    for (int cs = 0; cs < nst; cs += per_drain) {
-        const int ce = cs + per_drain < nst ? cs + per_drain : nst;
         if (producer) {
-            // a chunk holds an even number of read groups, so group q meets set q % 2
-            for (int q = cs / OZ_FG; q * OZ_FG < ce; q += 2) {
-                group(q, ce, xa);
-                if ((q + 1) * OZ_FG < ce) group(q + 1, ce, xb);
+            const int q0 = c * (OZ_CHUNK / OZ_FG);
+            // a unit holds an even number of read groups, so group q meets set q % 2
+            for (int q = q0; q < q0 + OZ_CHUNK / OZ_FG; q += 2) {
+                group(q, xa);
+                group(q + 1, xb);
             }
-            // drain: wait for the chunk's MMAs (cdone completes once per chunk
-            // and no thread runs more than one chunk behind), then read this
+            // drain: wait for the unit's MMAs (cdone completes once per unit and
+            // no thread runs more than one unit behind), then read this
             // thread's TMEM lane; levels combined smallest first, in double-float
-            ok = mbar_wait(&cdone, (uint32_t)((cs / per_drain) & 1), wait) && ok;
+            ok = mbar_wait(&cdone, (uint32_t)((u - u0) & 1), wait) && ok;
             tc_fence_after();
             const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
 #pragma unroll
@@ -434,31 +431,130 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                     acc_ls[a] = al;
                 }
             }
-        } else if (issuer) {
-            for (int st = cs; st < ce; st++) issue(st, cs);
-            tc_commit(&cdone);
+            if (u == u1 - 1 || c == nch - 1) {
+                // the tile segment ends: the whole tile goes to C, a part to the
+                // block's slot; the sums restart for the next tile
+                const long long R = (long long)rt * OZ_M + row;
+                const bool whole = seg_c0 == 0 && c == nch - 1;
+                const long long slot = 2LL * blockIdx.x + (t == t_first ? 0 : 1);
+#pragma unroll
+                for (int cc = 0; cc < OZ_DC; cc++) {
+                    const int a = (cbase + cc) * OZ_M + row;
+                    const double val = (double)acc_hs[a] + (double)acc_ls[a];
+                    acc_hs[a] = acc_ls[a] = 0.f;
+                    const long long jc = ct * OZ_N + cbase + cc;
+                    if (whole) {
+                        if (R < 2LL * k && jc < Mb)
+                            ((double *)(C + (R >> 1) * ldC) + (R & 1))[2 * (col_off + jc)] =
+                                ldexp(val, Ea[R >> 1] + Eb[jc]);
+                    } else {
+                        part[(slot * OZ_N + cbase + cc) * OZ_M + row] = val;
+                    }
+                }
+            }
         }
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
     }
-    if (!ok && err) atomicExch(err, 1);
-    // write: row of the tile -> basis vector (r0 + row) / 2, Re or Im part
-    const long long R = r0 + row;
-    if (producer && R < 2LL * k) {
-        const int l = (int)(R >> 1);
-        const int Ex = Ea[l];
-        double *crow = (double *)(C + (long long)l * ldC) + (R & 1);
+    } else {
+        // warp 16 (lane 0 issues; the block barrier once per unit, as the producers)
+        // The basis copies go out in the block's stage order (units u0 .. in
+        // order, OZ_CHUNK stages each), so their source advances one stage at
+        // a time and is recomputed once per unit
+        constexpr long long a_stage = (long long)OZ_S * OZ_M * OZ_KS;  // elements per stage
+        auto unit_a = [&](long long u) {
+            const long long t = u / nch;
+            return As + ((t % nrt) * nst + (u % nch) * OZ_CHUNK) * a_stage;
+        };
+        long long a_u = u0;
+        int a_s = 0;
+        const __nv_bfloat16 *a_base = unit_a(u0);
+        auto load_a = [&](int bb) {  // the next stage's A into buffer bb
+            uint64_t *fb = &afull[bb];
+            mbar_expect_tx(fb, OZ_SA);
+            bulk_g2s(dsm + bb * (OZ_SA + OZ_SB), a_base + a_s * a_stage, OZ_SA, fb);
+            if (++a_s == OZ_CHUNK) {
+                a_s = 0;
+                if (++a_u < u1) a_base = unit_a(a_u);
+            }
+        };
+        auto issue = [&](bool first_of_unit) {
+            ok = mbar_wait(&afull[b], ph, wait) && ok;
+            ok = mbar_wait(&bfull[b], ph, wait) && ok;
+            tc_fence_after();
+            // one descriptor per operand and stage; slices and K steps are
+            // constant offsets of its 16-byte address field
+            const uint32_t base = dsm0 + (uint32_t)(b * (OZ_SA + OZ_SB));
+            const uint64_t ad0 = smem_desc(base, 128, (OZ_KS / 8) * 128);
+            const uint64_t bd0 = smem_desc(base + OZ_SA, 128, (OZ_KS / 8) * 128);
+            const uint32_t acc0 = first_of_unit ? 0u : 1u;  // a unit's first stage overwrites the levels
 #pragma unroll
-        for (int c = 0; c < OZ_DC; c++) {
-            const long long jc = j0 + cbase + c;
-            const int a = (cbase + c) * OZ_M + row;
-            if (jc < Mb) crow[2 * (col_off + jc)] = ldexp((double)acc_hs[a] + (double)acc_ls[a], Ex + Eb[jc]);
+            for (int sa = 0; sa < OZ_S; sa++)
+#pragma unroll
+                for (int sb = 0; sb < OZ_S - sa; sb += 4) {
+                    const int gg = OZ_S - sa - sb < 4 ? OZ_S - sa - sb : 4;
+                    const int L = sa + sb;  // first level - 2
+#pragma unroll
+                    for (int kk = 0; kk < OZ_KS / 16; kk++) {
+                        const uint64_t ad = ad0 + (uint64_t)((sa * (OZ_M * OZ_KS * 2) + kk * 256) >> 4);
+                        const uint64_t bd = bd0 + (uint64_t)((sb * (OZ_N * OZ_KS * 2) + kk * 256) >> 4);
+                        // every level is first reached at sa = 0 (sb = L <= 6)
+                        const uint32_t ac = (sa == 0 && kk == 0) ? acc0 : 1u;
+                        tc_mma_bf16(tmem + (uint32_t)(L * OZ_N), ad, bd, idesc_bf16_f32(OZ_M, gg * OZ_N), ac);
+                    }
+                }
+            tc_commit(&done[b]);
+            // A of stage g + OZ_NBUF - 1 into the buffer of stage g - 1, once the
+            // MMAs of stage g - 1 are complete
+            if (g + OZ_NBUF - 1 < gtot) {
+                const int bp = b == 0 ? OZ_NBUF - 1 : b - 1;
+                if (g >= 1) ok = mbar_wait(&done[bp], b == 0 ? ph ^ 1u : ph, wait) && ok;
+                load_a(bp);  // stage g + OZ_NBUF - 1
+            }
+            advance();
+        };
+        if (issuer)
+            for (long long gg = 0; gg < OZ_NBUF - 1 && gg < gtot; gg++) load_a((int)gg);
+        for (long long u = u0; u < u1; u++) {
+            if (issuer) {
+                for (int s2 = 0; s2 < OZ_CHUNK; s2++) issue(s2 == 0);
+                tc_commit(&cdone);
+            }
+            __syncwarp();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
         }
     }
+    if (!ok && err) atomicExch(err, 1);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, OZ_TCOLS);
+}
+
+// The tiles that several blocks shared: the parts in chunk order (block
+// order), then the two scales, into C.  One block per tile; a tile that one
+// block finished returns at once.
+__global__ void k_oz_fixup(const double *__restrict__ part, const int *__restrict__ Ea, const int *__restrict__ Eb,
+                           int k, long long Mb, int nrt, int nch, long long U, int G, double2 *__restrict__ C,
+                           long long ldC, long long col_off) {
+    const long long t = blockIdx.x;
+    const int i0 = oz_block_of(t * nch, U, G), i1 = oz_block_of(t * nch + nch - 1, U, G);
+    if (i0 == i1) return;
+    const int rt = (int)(t % nrt);
+    const long long ct = t / nrt;
+    for (int e = threadIdx.x; e < OZ_M * OZ_N; e += blockDim.x) {
+        const int row = e % OZ_M, col = e / OZ_M;
+        const long long R = (long long)rt * OZ_M + row, jc = ct * OZ_N + col;
+        if (R >= 2LL * k || jc >= Mb) continue;
+        double sum = 0.0;
+        for (int i = i0; i <= i1; i++) {
+            const long long slot = 2LL * i + (oz_u0(i, U, G) / nch == t ? 0 : 1);
+            sum += part[(slot * OZ_N + col) * OZ_M + row];
+        }
+        ((double *)(C + (R >> 1) * ldC) + (R & 1))[2 * (col_off + jc)] = ldexp(sum, Ea[R >> 1] + Eb[jc]);
+    }
 }
 
 // Self-test of the bounded mbarrier wait used by every tensor-core kernel: one
@@ -469,10 +565,7 @@ __global__ void k_wait_selftest(long long cycles, int arrive, int *flag) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
-        if (arrive) {
-            unsigned long long st;
-            asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(smem_u32(&bar)));
-        }
+        if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
         if (!mbar_wait(&bar, 0, (unsigned long long)cycles)) *flag = 1;
     }
 }
@@ -482,10 +575,14 @@ cudaError_t launch_wait_selftest(long long cycles, int arrive, int *flag, cudaSt
     return cudaGetLastError();
 }
 
+// K padded to whole exact chunks (zero basis planes past 2N).
+static long long oz_kp(long long N) { return (2 * N + OZ_DRAIN - 1) / OZ_DRAIN * OZ_DRAIN; }
+
 size_t oz_workspace(long long N, int k, long long Mb) {
-    long long Kp = (2 * N + OZ_KS - 1) / OZ_KS * OZ_KS;
-    long long Rp = (2LL * k + OZ_M - 1) / OZ_M * OZ_M;
-    return (size_t)OZ_S * Rp * Kp * 2 + (size_t)(k + Mb) * 4 + 4096;
+    const long long Kp = oz_kp(N);
+    const long long Rp = (2LL * k + OZ_M - 1) / OZ_M * OZ_M;
+    const size_t parts = (size_t)2 * OZ_MAX_BLOCKS * OZ_M * OZ_N * sizeof(double);
+    return (size_t)OZ_S * Rp * Kp * 2 + parts + (size_t)(k + Mb) * 4 + 4096;
 }
 
 // C[:, col_off : col_off + Mb] for one batch of Mb columns; ws from oz_workspace.
@@ -493,11 +590,12 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
                               long long ldX, double2 *C, long long ldC, long long col_off, void *ws, int *err,
                               unsigned long long wait, cudaStream_t s) {
     if (k <= 0 || Mb <= 0) return cudaSuccess;
-    const long long Kp = (2 * N + OZ_KS - 1) / OZ_KS * OZ_KS;
+    const long long Kp = oz_kp(N);
     const long long Rp = (2LL * k + OZ_M - 1) / OZ_M * OZ_M;
     const long long Cp = (Mb + OZ_N - 1) / OZ_N * OZ_N;
     __nv_bfloat16 *As = (__nv_bfloat16 *)ws;
-    int *Ea = (int *)(As + (size_t)OZ_S * Rp * Kp);
+    double *part = (double *)(As + (size_t)OZ_S * Rp * Kp);
+    int *Ea = (int *)(part + (size_t)2 * OZ_MAX_BLOCKS * OZ_M * OZ_N);
     int *Eb = Ea + k;
     // zero fill of the A planes (small: rows 2k..Rp-1 and the K padding)
     cudaError_t e = cudaMemsetAsync(As, 0, (size_t)OZ_S * Rp * Kp * 2, s);
@@ -506,13 +604,23 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
     const long long ge = (Mb * 32 + 255) / 256;
     k_oz_exp_B<<<(unsigned)(ge < 4096 ? ge : 4096), 256, 0, s>>>(X, N, Mb, ldX, Eb);
     const size_t dsm = (size_t)OZ_NBUF * (OZ_SA + OZ_SB) + OZ_ACC;  // 126 KB ring + 64 KB running sums
-    static bool attr = false;
-    if (!attr) {
+    static int sms = 0;
+    if (!sms) {
         cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-        attr = true;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
     }
-    dim3 grid((unsigned)(Cp / OZ_N), (unsigned)(Rp / OZ_M));
-    k_oz_gemm<<<grid, OZ_THREADS, dsm, s>>>(As, X, N, ldX, Ea, Eb, k, Mb, Kp, C, ldC, col_off, err, wait);
+    const int nrt = (int)(Rp / OZ_M);
+    const long long tiles = (long long)nrt * (Cp / OZ_N);
+    const int nch = (int)(Kp / OZ_DRAIN);
+    const long long U = tiles * nch;  // work units
+    long long G = sms < OZ_MAX_BLOCKS ? sms : OZ_MAX_BLOCKS;
+    if (G > U) G = U;
+    k_oz_gemm<<<(unsigned)G, OZ_THREADS, dsm, s>>>(As, X, N, ldX, Ea, Eb, k, Mb, Kp, nrt, U, part, C, ldC, col_off,
+                                                  err, wait);
+    k_oz_fixup<<<(unsigned)tiles, 256, 0, s>>>(part, Ea, Eb, k, Mb, nrt, nch, U, (int)G, C, ldC, col_off);
     return cudaGetLastError();
 }
 
