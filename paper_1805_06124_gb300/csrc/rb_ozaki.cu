@@ -320,7 +320,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     const int nch = nst / OZ_CHUNK;
     const int G = (int)gridDim.x;
     const long long u0 = oz_u0(blockIdx.x, U, G), u1 = oz_u0(blockIdx.x + 1, U, G);
-    const long long t_first = u0 / nch;
+    const int nu = (int)(u1 - u0);  // units of this block
+    // tile indices fit 32 bits: X (16 N bytes per column) and Q fit in device memory
+    const int t_first = (int)(u0 / nch);
     const uint32_t dsm0 = smem_u32(dsm);
     // producer: this thread's column of a tile and its complex element of a stage
     const int jj = (threadIdx.x >> 3) & (OZ_N - 1), p0 = threadIdx.x & 7;
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
             v[u] = st < nlim ? x[(long long)st * (OZ_KS / 2)] : make_double2(0.0, 0.0);
         }
     };
-    const long long gtot = (u1 - u0) * OZ_CHUNK;  // stages of this block
+    const long long gtot = (long long)nu * OZ_CHUNK;  // stages of this block
     // the block's stage g: buffer b, phase parity ph (of this use of the buffer)
     int b = 0;
     uint32_t ph = 0;
@@ -381,15 +383,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     };
     int seg_c0 = 0;  // first chunk of the current tile segment
     if (producer) {
-    for (long long u = u0; u < u1; u++) {
-        const long long t = u / nch;
-        const int c = (int)(u % nch);
-        const int rt = (int)(t % nrt);
-        const long long ct = t / nrt;
-        if (u == u0 || c == 0) {  // a new tile: this thread's column, its scale and first reads
+    for (int du = 0; du < nu; du++) {
+        const long long u = u0 + du;
+        const int t = (int)(u / nch);
+        const int c = (int)(u - (long long)t * nch);
+        const int rt = t % nrt;
+        const int ct = t / nrt;
+        if (du == 0 || c == 0) {  // a new tile: this thread's column, its scale and first reads
             seg_c0 = c;
             if (producer) {
-                const long long j = ct * OZ_N + jj;
+                const long long j = (long long)ct * OZ_N + jj;
                 const bool live = j < Mb;
                 E = live ? Eb[j] : 0;
                 x = X + (live ? j : 0) * ldX + p0;
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
             // drain: wait for the unit's MMAs (cdone completes once per unit and
             // no thread runs more than one unit behind), then read this
             // thread's TMEM lane; levels combined smallest first, in double-float
-            ok = mbar_wait(&cdone, (uint32_t)((u - u0) & 1), wait) && ok;
+            ok = mbar_wait(&cdone, (uint32_t)(du & 1), wait) && ok;
             tc_fence_after();
             const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
 #pragma unroll
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                     acc_ls[a] = al;
                 }
             }
-            if (u == u1 - 1 || c == nch - 1) {
+            if (du == nu - 1 || c == nch - 1) {
                 // the tile segment ends: the whole tile goes to C, a part to the
                 // block's slot; the sums restart for the next tile
                 const long long R = (long long)rt * OZ_M + row;
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                     const int a = (cbase + cc) * OZ_M + row;
                     const double val = (double)acc_hs[a] + (double)acc_ls[a];
                     acc_hs[a] = acc_ls[a] = 0.f;
-                    const long long jc = ct * OZ_N + cbase + cc;
+                    const long long jc = (long long)ct * OZ_N + cbase + cc;
                     if (whole) {
                         if (R < 2LL * k && jc < Mb)
                             ((double *)(C + (R >> 1) * ldC) + (R & 1))[2 * (col_off + jc)] =
@@ -516,7 +519,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         };
         if (issuer)
             for (long long gg = 0; gg < OZ_NBUF - 1 && gg < gtot; gg++) load_a((int)gg);
-        for (long long u = u0; u < u1; u++) {
+        for (int du = 0; du < nu; du++) {
             if (issuer) {
                 for (int s2 = 0; s2 < OZ_CHUNK; s2++) issue(s2 == 0);
                 tc_commit(&cdone);

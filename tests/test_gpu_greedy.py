@@ -184,6 +184,9 @@ def _tc_bound(Q, X):
 
 @pytest.mark.parametrize("path", ["tensor_cores", "fp64"])
 def test_project_parity(orc, rbm, path):
+    """37 x 517 basis onto 333 columns: on the tensor cores 6 tiles of 3
+    exact chunks, one chunk per block, so every tile is the sum of three
+    blocks' parts (the stream-K fix-up)."""
     c = rbm.RB(device=0, project_fp64=(path == "fp64"))
     rng = np.random.default_rng(0)
     Q = rng.standard_normal((37, 517)) + 1j * rng.standard_normal((37, 517))
@@ -221,7 +224,8 @@ def test_trace_per_iteration(orc, rbm):
 @pytest.mark.parametrize("k", [64, 65, 130])
 def test_project_tc_row_tiles(orc, rbm, k):
     """k = 64, 65, 130: one, two (the second almost empty) and three 128-row
-    tiles of the tensor-core projection; odd N (K padding), ragged columns."""
+    tiles of the tensor-core projection; odd N (K padding to whole chunks),
+    ragged columns; every tile shared by four blocks."""
     c = rbm.RB(device=0)
     rng = np.random.default_rng(k)
     Q = rng.standard_normal((k, 777)) + 1j * rng.standard_normal((k, 777))
@@ -233,9 +237,11 @@ def test_project_tc_row_tiles(orc, rbm, k):
 
 
 def test_project_tc_column_batches(orc, rbm):
-    """N = 8192 and 20,000 columns: 313 column tiles, more than two waves of
-    the GPU's SMs, each slicing its columns inside the GEMM; checked against
-    the oracle on columns at both ends, in the middle and in the last wave."""
+    """N = 8192 and 20,000 columns: 313 column tiles of 32 chunks over the
+    persistent blocks (about 66 chunks each, so most blocks start or end
+    inside a tile and the fix-up adds the parts), each slicing its columns
+    inside the GEMM; checked against the oracle on columns at both ends, in
+    the middle and near the end."""
     c = rbm.RB(device=0)
     N, M = 8192, 20000
     rng = np.random.default_rng(11)
