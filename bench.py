@@ -372,25 +372,37 @@ def run_surrogate(args):
 
 
 def run_split_once(args):
-    """One rb_greedy_split call (after one warm-up call) on chirps N x M, seed 2,
-    tol 1e-10 -- the command the split form's profiles are taken with."""
-    import torch
+    """rb_greedy_split on chirps N x M, seed 2 (tol --tol, default 1e-10;
+    kmax --kmax, default 800; --switch-err, --no-switch): --warmup calls (at
+    most one), then --steps timed calls (CUDA events in the library), median
+    reported -- the command the split form's profiles are taken with."""
+    import numpy as np
     from paper_1805_06124_gb300 import rb, synth
-    c = rb.RB(device=0)
+    tol = 1e-10 if args.tol is None else args.tol
+    kmax = 800 if args.kmax is None else args.kmax
+    c = rb.RB(device=0, switch_err=args.switch_err, split_switch=not args.no_switch)
     q, m = synth.chirp_params(args.M, 2)
     S = c.generate(q, m, args.N)
     hi, lo = c.split(S)
     del S
-    r = c.greedy_split(hi, lo, 1e-10, 800)
-    if args.steps > 0:
-        r = c.greedy_split(hi, lo, 1e-10, 800)
-    print(json.dumps({"workload": f"split form, chirps N={args.N} x M={args.M} seed 2, tol 1e-10", "k": r["k"],
-                      "switch_iter": r["switch_iter"], "ms": round(r["ms_total"], 3)}), flush=True)
+    r = None
+    if args.warmup > 0 or args.steps <= 0:
+        r = c.greedy_split(hi, lo, tol, kmax)
+    ts = []
+    for _ in range(args.steps):
+        r = c.greedy_split(hi, lo, tol, kmax)
+        ts.append(r["ms_total"])
+    ms = float(np.median(ts)) if ts else r["ms_total"]
+    print(json.dumps({"workload": f"split form, chirps N={args.N} x M={args.M} seed 2, tol {tol}, kmax {kmax}, "
+                                  f"switch_err {args.switch_err}, switch {'off' if args.no_switch else 'on'}",
+                      "k": r["k"], "status": r["status"], "switch_iter": r["switch_iter"],
+                      "ms": round(ms, 3), "calls_timed": len(ts)}), flush=True)
 
 
 def run_project_once(args):
     """rb_project of a random k-vector basis onto M chirps of length N (tensor
-    cores unless --project-fp64); prints the time of the second call."""
+    cores unless --project-fp64): one warm-up call, then 10 calls timed with
+    CUDA events on the stream the library uses."""
     import torch
     from paper_1805_06124_gb300 import rb, synth
     c = rb.RB(device=0, project_fp64=args.project_fp64)
@@ -399,13 +411,17 @@ def run_project_once(args):
     X = c.generate(*synth.chirp_params(args.M, 5), args.N)
     C = c.project(Q, X)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    C = c.project(Q, X)
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        C = c.project(Q, X)
+    e1.record()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1) / reps
     print(json.dumps({"workload": f"rb_project k={args.k} N={args.N} M={args.M}",
-                      "path": "fp64" if args.project_fp64 else "tensor_cores", "ms": round(dt * 1e3, 3),
-                      "useful_TFLOPs": round(8.0 * args.k * args.N * args.M / dt / 1e12, 3)}), flush=True)
+                      "path": "fp64" if args.project_fp64 else "tensor_cores", "ms": round(ms, 3), "calls": reps,
+                      "useful_TFLOPs": round(8.0 * args.k * args.N * args.M / ms / 1e9, 3)}), flush=True)
 
 
 def run_recon_once(args):
@@ -964,6 +980,10 @@ def main():
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--mlp-mode", default="fourier-split", choices=["plain", "split", "fourier", "fourier-split"])
     ap.add_argument("--k", type=int, default=53)
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--kmax", type=int, default=None)
+    ap.add_argument("--switch-err", type=float, default=0.0)
+    ap.add_argument("--no-switch", action="store_true")
     ap.add_argument("--project-fp64", action="store_true")
     args = ap.parse_args()
     if args.workload == "surrogate":
