@@ -69,11 +69,14 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
 }
 
+// One try: the thread may be suspended until the phase completes or about
+// 2 us (the suspend-time hint, in ns) have passed, so a waiting warp issues
+// few instructions.
 __device__ __forceinline__ uint32_t mbar_try(uint64_t *bar, uint32_t parity) {
     uint32_t done;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done)
-                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "r"(smem_u32(bar)), "r"(parity), "r"(2000u)
                  : "memory");
     return done;
 }
