@@ -905,8 +905,16 @@ __global__ void __launch_bounds__(LP_THREADS, 1) k_lo_project_tc(Prob p, int nt,
     const long long nstg = (2 * p.N + LKC - 1) / LKC;
     bool ok = true;
     long long gs = 0;  // stages run by this block so far (all tiles)
-    auto buf = [&](long long g) { return dsm + (int)(g % LP_NBUF) * LSTAGE; };
-    auto par = [&](long long g) { return (uint32_t)((g / LP_NBUF) & 1); };
+    // buffer and phase parity of the block's next stage, carried along by
+    // every role (each runs every stage once), so no stage count is divided
+    int cb = 0;
+    uint32_t cph = 0;
+    auto advance = [&]() {
+        if (++cb == LP_NBUF) {
+            cb = 0;
+            cph ^= 1u;
+        }
+    };
     LpRegs R[LP_SETS];  // (warp 16 does not use them)
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int rt = (int)(tile % nrt);
@@ -924,22 +932,23 @@ __global__ void __launch_bounds__(LP_THREADS, 1) k_lo_project_tc(Prob p, int nt,
             auto produce = [&](long long s, const LpRegs &Rc, LpRegs &Rn) {
                 if (s + LP_AHEAD < nstg) lp_load(p, T, s + LP_AHEAD, nfull, Rn);
                 lp_prefetch(p, T, s + LP_PF, nfull);
-                const long long g = g0 + s;
-                uint64_t *fb = &bfull[g % LP_NBUF];
-                if (g >= LP_NBUF) {
-                    // one lane polls; __syncwarp orders the warp's stores after it
+                uint64_t *fb = &bfull[cb];
+                if (g0 + s >= LP_NBUF) {
+                    // one lane polls (the MMAs of the buffer's previous stage);
+                    // __syncwarp orders the warp's stores after it
                     bool wok = true;
-                    if (lane == 0) wok = mbar_wait(&done[g % LP_NBUF], par(g - LP_NBUF), p.wait_cycles);
+                    if (lane == 0) wok = mbar_wait(&done[cb], cph ^ 1u, p.wait_cycles);
                     wok = __shfl_sync(0xffffffffu, wok ? 1 : 0, 0) != 0;
                     __syncwarp();
                     ok = ok && wok;
                 }
-                lp_store(nt, T, Rc, buf(g) + LA_STAGE);
+                lp_store(nt, T, Rc, dsm + cb * LSTAGE + LA_STAGE);
                 // each thread makes its own stores visible to the tensor core
                 // (async proxy); after the warp's, lane 0 arrives for it
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(fb)) : "memory");
+                advance();
             };
             for (long long s = 0; s < nstg; s += LP_SETS) {
 #pragma unroll
@@ -950,21 +959,20 @@ __global__ void __launch_bounds__(LP_THREADS, 1) k_lo_project_tc(Prob p, int nt,
             // lane 0 of warp 17: the A pieces of every stage, into a buffer
             // whose MMAs are done, announced on its bfull
             for (long long s = 0; s < nstg; s++) {
-                const long long g = g0 + s;
-                uint64_t *fb = &bfull[g % LP_NBUF];
-                if (g >= LP_NBUF) ok = mbar_wait(&done[g % LP_NBUF], par(g - LP_NBUF), p.wait_cycles) && ok;
+                uint64_t *fb = &bfull[cb];
+                if (g0 + s >= LP_NBUF) ok = mbar_wait(&done[cb], cph ^ 1u, p.wait_cycles) && ok;
                 // arrive and announce the bytes in one step, before the copy:
                 // the phase cannot complete without them
                 mbar_expect_tx(fb, LA_STAGE);
-                bulk_g2s(buf(g), ga + s * LA_STAGE, LA_STAGE, fb);
+                bulk_g2s(dsm + cb * LSTAGE, ga + s * LA_STAGE, LA_STAGE, fb);
+                advance();
             }
         } else if (issuer) {
             for (long long s = 0; s < nstg; s++) {
-                const long long g = g0 + s;
-                const int b = (int)(g % LP_NBUF);
-                ok = mbar_wait(&bfull[b], par(g), p.wait_cycles) && ok;
+                const int b = cb;
+                ok = mbar_wait(&bfull[b], cph, p.wait_cycles) && ok;
                 tc_fence_after();
-                const uint32_t sa = smem_u32(buf(g)), sb = sa + LA_STAGE;
+                const uint32_t sa = smem_u32(dsm + b * LSTAGE), sb = sa + LA_STAGE;
 #pragma unroll
                 for (int kk = 0; kk < LKC / 16; kk++) {
                     // K step kk: two core matrices along K
@@ -977,14 +985,19 @@ __global__ void __launch_bounds__(LP_THREADS, 1) k_lo_project_tc(Prob p, int nt,
                     tc_mma_bf16(tmem, al, bh, idesc, 1u);
                 }
                 tc_commit(&done[b]);
+                advance();
             }
+        } else {
+            // the other lanes of warps 16 and 17 keep the stage count with their lane 0
+            for (long long s = 0; s < nstg; s++) advance();
         }
         // the other lanes of the MMA and A-copy warps wait here, converged,
         // while their lane 0 works
         if (warp >= LP_PWARPS) __syncwarp();
         gs = g0 + nstg;
-        // every thread: the tile's last MMAs (the latest phase of that barrier)
-        ok = mbar_wait(&done[(gs - 1) % LP_NBUF], par(gs - 1), p.wait_cycles) && ok;
+        // every thread: the tile's last MMAs (the latest phase of that barrier:
+        // the stage before the next one)
+        ok = mbar_wait(&done[cb == 0 ? LP_NBUF - 1 : cb - 1], cb == 0 ? cph ^ 1u : cph, p.wait_cycles) && ok;
         if (!ok) s_bad = 1;
         __syncthreads();
         tc_fence_after();
