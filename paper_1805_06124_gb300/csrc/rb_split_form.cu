@@ -772,6 +772,14 @@ __device__ __forceinline__ void lp_tile(const Prob &p, long long j0, int nt, LpT
 __device__ __forceinline__ void lp_load(const Prob &p, const LpTile &T, long long stg, long long nfull, LpRegs &R) {
     const int lane = threadIdx.x & 31;
     const long long gstride = 64 * (p.ldH >> 1);  // float4 between a lane's groups
+    if (stg < nfull && T.valid == (1u << LP_GROUPS) - 1u) {
+        // the common case: a whole stage of full column groups, no tests
+#pragma unroll
+        for (int x = 0; x < LP_GROUPS; x++)
+#pragma unroll
+            for (int i = 0; i < LP_CH; i++) R.v[x][i] = ld_stream(T.base + x * gstride + stg * (LKC / 4) + 8 * i);
+        return;
+    }
 #pragma unroll
     for (int x = 0; x < LP_GROUPS; x++) {
 #pragma unroll
@@ -803,14 +811,18 @@ __device__ __forceinline__ void lp_load(const Prob &p, const LpTile &T, long lon
 constexpr int LP_PF = 4;  // stages of lo prefetched into L2 ahead
 __device__ __forceinline__ void lp_prefetch(const Prob &p, const LpTile &T, long long stg, long long nfull) {
     const int lane = threadIdx.x & 31;
-    if ((lane & 7) != 0 || stg >= nfull) return;
+    if (stg >= nfull) return;  // warp-uniform
     const long long gstride = 64 * (p.ldH >> 1);
+    // one lane in eight issues it, by predicate rather than a branch (no divergence)
+    const uint32_t lead = (lane & 7) == 0 ? 1u : 0u;
 #pragma unroll
     for (int x = 0; x < LP_GROUPS; x++) {
-        if (!(T.valid & (1u << x))) continue;
+        const uint32_t on = lead & (T.valid >> x);
 #pragma unroll
         for (int i = 0; i < LP_CH; i++)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(T.base + x * gstride + stg * (LKC / 4) + 8 * i));
+            asm volatile("{\n.reg .pred q;\nsetp.ne.u32 q, %1, 0;\n@q prefetch.global.L2 [%0];\n}\n" ::"l"(
+                             T.base + x * gstride + stg * (LKC / 4) + 8 * i),
+                         "r"(on & 1u));
     }
 }
 
