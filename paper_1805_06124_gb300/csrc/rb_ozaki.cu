@@ -240,13 +240,16 @@ __device__ __forceinline__ void slice7_words(double re, double im, int E, uint32
 // slice planes of each stage straight into the stage's shared-memory buffer:
 // thread t owns column 64 ct + t / 8 and complex element t % 8 of every
 // stage, and reads X in groups of OZ_FG stages (512 contiguous bytes per
-// column per group), two groups ahead of the slicing.  Lane 0 of warp 16
+// column per group), two groups ahead of the slicing.  Lane 0 of warp 17
 // fills the A half of each buffer with one bulk copy of the pre-sliced basis
-// (28 KB, L2-resident) and issues the stage's MMAs: slice sa of A against the
+// (28 KB, L2-resident) as soon as the buffer's previous MMAs are done.  Lane
+// 0 of warp 16 issues the stage's MMAs: slice sa of A against the
 // consecutive B planes sb .. sb+g-1 as one operand of 64 g rows (the planes
 // are 64 rows apart in the K-major layout), whose product lands on the TMEM
 // levels sa+sb .. sa+sb+g-1 (the levels are 64 columns apart) -- 10 MMAs of
-// N = 64 .. 256 per stage.  Barriers per buffer: "afull" counts the A bytes,
+// N = 64 .. 256 per stage.  The producers and warp 16 meet at a named barrier
+// after each unit (the levels drained before the next unit overwrites them);
+// warp 17 stays out of it and copies ahead across units.  Barriers per buffer: "afull" counts the A bytes,
 // "bfull" one arrival per producer warp, "done" receives the MMA commit; the
 // n-th phase of buffer b belongs to the block's stage b + OZ_NBUF n (buffer
 // and phase parity are carried along with the stage count).  At the end of
@@ -257,7 +260,7 @@ __device__ __forceinline__ void slice7_words(double re, double im, int E, uint32
 constexpr int OZ_NBUF = 3;
 constexpr int OZ_PWARPS = 16;
 constexpr int OZ_PRODUCERS = 32 * OZ_PWARPS;
-constexpr int OZ_THREADS = OZ_PRODUCERS + 32;      // 17 warps
+constexpr int OZ_THREADS = OZ_PRODUCERS + 64;      // 18 warps: + the MMA warp and the copy warp
 constexpr int OZ_FG = 4;                           // stages per X read group
 constexpr int OZ_CHUNK = OZ_DRAIN / OZ_KS;         // stages per work unit (32)
 constexpr int OZ_DC = OZ_N / (OZ_PWARPS / 4);      // columns drained per thread (16)
@@ -295,7 +298,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = warp < OZ_PWARPS;
-    const bool issuer = threadIdx.x == OZ_PRODUCERS;
+    const bool issuer = threadIdx.x == OZ_PRODUCERS;       // lane 0 of warp 16
+    const bool copier = threadIdx.x == OZ_PRODUCERS + 32;  // lane 0 of warp 17
     const int row = 32 * (warp & 3) + lane, cbase = OZ_DC * ((warp >> 2) & 3);
     float *acc_hs = (float *)(dsm + OZ_NBUF * (OZ_SA + OZ_SB));  // [column][row]
     float *acc_ls = acc_hs + OZ_M * OZ_N;
@@ -345,6 +349,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     int b = 0;
     uint32_t ph = 0;
     long long g = 0;
+    // the barrier of the producers and the MMA warp at the end of a unit: the
+    // levels are drained before the next unit's first MMAs overwrite them
+    auto unit_sync = [&]() {
+        tc_fence_before();
+        asm volatile("bar.sync 1, %0;" ::"r"(OZ_PRODUCERS + 32) : "memory");
+        tc_fence_after();
+    };
     auto advance = [&]() {
         g++;
         if (++b == OZ_NBUF) {
@@ -456,32 +467,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                 }
             }
         }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
+        unit_sync();
     }
-    } else {
-        // warp 16 (lane 0 issues; the block barrier once per unit, as the producers)
-        // The basis copies go out in the block's stage order (units u0 .. in
-        // order, OZ_CHUNK stages each), so their source advances one stage at
-        // a time and is recomputed once per unit
-        constexpr long long a_stage = (long long)OZ_S * OZ_M * OZ_KS;  // elements per stage
-        auto unit_a = [&](long long u) {
-            const long long t = u / nch;
-            return As + ((t % nrt) * nst + (u % nch) * OZ_CHUNK) * a_stage;
-        };
-        long long a_u = u0;
-        int a_s = 0;
-        const __nv_bfloat16 *a_base = unit_a(u0);
-        auto load_a = [&](int bb) {  // the next stage's A into buffer bb
-            uint64_t *fb = &afull[bb];
-            mbar_expect_tx(fb, OZ_SA);
-            bulk_g2s(dsm + bb * (OZ_SA + OZ_SB), a_base + a_s * a_stage, OZ_SA, fb);
-            if (++a_s == OZ_CHUNK) {
-                a_s = 0;
-                if (++a_u < u1) a_base = unit_a(a_u);
-            }
-        };
+    } else if (warp == OZ_PWARPS) {
+        // warp 16: lane 0 issues; the unit barrier with the producers
         auto issue = [&](bool first_of_unit) {
             ok = mbar_wait(&afull[b], ph, wait) && ok;
             ok = mbar_wait(&bfull[b], ph, wait) && ok;
@@ -508,27 +497,48 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                     }
                 }
             tc_commit(&done[b]);
-            // A of stage g + OZ_NBUF - 1 into the buffer of stage g - 1, once the
-            // MMAs of stage g - 1 are complete
-            if (g + OZ_NBUF - 1 < gtot) {
-                const int bp = b == 0 ? OZ_NBUF - 1 : b - 1;
-                if (g >= 1) ok = mbar_wait(&done[bp], b == 0 ? ph ^ 1u : ph, wait) && ok;
-                load_a(bp);  // stage g + OZ_NBUF - 1
-            }
             advance();
         };
-        if (issuer)
-            for (long long gg = 0; gg < OZ_NBUF - 1 && gg < gtot; gg++) load_a((int)gg);
         for (int du = 0; du < nu; du++) {
             if (issuer) {
                 for (int s2 = 0; s2 < OZ_CHUNK; s2++) issue(s2 == 0);
                 tc_commit(&cdone);
             }
             __syncwarp();
-            tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
+            unit_sync();
         }
+    } else {
+        // warp 17: lane 0 copies the basis planes of every stage into its
+        // buffer once the buffer's previous MMAs are done, across unit
+        // boundaries (it keeps out of the unit barrier)
+        // The basis copies go out in the block's stage order (units u0 .. in
+        // order, OZ_CHUNK stages each), so their source advances one stage at
+        // a time and is recomputed once per unit
+        constexpr long long a_stage = (long long)OZ_S * OZ_M * OZ_KS;  // elements per stage
+        auto unit_a = [&](long long u) {
+            const long long t = u / nch;
+            return As + ((t % nrt) * nst + (u % nch) * OZ_CHUNK) * a_stage;
+        };
+        long long a_u = u0;
+        int a_s = 0;
+        const __nv_bfloat16 *a_base = unit_a(u0);
+        auto load_a = [&](int bb) {  // the next stage's A into buffer bb
+            uint64_t *fb = &afull[bb];
+            mbar_expect_tx(fb, OZ_SA);
+            bulk_g2s(dsm + bb * (OZ_SA + OZ_SB), a_base + a_s * a_stage, OZ_SA, fb);
+            if (++a_s == OZ_CHUNK) {
+                a_s = 0;
+                if (++a_u < u1) a_base = unit_a(a_u);
+            }
+        };
+        if (copier) {
+            for (long long gg = 0; gg < gtot; gg++) {
+                if (gg >= OZ_NBUF) ok = mbar_wait(&done[b], ph ^ 1u, wait) && ok;  // the MMAs of stage gg - OZ_NBUF
+                load_a(b);
+                advance();
+            }
+        }
+        __syncwarp();
     }
     if (!ok && err) atomicExch(err, 1);
     tc_fence_before();
