@@ -431,12 +431,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                 tmem_ld4_levels(tmem + lane_off + (uint32_t)(cbase + 4 * h), v);
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
+                    // levels added smallest first by TwoSum, the errors gathered
+                    // in tl (normalised once, by the add into the running sums)
                     float th = 0.f, tl = 0.f;
 #pragma unroll
                     for (int L = OZ_LV - 1; L >= 0; L--) {
                         // level L+2 carries 2^(-7 (L+2)): an exact power-of-two factor
-                        float xl = v[L][e] * __int_as_float((127 - OZ_BITS * (L + 2)) << 23);
-                        dfs_add(th, tl, xl, 0.f);
+                        const float xl = v[L][e] * __int_as_float((127 - OZ_BITS * (L + 2)) << 23);
+                        float sh, se;
+                        two_sum(th, xl, sh, se);
+                        th = sh;
+                        tl = __fadd_rn(tl, se);
                     }
                     const int a = (cbase + 4 * h + e) * OZ_M + row;
                     float ah = acc_hs[a], al = acc_ls[a];
