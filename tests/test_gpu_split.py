@@ -241,3 +241,24 @@ def test_split_switch_on_candidate_count_large_m(orc, rbm):
         info.update(switch_iter=int(g["switch_iter"]), ms=round(float(g["ms_total"]), 3))
         res[sw] = info
     print("switch", res[True], "no switch", res[False])
+
+
+def test_split_switch_then_exact_rank_and_kmax(orc, rbm):
+    """A switch at the first iterations (switch_err = 1: every error is below
+    the largest norm), then the loop ends in the hi + lo phase: on exact rank
+    (IMGS finds the pivot in the span) and on kmax."""
+    S = synth.low_rank(400, 300, 7, seed=6)
+    scale = float(np.max(np.sum(np.abs(S) ** 2, axis=1)))
+    c = rbm.RB(device=0, switch_err=1.0)
+    H, L = split_upload(orc, S)
+    g = npy(c.greedy_split(H, L, 1e-11 * scale, 50))
+    assert g["k"] == 7 and g["status"] == 0 and 0 < g["switch_iter"] <= 2, (g["k"], g["status"], g["switch_iter"])
+    rep = parity.replay_and_check(orc, S, g, 1e-11 * scale, 50)
+    parity.compare(g, rep, S, err_atol=1e-12 * scale, c_rel=c_rel(S.shape[1]))
+    S2 = synth.chirps(512, 700, seed=2)
+    H2, L2 = split_upload(orc, S2)
+    g2 = npy(c.greedy_split(H2, L2, 1e-12, 10))
+    assert g2["k"] == 10 and g2["status"] == rbm.KMAX_REACHED and 0 < g2["switch_iter"] < 10, g2["switch_iter"]
+    rep2 = parity.replay_and_check(orc, S2, g2, 1e-12, 10)
+    parity.compare(g2, rep2, S2, c_rel=c_rel(S2.shape[1]))
+    c.close()
