@@ -372,11 +372,15 @@ void rb_shard_destroy(rb_shard *sh);
  * none).  Returns RB_ENONFINITE for NaN/Inf in S. */
 rb_status rb_shard_init(rb_shard *sh, double *best_err, long long *best_idx);
 /* The owner's side of the send: column j (global index, owned by this rank)
- * copied to dst (device, N complex128, 16-byte aligned) and its stored norm
- * ||s_j||^2 to *norm2 (host).  Synchronises the stream. */
+ * copied to dst (device, 16-byte aligned) and its stored norm ||s_j||^2 to
+ * *norm2 (host; synchronises the stream), or, when norm2 is NULL, into the
+ * real part of dst[N] on the device (dst then holds N + 1 complex128 entries;
+ * asynchronous on the stream). */
 rb_status rb_shard_column(rb_shard *sh, long long j, void *dst, double *norm2);
 /* Every rank: IMGS of the received pivot column v (device, N complex128) with
- * norm2 from its owner against the current basis (MGSCI, Sec. 6.1.2), the new
+ * norm2 from its owner (a negative norm2: taken from the real part of v[N]
+ * on the device, v then holding N + 1 entries) against the current basis
+ * (MGSCI, Sec. 6.1.2), the new
  * basis vector appended (pivots[k] = j), then the sweep of this rank's
  * columns; returns the next local candidate.  *appended = 0 when v lay in the
  * span of the basis (exact rank: the caller stops).  Errors: RB_EORTHO,

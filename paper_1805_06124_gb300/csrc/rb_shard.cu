@@ -47,13 +47,15 @@ __global__ void __launch_bounds__(kThreads) k_shard_begin(Prob p, const double2 
          i += (long long)gridDim.x * blockDim.x)
         p.v[i] = vin[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // a negative norm from the host: the owner's norm travels in vin[N].x
+        const double n2 = vnorm2 >= 0.0 ? vnorm2 : vin[p.N].x;
         st->stop = 0;
         st->force_stop = 0;
         st->status = RB_OK;
         st->passes = 0;
         st->accepted = (st->k == 0);
-        st->before2 = vnorm2;
-        st->after2 = vnorm2;
+        st->before2 = n2;
+        st->after2 = n2;
     }
 }
 
@@ -252,7 +254,7 @@ rb_status rb_shard_init(rb_shard *sh, double *best_err, long long *best_idx) {
 }
 
 rb_status rb_shard_column(rb_shard *sh, long long j, void *dst, double *norm2) {
-    if (!sh || !dst || !norm2) return RB_EINVAL;
+    if (!sh || !dst) return RB_EINVAL;
     const long long jl = j - sh->col0;
     if (jl < 0 || jl >= sh->p.M) return shard_fail(sh, RB_EINVAL, "rb_shard_column: column not owned by this shard");
     cudaStream_t sm = rbk::ctx_stream(sh->ctx);
@@ -260,15 +262,22 @@ rb_status rb_shard_column(rb_shard *sh, long long j, void *dst, double *norm2) {
     SH_CK(cudaMemcpyAsync(dst, sh->p.S + jl * sh->p.ldS, (size_t)sh->p.N * sizeof(double2), cudaMemcpyDeviceToDevice,
                           sm),
           "column copy");
-    SH_CK(cudaMemcpyAsync(norm2, sh->p.norm2 + jl, sizeof(double), cudaMemcpyDeviceToHost, sm), "norm copy");
-    SH_CK(cudaStreamSynchronize(sm), "stream sync");
+    if (norm2) {
+        SH_CK(cudaMemcpyAsync(norm2, sh->p.norm2 + jl, sizeof(double), cudaMemcpyDeviceToHost, sm), "norm copy");
+        SH_CK(cudaStreamSynchronize(sm), "stream sync");
+    } else {
+        // the norm into dst[N] (real part, imaginary part zero), on the device
+        double2 *d = (double2 *)dst + sh->p.N;
+        SH_CK(cudaMemcpyAsync(d, sh->p.norm2 + jl, sizeof(double), cudaMemcpyDeviceToDevice, sm), "norm copy");
+        SH_CK(cudaMemsetAsync((double *)d + 1, 0, sizeof(double), sm), "norm copy");
+    }
     return RB_OK;
 }
 
 rb_status rb_shard_append(rb_shard *sh, const void *v, double vnorm2, long long j, double *best_err,
                           long long *best_idx, int *appended) {
-    if (!sh || !v || !(vnorm2 >= 0.0) || j < 0) return sh ? shard_fail(sh, RB_EINVAL, "rb_shard_append: bad arguments")
-                                                          : RB_EINVAL;
+    if (!sh || !v || std::isnan(vnorm2) || j < 0)
+        return sh ? shard_fail(sh, RB_EINVAL, "rb_shard_append: bad arguments") : RB_EINVAL;
     if (appended) *appended = 0;
     if (sh->status < 0) return shard_fail(sh, (rb_status)sh->status, "rb_shard_append: the shard has failed");
     if (sh->rank_end) return shard_fail(sh, RB_ESTATE, "rb_shard_append: the basis is already complete");

@@ -575,18 +575,16 @@ class Shard:
         return e.value, j.value
 
     def column(self, j: int, buf):
-        """Column j (owned here) into buf[:N], its norm into buf[N]."""
-        n2 = c_double()
-        self.ctx._check(self.lib.rb_shard_column(self._h, int(j), buf.data_ptr(), ctypes.byref(n2)))
-        buf[self.N] = complex(n2.value, 0.0)
-        return n2.value
+        """Column j (owned here) into buf[:N], its norm into buf[N], on the
+        device (asynchronous on the context's stream)."""
+        self.ctx._check(self.lib.rb_shard_column(self._h, int(j), buf.data_ptr(), None))
 
     def append(self, buf, j: int):
-        """IMGS of the received pivot column (buf from the owner) and the sweep
-        of this rank's columns; returns (best_err, best_idx, appended)."""
-        n2 = float(buf[self.N].real.item())
+        """IMGS of the received pivot column (buf from the owner, its norm in
+        buf[N], read on the device) and the sweep of this rank's columns;
+        returns (best_err, best_idx, appended)."""
         e, jj, app = c_double(), c_ll(), c_int()
-        self.ctx._check(self.lib.rb_shard_append(self._h, buf.data_ptr(), n2, int(j), ctypes.byref(e),
+        self.ctx._check(self.lib.rb_shard_append(self._h, buf.data_ptr(), -1.0, int(j), ctypes.byref(e),
                                                  ctypes.byref(jj), ctypes.byref(app)))
         return e.value, jj.value, bool(app.value)
 

@@ -65,9 +65,10 @@ class TorchComm:
     def allgather(self, triple):
         import torch
         t = torch.tensor(list(triple), dtype=torch.float64, device=self.device)
-        out = [torch.empty_like(t) for _ in range(self.size)]
-        self.dist.all_gather(out, t, group=self.group)
-        return [tuple(x.tolist()) for x in out]
+        out = torch.empty(3 * self.size, dtype=torch.float64, device=self.device)
+        self.dist.all_gather_into_tensor(out, t, group=self.group)
+        v = out.tolist()  # one read of all ranks' triples
+        return [tuple(v[3 * r:3 * r + 3]) for r in range(self.size)]
 
     def gather_ranges(self, ranges):
         out = [None] * self.size
