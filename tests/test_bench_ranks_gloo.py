@@ -1,5 +1,5 @@
-"""bench.py's multi-rank accounting (replicas: max time, summed work) with two
-gloo ranks on the CPU."""
+"""bench.py's multi-rank accounting (the slowest rank's time, the work summed
+over ranks: the column-sharded run's value) with two gloo ranks on the CPU."""
 import os
 import sys
 
