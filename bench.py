@@ -733,6 +733,7 @@ def run_sharded(args):
 
 
 def run_ours(args):
+    """The one-GPU run (main sends launches of several ranks to run_sharded)."""
     import torch
     from paper_1805_06124_gb300 import rb, synth
 
@@ -940,7 +941,7 @@ def run_ours(args):
                            "sweep": args.sweep, "k": k, "time_to_basis_ms": round(ms_max / args.steps, 3),
                            "pct_of_hbm_peak": round(100 * value / peak, 1),
                            "l2": "inputs larger than L2 (S is 34 GB; no flush needed)",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": "single GPU"},
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                              "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                              "kernel": "k_sweep (fused dot + bookkeeping + argmax)",
