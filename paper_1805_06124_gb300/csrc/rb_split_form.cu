@@ -1,9 +1,9 @@
 // rb_split_form.cu -- the split-precision form of the greedy sweep.
 //
 // S is stored as complex64 hi + lo (hi = fl32(s), lo = fl32(s - hi)).  Every
-// sweep reads hi only (8 bytes per element); lo is read for the candidate
-// columns of the exact re-check and once, at the end, by the projection of
-// the basis onto lo.
+// sweep of the hi-only phase reads hi only (8 bytes per element); lo is read
+// for the candidate columns of the exact re-check and once by the projection
+// of the basis onto lo (at the switch or at the end).
 //
 // Hi-only sweep.  c~ = q^H hi_j is accumulated against a fixed offset: each of
 // the 64 lane chains of a column (lane, element parity) keeps S = 1.5 sigma +
@@ -31,9 +31,16 @@
 // over the candidates is the pivot.  A column that stays a candidate only
 // adds the newest row.
 //
+// Switch.  When more columns are candidates than the switch count (the
+// bounds no longer separate them), or every error is certified below
+// switch_err * max ||s_j||^2, the basis so far is projected onto lo on the
+// tensor cores (C += Q^H lo), acc is rebuilt from the now exact C, and every
+// later sweep is the FP64 form's double-float sweep over hi + lo (k_sweep in
+// rb_sweep.cu, gated on the phase).
+//
 // End.  When every upper bound is below tol (or the exact pivot error is, or
-// kmax is reached), the basis is projected onto lo on the tensor cores, C +=
-// Q^H lo, and the final errors and argmax are taken from C.
+// kmax is reached) in the hi-only phase, the basis is projected onto lo the
+// same way and the final errors and argmax are taken from C.
 #include "rb_internal.cuh"
 #include "rb_tc.cuh"
 
