@@ -236,6 +236,21 @@ def test_project_tc_row_tiles(orc, rbm, k):
     c.close()
 
 
+@pytest.mark.parametrize("k,N,M", [(1, 1, 1), (2, 3, 5), (1, 700, 1), (64, 2000, 64), (5, 4096, 130)])
+def test_project_tc_small_shapes(orc, rbm, k, N, M):
+    """Edge shapes of the stream-K projection: one sample (K padded to one
+    exact chunk), one column, k = 1 (two rows), one tile of several chunks
+    shared by as many blocks, a tile count equal to the chunk count."""
+    c = rbm.RB(device=0)
+    rng = np.random.default_rng(k * 1000 + N + M)
+    Q = rng.standard_normal((k, N)) + 1j * rng.standard_normal((k, N))
+    X = rng.standard_normal((M, N)) + 1j * rng.standard_normal((M, N))
+    Cg = c.project(upload(Q), upload(X)).cpu().numpy()
+    Cr = orc.project(Q, X)
+    assert np.max(np.abs(Cg - Cr)) < _tc_bound(Q, X), (np.max(np.abs(Cg - Cr)), _tc_bound(Q, X))
+    c.close()
+
+
 def test_project_tc_column_batches(orc, rbm):
     """N = 8192 and 20,000 columns: 313 column tiles of 32 chunks over the
     persistent blocks (about 66 chunks each, so most blocks start or end
