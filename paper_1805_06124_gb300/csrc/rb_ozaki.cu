@@ -27,7 +27,7 @@ constexpr int OZ_BITS = 7;       // bits per slice
 constexpr int OZ_LV = OZ_S;      // levels 2..8 -> 7 accumulators
 constexpr int OZ_M = 128;        // A rows per tile
 constexpr int OZ_N = 64;         // B rows (columns of C) per tile
-constexpr int OZ_KS = 16;        // K per shared-memory stage (a ring of OZ_NBUF stage buffers)
+constexpr int OZ_KS = 16;        // K per shared-memory stage
 constexpr int OZ_DRAIN = 512;    // K per exact TMEM chunk
 constexpr int OZ_TCOLS = 512;    // TMEM columns allocated (7 levels x 64 used)
 
@@ -238,9 +238,10 @@ __device__ __forceinline__ void slice7_words(double re, double im, int E, uint32
 //
 // Roles.  Warps 0-15 (512 producer threads) read X and write the seven B
 // slice planes of each stage straight into the stage's shared-memory buffer:
-// thread t owns column 64 ct + t / 8 and complex element t % 8 of every
-// stage, and reads X in groups of OZ_FG stages (512 contiguous bytes per
-// column per group), two groups ahead of the slicing.  Lane 0 of warp 17
+// lane l of warp w owns column 64 ct + 8 (w / 2) + l / 4 and complex
+// element 4 (w % 2) + l % 4 of every stage, and reads X in groups of OZ_FG
+// stages (the 512 contiguous bytes of a column per group come from two
+// warps), two groups ahead of the slicing.  Lane 0 of warp 17
 // fills the A half of each buffer with one bulk copy of the pre-sliced basis
 // (28 KB, L2-resident) as soon as the buffer's previous MMAs are done.  Lane
 // 0 of warp 16 issues the stage's MMAs: slice sa of A against the
@@ -249,31 +250,55 @@ __device__ __forceinline__ void slice7_words(double re, double im, int E, uint32
 // levels sa+sb .. sa+sb+g-1 (the levels are 64 columns apart) -- 10 MMAs of
 // N = 64 .. 256 per stage.  The producers and warp 16 meet at a named barrier
 // after each unit (the levels drained before the next unit overwrites them);
-// warp 17 stays out of it and copies ahead across units.  Barriers per buffer: "afull" counts the A bytes,
-// "bfull" one arrival per producer warp, "done" receives the MMA commit; the
-// n-th phase of buffer b belongs to the block's stage b + OZ_NBUF n (buffer
-// and phase parity are carried along with the stage count).  At the end of
-// each unit the producers drain the TMEM levels into double-float running
-// sums kept in shared memory (column-major, so a warp's 32 rows are 32
+// warp 17 stays out of it and copies ahead across units.
+//
+// Two rings: OZ_NA buffers for A, OZ_NB (deeper) for B, so that the producers
+// can run further ahead of the MMAs than the A copies need to.  Barriers per
+// buffer: "afull" counts the A bytes, "bfull" one arrival per producer warp,
+// "adone" / "bdone" receive the MMA commit of the buffer's stage; the n-th
+// phase of buffer b of a ring of depth D belongs to the block's stage b + D n
+// (buffer and phase parity are carried along with the stage count).  Before
+// draining a unit the producers already store the first read group of the
+// next unit of the same tile (its buffers were freed by this unit's MMAs),
+// so that the MMAs restart as soon as the drain ends.  At the end of each
+// unit the producers drain the TMEM levels into double-float running sums
+// kept in shared memory (column-major, so a warp's 32 rows are 32
 // consecutive words): thread (warp w, lane l) owns row 32 (w % 4) + l and
 // columns 16 (w / 4) .. + 15.
-constexpr int OZ_NBUF = 3;
+constexpr int OZ_NA = 3;  // A ring depth
+constexpr int OZ_NB = 5;  // B ring depth
 constexpr int OZ_PWARPS = 16;
 constexpr int OZ_PRODUCERS = 32 * OZ_PWARPS;
 constexpr int OZ_THREADS = OZ_PRODUCERS + 64;      // 18 warps: + the MMA warp and the copy warp
 constexpr int OZ_FG = 4;                           // stages per X read group
 constexpr int OZ_CHUNK = OZ_DRAIN / OZ_KS;         // stages per work unit (32)
 constexpr int OZ_DC = OZ_N / (OZ_PWARPS / 4);      // columns drained per thread (16)
-constexpr int OZ_SA = OZ_S * OZ_M * OZ_KS * 2;     // A half of a stage buffer (28 KB)
-constexpr int OZ_SB = OZ_S * OZ_N * OZ_KS * 2;     // B half (14 KB)
+constexpr int OZ_SA = OZ_S * OZ_M * OZ_KS * 2;     // A part of a stage (28 KB)
+constexpr int OZ_SB = OZ_S * OZ_N * OZ_KS * 2;     // B part (14 KB)
 constexpr int OZ_ACC = 2 * OZ_M * OZ_N * 4;        // running sums, hi and lo (64 KB)
 constexpr int OZ_MAX_BLOCKS = 256;                 // blocks of the persistent launch (at most)
 static_assert(OZ_CHUNK % (2 * OZ_FG) == 0 && OZ_FG % 2 == 0, "units hold whole pairs of read groups");
+// the early read group of the next unit waits only for MMAs of this unit
+static_assert(OZ_FG < OZ_NB, "B ring deeper than a read group");
 static_assert(OZ_PRODUCERS == OZ_N * (OZ_KS / 2), "one complex element per producer and stage");
 // the grouped MMAs: plane sb + 1 of a B stage starts where row OZ_N of plane sb
 // would (8-row groups (OZ_KS / 8) * 128 bytes apart), and the levels fit TMEM
 static_assert((OZ_N / 8) * ((OZ_KS / 8) * 128) == OZ_N * OZ_KS * 2, "B planes contiguous as rows");
 static_assert(OZ_LV * OZ_N <= OZ_TCOLS && 4 * OZ_N <= 256, "level columns");
+
+// A position in a ring of D buffers: the buffer and the phase parity of its
+// current use.
+struct RingPos {
+    int i;
+    uint32_t ph;
+};
+template <int D>
+__device__ __forceinline__ void ring_next(RingPos &r) {
+    if (++r.i == D) {
+        r.i = 0;
+        r.ph ^= 1u;
+    }
+}
 
 // First unit of block i of G over U units.
 __host__ __device__ __forceinline__ long long oz_u0(long long i, long long U, long long G) { return i * U / G; }
@@ -294,24 +319,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                                                         long long ldC, long long col_off, int *err,
                                                         unsigned long long wait) {
     extern __shared__ __align__(1024) uint8_t dsm[];
-    __shared__ __align__(8) uint64_t afull[OZ_NBUF], bfull[OZ_NBUF], done[OZ_NBUF], cdone;
+    __shared__ __align__(8) uint64_t afull[OZ_NA], adone[OZ_NA], bfull[OZ_NB], bdone[OZ_NB], cdone;
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = warp < OZ_PWARPS;
     const bool issuer = threadIdx.x == OZ_PRODUCERS;       // lane 0 of warp 16
     const bool copier = threadIdx.x == OZ_PRODUCERS + 32;  // lane 0 of warp 17
     const int row = 32 * (warp & 3) + lane, cbase = OZ_DC * ((warp >> 2) & 3);
-    float *acc_hs = (float *)(dsm + OZ_NBUF * (OZ_SA + OZ_SB));  // [column][row]
+    uint8_t *bring = dsm + OZ_NA * OZ_SA;                        // the B ring after the A ring
+    float *acc_hs = (float *)(bring + OZ_NB * OZ_SB);            // [column][row]
     float *acc_ls = acc_hs + OZ_M * OZ_N;
     if (producer)
 #pragma unroll
         for (int c = 0; c < OZ_DC; c++) acc_hs[(cbase + c) * OZ_M + row] = acc_ls[(cbase + c) * OZ_M + row] = 0.f;
     if (warp == 0) tmem_alloc(&tslot, OZ_TCOLS);
     if (threadIdx.x == 0) {
-        for (int b = 0; b < OZ_NBUF; b++) {
+        for (int b = 0; b < OZ_NA; b++) {
             mbar_init(&afull[b], 1);
+            mbar_init(&adone[b], 1);
+        }
+        for (int b = 0; b < OZ_NB; b++) {
             mbar_init(&bfull[b], OZ_PWARPS);
-            mbar_init(&done[b], 1);
+            mbar_init(&bdone[b], 1);
         }
         mbar_init(&cdone, 1);
     }
@@ -329,7 +358,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     const int t_first = (int)(u0 / nch);
     const uint32_t dsm0 = smem_u32(dsm);
     // producer: this thread's column of a tile and its complex element of a stage
-    const int jj = (threadIdx.x >> 3) & (OZ_N - 1), p0 = threadIdx.x & 7;
+    // warp w covers 8 columns x 4 complex elements: its slice words of one plane
+    // are 32 consecutive words of the K-major buffer (one store, no bank conflict)
+    const int jj = 8 * ((warp >> 1) & 7) + (lane >> 2), p0 = 4 * (warp & 1) + (lane & 3);
     constexpr int pstride = OZ_N * OZ_KS / 2;  // plane stride in 32-bit words
     const uint32_t woff = kmajor_off(jj, 2 * p0, OZ_KS) >> 2;
     int E = 0, nlim = 0;                       // of the current tile's column
@@ -345,9 +376,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         }
     };
     const long long gtot = (long long)nu * OZ_CHUNK;  // stages of this block
-    // the block's stage g: buffer b, phase parity ph (of this use of the buffer)
-    int b = 0;
-    uint32_t ph = 0;
+    // this thread's position in each ring (buffer, phase parity of its use)
+    // and its role's count of the block's stages
+    RingPos ra{0, 0u}, rb{0, 0u};
     long long g = 0;
     // the barrier of the producers and the MMA warp at the end of a unit: the
     // levels are drained before the next unit's first MMAs overwrite them
@@ -356,43 +387,46 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         asm volatile("bar.sync 1, %0;" ::"r"(OZ_PRODUCERS + 32) : "memory");
         tc_fence_after();
     };
-    auto advance = [&]() {
-        g++;
-        if (++b == OZ_NBUF) {
-            b = 0;
-            ph ^= 1u;
-        }
-    };
-    // store the slice words of tile stage st (zeros past the column's end)
-    // once its buffer is free; the warp's stores become visible to the tensor
-    // core, then one lane arrives
-    auto put = [&](int st, const uint32_t (&w)[OZ_S]) {
-        if (g >= OZ_NBUF) ok = mbar_wait(&done[b], ph ^ 1u, wait) && ok;  // the MMAs of stage g - OZ_NBUF
-        uint32_t *o = (uint32_t *)(dsm + b * (OZ_SA + OZ_SB) + OZ_SA) + woff;
+    // the slice words of tile stage st (zeros past the column's end) into the
+    // stage's B buffer, once the MMAs of stage g - OZ_NB are done with it
+    auto store = [&](int st, const uint32_t (&w)[OZ_S]) {
+        if (g >= OZ_NB) ok = mbar_wait(&bdone[rb.i], rb.ph ^ 1u, wait) && ok;
+        uint32_t *o = (uint32_t *)(bring + rb.i * OZ_SB) + woff;
         const bool in = st < nlim;
 #pragma unroll
         for (int t = 0; t < OZ_S; t++) o[t * pstride] = in ? w[t] : 0u;
+    };
+    // two consecutive stages: one fence makes both buffers visible to the
+    // tensor core, then one lane arrives on each
+    auto put2 = [&](int st, const uint32_t (&w0)[OZ_S], const uint32_t (&w1)[OZ_S]) {
+        store(st, w0);
+        const int b0 = rb.i;
+        ring_next<OZ_NB>(rb);
+        g++;
+        store(st + 1, w1);
         fence_async_smem();
         __syncwarp();
-        if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[b])) : "memory");
-        advance();
+        if (lane == 0) {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[b0])) : "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[rb.i])) : "memory");
+        }
+        ring_next<OZ_NB>(rb);
+        g++;
     };
     // a read group in pairs of stages: both stages' values are sliced first
-    // (independent work), then stored in order
+    // (independent work), then stored
     auto group = [&](int q, double2 (&v)[OZ_FG]) {
 #pragma unroll
         for (int u = 0; u < OZ_FG; u += 2) {
-            const int st = q * OZ_FG + u;
             uint32_t w0[OZ_S], w1[OZ_S];
             slice7_words(v[u].x, v[u].y, E, w0);
             slice7_words(v[u + 1].x, v[u + 1].y, E, w1);
-            put(st, w0);
-            put(st + 1, w1);
+            put2(q * OZ_FG + u, w0, w1);
         }
         if (q + 2 < ngr) fetch(q + 2, v);
     };
-    int seg_c0 = 0;  // first chunk of the current tile segment
+    int seg_c0 = 0;    // first chunk of the current tile segment
+    bool early = false;  // this unit's first read group was stored before the last drain
     if (producer) {
     for (int du = 0; du < nu; du++) {
         const long long u = u0 + du;
@@ -402,23 +436,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         const int ct = t / nrt;
         if (du == 0 || c == 0) {  // a new tile: this thread's column, its scale and first reads
             seg_c0 = c;
-            if (producer) {
-                const long long j = (long long)ct * OZ_N + jj;
-                const bool live = j < Mb;
-                E = live ? Eb[j] : 0;
-                x = X + (live ? j : 0) * ldX + p0;
-                nlim = live ? (int)((N - p0 + (OZ_KS / 2) - 1) / (OZ_KS / 2)) : 0;  // stages holding the element
-                fetch(c * (OZ_CHUNK / OZ_FG), xa);
-                fetch(c * (OZ_CHUNK / OZ_FG) + 1, xb);
-            }
+            const long long j = (long long)ct * OZ_N + jj;
+            const bool live = j < Mb;
+            E = live ? Eb[j] : 0;
+            x = X + (live ? j : 0) * ldX + p0;
+            nlim = live ? (int)((N - p0 + (OZ_KS / 2) - 1) / (OZ_KS / 2)) : 0;  // stages holding the element
+            fetch(c * (OZ_CHUNK / OZ_FG), xa);
+            fetch(c * (OZ_CHUNK / OZ_FG) + 1, xb);
         }
-        if (producer) {
-            const int q0 = c * (OZ_CHUNK / OZ_FG);
-            // a unit holds an even number of read groups, so group q meets set q % 2
-            for (int q = q0; q < q0 + OZ_CHUNK / OZ_FG; q += 2) {
-                group(q, xa);
-                group(q + 1, xb);
+        {
+            // read group q uses register set q % 2 (a unit starts on an even group)
+            const int q0 = c * (OZ_CHUNK / OZ_FG), q1 = q0 + OZ_CHUNK / OZ_FG;
+            for (int q = q0 + (early ? 1 : 0); q < q1; q++) {
+                if (q & 1) group(q, xb);
+                else group(q, xa);
             }
+            // the next unit's first read group, when that unit continues this
+            // tile: its OZ_FG < OZ_NB buffers wait only for MMAs of this unit
+            early = du + 1 < nu && c + 1 < nch;
+            if (early) group(q1, xa);
             // drain: wait for the unit's MMAs (cdone completes once per unit and
             // no thread runs more than one unit behind), then read this
             // thread's TMEM lane; levels combined smallest first, in double-float
@@ -477,14 +513,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     } else if (warp == OZ_PWARPS) {
         // warp 16: lane 0 issues; the unit barrier with the producers
         auto issue = [&](bool first_of_unit) {
-            ok = mbar_wait(&afull[b], ph, wait) && ok;
-            ok = mbar_wait(&bfull[b], ph, wait) && ok;
+            ok = mbar_wait(&afull[ra.i], ra.ph, wait) && ok;
+            ok = mbar_wait(&bfull[rb.i], rb.ph, wait) && ok;
             tc_fence_after();
             // one descriptor per operand and stage; slices and K steps are
             // constant offsets of its 16-byte address field
-            const uint32_t base = dsm0 + (uint32_t)(b * (OZ_SA + OZ_SB));
-            const uint64_t ad0 = smem_desc(base, 128, (OZ_KS / 8) * 128);
-            const uint64_t bd0 = smem_desc(base + OZ_SA, 128, (OZ_KS / 8) * 128);
+            const uint64_t ad0 = smem_desc(dsm0 + (uint32_t)(ra.i * OZ_SA), 128, (OZ_KS / 8) * 128);
+            const uint64_t bd0 = smem_desc(dsm0 + (uint32_t)(OZ_NA * OZ_SA + rb.i * OZ_SB), 128, (OZ_KS / 8) * 128);
             const uint32_t acc0 = first_of_unit ? 0u : 1u;  // a unit's first stage overwrites the levels
 #pragma unroll
             for (int sa = 0; sa < OZ_S; sa++)
@@ -501,8 +536,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                         tc_mma_bf16(tmem + (uint32_t)(L * OZ_N), ad, bd, idesc_bf16_f32(OZ_M, gg * OZ_N), ac);
                     }
                 }
-            tc_commit(&done[b]);
-            advance();
+            tc_commit(&adone[ra.i]);
+            tc_commit(&bdone[rb.i]);
+            ring_next<OZ_NA>(ra);
+            ring_next<OZ_NB>(rb);
         };
         for (int du = 0; du < nu; du++) {
             if (issuer) {
@@ -530,7 +567,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         auto load_a = [&](int bb) {  // the next stage's A into buffer bb
             uint64_t *fb = &afull[bb];
             mbar_expect_tx(fb, OZ_SA);
-            bulk_g2s(dsm + bb * (OZ_SA + OZ_SB), a_base + a_s * a_stage, OZ_SA, fb);
+            bulk_g2s(dsm + bb * OZ_SA, a_base + a_s * a_stage, OZ_SA, fb);
             if (++a_s == OZ_CHUNK) {
                 a_s = 0;
                 if (++a_u < u1) a_base = unit_a(a_u);
@@ -538,9 +575,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
         };
         if (copier) {
             for (long long gg = 0; gg < gtot; gg++) {
-                if (gg >= OZ_NBUF) ok = mbar_wait(&done[b], ph ^ 1u, wait) && ok;  // the MMAs of stage gg - OZ_NBUF
-                load_a(b);
-                advance();
+                if (gg >= OZ_NA) ok = mbar_wait(&adone[ra.i], ra.ph ^ 1u, wait) && ok;  // the MMAs of stage gg - OZ_NA
+                load_a(ra.i);
+                ring_next<OZ_NA>(ra);
             }
         }
         __syncwarp();
@@ -621,7 +658,7 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
     k_oz_slice_A<<<k, 256, 0, s>>>(Q, N, k, ldQ, Kp, Rp, As, Ea);
     const long long ge = (Mb * 32 + 255) / 256;
     k_oz_exp_B<<<(unsigned)(ge < 4096 ? ge : 4096), 256, 0, s>>>(X, N, Mb, ldX, Eb);
-    const size_t dsm = (size_t)OZ_NBUF * (OZ_SA + OZ_SB) + OZ_ACC;  // 126 KB ring + 64 KB running sums
+    const size_t dsm = (size_t)OZ_NA * OZ_SA + (size_t)OZ_NB * OZ_SB + OZ_ACC;  // 154 KB of rings + 64 KB sums
     static int sms = 0;
     if (!sms) {
         cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
