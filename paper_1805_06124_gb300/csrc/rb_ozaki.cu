@@ -29,7 +29,8 @@ constexpr int OZ_M = 128;        // A rows per tile
 constexpr int OZ_N = 64;         // B rows (columns of C) per tile
 constexpr int OZ_KS = 16;        // K per shared-memory stage
 constexpr int OZ_DRAIN = 512;    // K per exact TMEM chunk
-constexpr int OZ_TCOLS = 512;    // TMEM columns allocated (7 levels x 64 used)
+constexpr int OZ_TCOLS = 512;    // TMEM columns allocated (7 levels x 64, then the running sums' high words)
+constexpr int OZ_ACOL = OZ_LV * 64;  // first column of the running sums
 
 // The basis slice planes are stored tile by tile in the K-major shared-memory
 // layout the MMAs read (8-row x 16-byte core matrices, see kmajor_off), so that
@@ -163,26 +164,52 @@ __global__ void k_oz_exp_B(const double2 *__restrict__ X, long long N, long long
 __device__ __forceinline__ void dfs_add(float &ah, float &al, float bh, float bl) { df_add(ah, al, bh, bl); }
 
 // Four FP32 columns of this thread's TMEM lane from each of the seven level
-// accumulators (level L at column offset L * OZ_N), with one wait for all
-// 28 values: the wait names every register, so no use can move above it.
-__device__ __forceinline__ void tmem_ld4_levels(uint32_t taddr, float (&v)[OZ_LV][4]) {
-    uint32_t r[OZ_LV][4];
+// accumulators (level L at column offset L * OZ_N) and from the running
+// sums' high words (at tacc), with one wait for all 32 values: the wait
+// names every register, so no use can move above it.
+__device__ __forceinline__ void tmem_ld4_levels(uint32_t taddr, uint32_t tacc, float (&v)[OZ_LV][4], float (&a)[4]) {
+    uint32_t r[OZ_LV + 1][4];
 #pragma unroll
-    for (int L = 0; L < OZ_LV; L++)
+    for (int L = 0; L <= OZ_LV; L++)
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                      : "=r"(r[L][0]), "=r"(r[L][1]), "=r"(r[L][2]), "=r"(r[L][3])
-                     : "r"(taddr + (uint32_t)(L * OZ_N)));
+                     : "r"(L < OZ_LV ? taddr + (uint32_t)(L * OZ_N) : tacc));
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[1][0]), "+r"(r[1][1]),
                    "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]),
                    "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]), "+r"(r[4][0]), "+r"(r[4][1]),
                    "+r"(r[4][2]), "+r"(r[4][3]), "+r"(r[5][0]), "+r"(r[5][1]), "+r"(r[5][2]), "+r"(r[5][3]),
-                   "+r"(r[6][0]), "+r"(r[6][1]), "+r"(r[6][2]), "+r"(r[6][3]));
+                   "+r"(r[6][0]), "+r"(r[6][1]), "+r"(r[6][2]), "+r"(r[6][3]), "+r"(r[7][0]), "+r"(r[7][1]),
+                   "+r"(r[7][2]), "+r"(r[7][3]));
 #pragma unroll
     for (int L = 0; L < OZ_LV; L++)
 #pragma unroll
         for (int e = 0; e < 4; e++) v[L][e] = __uint_as_float(r[L][e]);
+#pragma unroll
+    for (int e = 0; e < 4; e++) a[e] = __uint_as_float(r[OZ_LV][e]);
 }
+
+// Four FP32 values into four consecutive columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const float (&a)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(__float_as_uint(a[0])),
+                 "r"(__float_as_uint(a[1])), "r"(__float_as_uint(a[2])), "r"(__float_as_uint(a[3]))
+                 : "memory");
+}
+
+// Four consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&a)[4]) {
+    uint32_t r0, r1, r2, r3;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3));
+    a[0] = __uint_as_float(r0);
+    a[1] = __uint_as_float(r1);
+    a[2] = __uint_as_float(r2);
+    a[3] = __uint_as_float(r3);
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Snapshot (B) slices inside the GEMM.  X = round(v 2^(49-E)) is formed as
 // the magnitude |X| (one right shift of the 53-bit significand, at least 5
@@ -252,8 +279,8 @@ __device__ __forceinline__ void slice7_words(double re, double im, int E, uint32
 // after each unit (the levels drained before the next unit overwrites them);
 // warp 17 stays out of it and copies ahead across units.
 //
-// Two rings: OZ_NA buffers for A, OZ_NB (deeper) for B, so that the producers
-// can run further ahead of the MMAs than the A copies need to.  Barriers per
+// Two rings: OZ_NA buffers for A (a copy from L2 takes a few stages to
+// land) and OZ_NB for B (the producers run ahead of the MMAs).  Barriers per
 // buffer: "afull" counts the A bytes, "bfull" one arrival per producer warp,
 // "adone" / "bdone" receive the MMA commit of the buffer's stage; the n-th
 // phase of buffer b of a ring of depth D belongs to the block's stage b + D n
@@ -262,10 +289,12 @@ __device__ __forceinline__ void slice7_words(double re, double im, int E, uint32
 // next unit of the same tile (its buffers were freed by this unit's MMAs),
 // so that the MMAs restart as soon as the drain ends.  At the end of each
 // unit the producers drain the TMEM levels into double-float running sums
-// kept in shared memory (column-major, so a warp's 32 rows are 32
-// consecutive words): thread (warp w, lane l) owns row 32 (w % 4) + l and
-// columns 16 (w / 4) .. + 15.
-constexpr int OZ_NA = 3;  // A ring depth
+// whose high words stay in TMEM (the 64 columns after the levels) and whose
+// low words sit in shared memory (column-major, so a warp's 32 rows are 32
+// consecutive words): thread (warp w, lane l) owns row 32 (w % 4) + l (its
+// TMEM lane) and columns 16 (w / 4) .. + 15.  Keeping the high words out of
+// shared memory leaves room for a fourth A buffer.
+constexpr int OZ_NA = 4;  // A ring depth
 constexpr int OZ_NB = 5;  // B ring depth
 constexpr int OZ_PWARPS = 16;
 constexpr int OZ_PRODUCERS = 32 * OZ_PWARPS;
@@ -275,7 +304,7 @@ constexpr int OZ_CHUNK = OZ_DRAIN / OZ_KS;         // stages per work unit (32)
 constexpr int OZ_DC = OZ_N / (OZ_PWARPS / 4);      // columns drained per thread (16)
 constexpr int OZ_SA = OZ_S * OZ_M * OZ_KS * 2;     // A part of a stage (28 KB)
 constexpr int OZ_SB = OZ_S * OZ_N * OZ_KS * 2;     // B part (14 KB)
-constexpr int OZ_ACC = 2 * OZ_M * OZ_N * 4;        // running sums, hi and lo (64 KB)
+constexpr int OZ_ACC = OZ_M * OZ_N * 4;            // running sums' low words (32 KB)
 constexpr int OZ_MAX_BLOCKS = 256;                 // blocks of the persistent launch (at most)
 static_assert(OZ_CHUNK % (2 * OZ_FG) == 0 && OZ_FG % 2 == 0, "units hold whole pairs of read groups");
 // the early read group of the next unit waits only for MMAs of this unit
@@ -284,7 +313,7 @@ static_assert(OZ_PRODUCERS == OZ_N * (OZ_KS / 2), "one complex element per produ
 // the grouped MMAs: plane sb + 1 of a B stage starts where row OZ_N of plane sb
 // would (8-row groups (OZ_KS / 8) * 128 bytes apart), and the levels fit TMEM
 static_assert((OZ_N / 8) * ((OZ_KS / 8) * 128) == OZ_N * OZ_KS * 2, "B planes contiguous as rows");
-static_assert(OZ_LV * OZ_N <= OZ_TCOLS && 4 * OZ_N <= 256, "level columns");
+static_assert(OZ_LV * OZ_N <= OZ_ACOL && OZ_ACOL + OZ_N <= OZ_TCOLS && 4 * OZ_N <= 256, "level columns");
 
 // A position in a ring of D buffers: the buffer and the phase parity of its
 // current use.
@@ -327,11 +356,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     const bool copier = threadIdx.x == OZ_PRODUCERS + 32;  // lane 0 of warp 17
     const int row = 32 * (warp & 3) + lane, cbase = OZ_DC * ((warp >> 2) & 3);
     uint8_t *bring = dsm + OZ_NA * OZ_SA;                        // the B ring after the A ring
-    float *acc_hs = (float *)(bring + OZ_NB * OZ_SB);            // [column][row]
-    float *acc_ls = acc_hs + OZ_M * OZ_N;
+    float *acc_ls = (float *)(bring + OZ_NB * OZ_SB);            // low words, [column][row]
     if (producer)
 #pragma unroll
-        for (int c = 0; c < OZ_DC; c++) acc_hs[(cbase + c) * OZ_M + row] = acc_ls[(cbase + c) * OZ_M + row] = 0.f;
+        for (int c = 0; c < OZ_DC; c++) acc_ls[(cbase + c) * OZ_M + row] = 0.f;
     if (warp == 0) tmem_alloc(&tslot, OZ_TCOLS);
     if (threadIdx.x == 0) {
         for (int b = 0; b < OZ_NA; b++) {
@@ -348,6 +376,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
+    // this thread's TMEM lane (its row) and the running sums' high words
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t tacc = tmem + lane_off + (uint32_t)(OZ_ACOL + cbase);
+    if (producer) {
+        const float z[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int h = 0; h < OZ_DC / 4; h++) tmem_st4(tacc + 4 * h, z);
+        tmem_wait_st();
+    }
     bool ok = true;
     const int nst = (int)(Kp / OZ_KS);  // whole units, Kp <= 2^23
     const int nch = nst / OZ_CHUNK;
@@ -460,11 +497,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
             // thread's TMEM lane; levels combined smallest first, in double-float
             ok = mbar_wait(&cdone, (uint32_t)(du & 1), wait) && ok;
             tc_fence_after();
-            const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
 #pragma unroll
             for (int h = 0; h < OZ_DC / 4; h++) {
-                float v[OZ_LV][4];
-                tmem_ld4_levels(tmem + lane_off + (uint32_t)(cbase + 4 * h), v);
+                float v[OZ_LV][4], ah[4];
+                tmem_ld4_levels(tmem + lane_off + (uint32_t)(cbase + 4 * h), tacc + 4 * h, v, ah);
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
                     // levels added smallest first by TwoSum, the errors gathered
@@ -480,32 +516,41 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __nv_bfloat16 *
                         tl = __fadd_rn(tl, se);
                     }
                     const int a = (cbase + 4 * h + e) * OZ_M + row;
-                    float ah = acc_hs[a], al = acc_ls[a];
-                    dfs_add(ah, al, th, tl);
-                    acc_hs[a] = ah;
+                    float al = acc_ls[a];
+                    dfs_add(ah[e], al, th, tl);
                     acc_ls[a] = al;
                 }
+                tmem_st4(tacc + 4 * h, ah);
             }
+            tmem_wait_st();
             if (du == nu - 1 || c == nch - 1) {
                 // the tile segment ends: the whole tile goes to C, a part to the
-                // block's slot; the sums restart for the next tile
+                // block's slot; the sums restart at zero for the next tile
                 const long long R = (long long)rt * OZ_M + row;
                 const bool whole = seg_c0 == 0 && c == nch - 1;
                 const long long slot = 2LL * blockIdx.x + (t == t_first ? 0 : 1);
 #pragma unroll
-                for (int cc = 0; cc < OZ_DC; cc++) {
-                    const int a = (cbase + cc) * OZ_M + row;
-                    const double val = (double)acc_hs[a] + (double)acc_ls[a];
-                    acc_hs[a] = acc_ls[a] = 0.f;
-                    const long long jc = (long long)ct * OZ_N + cbase + cc;
-                    if (whole) {
-                        if (R < 2LL * k && jc < Mb)
-                            ((double *)(C + (R >> 1) * ldC) + (R & 1))[2 * (col_off + jc)] =
-                                ldexp(val, Ea[R >> 1] + Eb[jc]);
-                    } else {
-                        part[(slot * OZ_N + cbase + cc) * OZ_M + row] = val;
+                for (int h = 0; h < OZ_DC / 4; h++) {
+                    float ah[4];
+                    tmem_ld4(tacc + 4 * h, ah);
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int cl = cbase + 4 * h + e;
+                        const double val = (double)ah[e] + (double)acc_ls[cl * OZ_M + row];
+                        acc_ls[cl * OZ_M + row] = 0.f;
+                        ah[e] = 0.f;
+                        const long long jc = (long long)ct * OZ_N + cl;
+                        if (whole) {
+                            if (R < 2LL * k && jc < Mb)
+                                ((double *)(C + (R >> 1) * ldC) + (R & 1))[2 * (col_off + jc)] =
+                                    ldexp(val, Ea[R >> 1] + Eb[jc]);
+                        } else {
+                            part[(slot * OZ_N + cl) * OZ_M + row] = val;
+                        }
                     }
+                    tmem_st4(tacc + 4 * h, ah);
                 }
+                tmem_wait_st();
             }
         }
         unit_sync();
@@ -658,7 +703,7 @@ cudaError_t launch_project_tc(const double2 *Q, long long N, int k, long long ld
     k_oz_slice_A<<<k, 256, 0, s>>>(Q, N, k, ldQ, Kp, Rp, As, Ea);
     const long long ge = (Mb * 32 + 255) / 256;
     k_oz_exp_B<<<(unsigned)(ge < 4096 ? ge : 4096), 256, 0, s>>>(X, N, Mb, ldX, Eb);
-    const size_t dsm = (size_t)OZ_NA * OZ_SA + (size_t)OZ_NB * OZ_SB + OZ_ACC;  // 154 KB of rings + 64 KB sums
+    const size_t dsm = (size_t)OZ_NA * OZ_SA + (size_t)OZ_NB * OZ_SB + OZ_ACC;  // 182 KB of rings + 32 KB of sums
     static int sms = 0;
     if (!sms) {
         cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
