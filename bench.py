@@ -881,7 +881,10 @@ def run_ours(args):
                    "sample": f"the whole workload: one full greedy on all {M} columns (N={N}, seed {SEED}, "
                              f"tol {TOL}), k={k_o}, {t_o:.1f} s, OpenMP build (column loops on all host cores, "
                              f"results identical to one thread)",
-                   "k": k_o, "pivots_equal_gpu_prefix": common}
+                   "k": k_o, "pivots_equal_gpu_prefix": common,
+                   "pivot_note": "the columns are unit-norm chirps, so the first pivot is a tie to rounding and the "
+                                 "unforced runs part there; parity is checked by replaying the GPU's pivots "
+                                 "through the oracle (tests/test_gpu_fullsize.py)"}
             del r_o
         except Exception as e:  # no OpenMP runtime on this host
             cpu = {"unavailable": str(e)[:200]}
