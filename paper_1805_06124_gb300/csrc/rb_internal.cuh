@@ -55,6 +55,8 @@ struct DevState {
     double sel_max;             // streamed form: largest stale bound of the iteration
     unsigned int ticket_sel;
     int pad2;
+    unsigned int bar_count;     // grid barrier of the fused IMGS kernel: arrivals
+    unsigned int bar_gen;       // and generation
 };
 
 // Problem description passed by value to every kernel of a greedy call.
