@@ -644,13 +644,20 @@ __global__ void k_oz_fixup(const double *__restrict__ part, const int *__restric
     if (i0 == i1) return;
     const int rt = (int)(t % nrt);
     const long long ct = t / nrt;
+    // the sharing blocks' slots, once per block (64-bit divisions), not per element
+    constexpr int MAXS = 64;
+    __shared__ long long s_slot[MAXS];
+    const int ns = i1 - i0 + 1;
+    auto slot_of = [&](int i) { return 2LL * i + (oz_u0(i, U, G) / nch == t ? 0 : 1); };
+    for (int j = threadIdx.x; j < ns && j < MAXS; j += blockDim.x) s_slot[j] = slot_of(i0 + j);
+    __syncthreads();
     for (int e = threadIdx.x; e < OZ_M * OZ_N; e += blockDim.x) {
         const int row = e % OZ_M, col = e / OZ_M;
         const long long R = (long long)rt * OZ_M + row, jc = ct * OZ_N + col;
         if (R >= 2LL * k || jc >= Mb) continue;
         double sum = 0.0;
-        for (int i = i0; i <= i1; i++) {
-            const long long slot = 2LL * i + (oz_u0(i, U, G) / nch == t ? 0 : 1);
+        for (int j = 0; j < ns; j++) {
+            const long long slot = j < MAXS ? s_slot[j] : slot_of(i0 + j);
             sum += part[(slot * OZ_N + col) * OZ_M + row];
         }
         ((double *)(C + (R >> 1) * ldC) + (R & 1))[2 * (col_off + jc)] = ldexp(sum, Ea[R >> 1] + Eb[jc]);
